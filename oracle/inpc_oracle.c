@@ -1,0 +1,670 @@
+/*
+ * inpc_oracle.c -- plain, slow, FP64 CPU oracle for the INPC hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package's smoke check
+ * and the benchmark's CPU-baseline leg may load this library.  It shares no
+ * code, header, table or helper with the CUDA path; it is written directly
+ * from the paper's definitions, one function per step, in the paper's order:
+ *
+ *   sampling      Sec. 3.2 "Viewpoint-Specific Sampling" (multinomial sampling
+ *                 with replacement, uniform position in the chosen leaf), with
+ *                 the precision remark of Sec. 3.1 "Subdivision";
+ *   hash query    Sec. 3.3 and App. A.5 (multi-resolution grid, trilinear
+ *                 interpolation per level, features concatenated);
+ *   rasterizer    Sec. 3.4 (Eq. 5 projection, Eq. 6 bilinear opacity),
+ *                 Eq. 1 front-to-back alpha blending, App. A.6 early stop at
+ *                 transmittance 1e-4 and Algorithm 1's stage order;
+ *   backward      App. A.6 "During optimization ..." (per-splat gradients
+ *                 combined into per-point gradients), written here as the
+ *                 plain analytic derivative of the forward definition.
+ *
+ * Readings where the paper is silent (all listed in the design notes):
+ *   - leaf weights are quantised to integers q_i = rint(w_i / max w * 2^29)
+ *     and the CDF is their exact prefix sum (FP64 holds every partial sum
+ *     exactly while the leaf count stays below 2^24, the paper's 256^3 cap);
+ *   - the leaf drawn for a 53-bit uniform integer b is the smallest i with
+ *     cdf_i > floor(b * Q / 2^53), Q = sum q (zero-weight leaves never drawn);
+ *   - the sampled list of leaf indices is emitted grouped by leaf, in
+ *     ascending leaf order (the draws fix only how many samples each leaf
+ *     gets); positions are drawn per output slot;
+ *   - random numbers come from Philox4x32-10 (Salmon et al., SC'11) keyed by
+ *     the 64-bit seed, counter (sample lo, sample hi, view, purpose);
+ *   - a level-l leaf spans center +- root_size * 2^-l / 2, half-open;
+ *   - grid level l has resolution N_l; vertex coordinates 0..N_l; the level is
+ *     stored densely iff (N_l+1)^3 <= T, else through the spatial hash
+ *     x*1 ^ y*2654435761 ^ z*805459861 (mod T);
+ *   - the projection (Eq. 5) is evaluated in the kernel's FP32 arithmetic with
+ *     a fixed operation order, because it decides integer pixel indices and
+ *     the depth order; everything downstream of it is FP64 here;
+ *   - pixel (i, j) has its center at (i + 0.5, j + 0.5);
+ *   - per-pixel order: ascending (FP32 depth, point id);
+ *   - alpha = min(alpha_h * w, alpha_max); blending stops after the fragment
+ *     whose update takes T below t_min (that fragment is included);
+ *   - a point's feature gradient is the plain sum of its splat gradients; its
+ *     opacity gradient sums the splat gradients times dalpha/dalpha_h.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_OK 0
+#define ORACLE_ERR_ARG -1
+#define ORACLE_ERR_WEIGHTS -2
+#define ORACLE_ERR_NOMEM -3
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw,       */
+/* "Parallel random numbers: as easy as 1, 2, 3", SC'11).  One round maps   */
+/* the 4-word counter through two 32x32->64 multiplications whose high      */
+/* halves are xored with the other two words and the round key; the key is  */
+/* advanced by the Weyl constants between rounds.                           */
+/* ------------------------------------------------------------------------ */
+static const uint32_t PHILOX_MUL_A = 0xD2511F53u;
+static const uint32_t PHILOX_MUL_B = 0xCD9E8D57u;
+static const uint32_t PHILOX_WEYL_A = 0x9E3779B9u;
+static const uint32_t PHILOX_WEYL_B = 0xBB67AE85u;
+
+void oracle_philox4x32_10(const uint32_t key_in[2], const uint32_t ctr_in[4], uint32_t out[4]) {
+  uint32_t x0 = ctr_in[0], x1 = ctr_in[1], x2 = ctr_in[2], x3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += PHILOX_WEYL_A;
+      k1 += PHILOX_WEYL_B;
+    }
+    uint64_t pa = (uint64_t)PHILOX_MUL_A * (uint64_t)x0;
+    uint64_t pb = (uint64_t)PHILOX_MUL_B * (uint64_t)x2;
+    uint32_t pa_hi = (uint32_t)(pa >> 32), pa_lo = (uint32_t)pa;
+    uint32_t pb_hi = (uint32_t)(pb >> 32), pb_lo = (uint32_t)pb;
+    uint32_t y0 = pb_hi ^ x1 ^ k0;
+    uint32_t y1 = pb_lo;
+    uint32_t y2 = pa_hi ^ x3 ^ k1;
+    uint32_t y3 = pa_lo;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Bulk form for statistical tests: out[4*i..] = Philox(key, (i + ctr0, ctr1, ctr2, ctr3)). */
+void oracle_philox_stream(uint64_t seed, uint32_t ctr1, uint32_t ctr2, uint32_t ctr3,
+                          int64_t n, uint32_t* out) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int64_t i = 0; i < n; ++i) {
+    uint32_t ctr[4] = {(uint32_t)i, ctr1, ctr2, ctr3};
+    oracle_philox4x32_10(key, ctr, out + 4 * i);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sampling (Sec. 3.2): multinomial sampling with replacement over leaves,  */
+/* then a uniform position inside the chosen leaf.                          */
+/* ------------------------------------------------------------------------ */
+
+/* Quantised weights and their inclusive prefix sum.  Returns Q (the total)
+ * through *total.  Errors: negative, NaN or infinite weight, or no positive
+ * weight. */
+int oracle_build_cdf(const double* w, int64_t n_leaves, double* cdf, double* total) {
+  if (n_leaves <= 0 || n_leaves > (1ll << 24)) return ORACLE_ERR_ARG;
+  double wmax = 0.0;
+  for (int64_t i = 0; i < n_leaves; ++i) {
+    if (!(w[i] >= 0.0) || isinf(w[i])) return ORACLE_ERR_WEIGHTS;
+    if (w[i] > wmax) wmax = w[i];
+  }
+  if (!(wmax > 0.0)) return ORACLE_ERR_WEIGHTS;
+  double run = 0.0;
+  for (int64_t i = 0; i < n_leaves; ++i) {
+    double q = rint(ldexp(w[i] / wmax, 29));
+    run += q; /* exact: every partial sum is an integer below 2^53 */
+    cdf[i] = run;
+  }
+  *total = run;
+  return ORACLE_OK;
+}
+
+/* Smallest i with cdf[i] > r (cdf non-decreasing, r < cdf[n-1]). */
+int64_t oracle_search_cdf(const double* cdf, int64_t n_leaves, double r) {
+  int64_t lo = 0, hi = n_leaves - 1;
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (cdf[mid] > r) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+/* r = floor(b * Q / 2^53) for a 53-bit b, in exact 128-bit integer arithmetic. */
+uint64_t oracle_scale_draw(uint64_t b53, uint64_t Q) {
+  unsigned __int128 p = (unsigned __int128)b53 * (unsigned __int128)Q;
+  return (uint64_t)(p >> 53);
+}
+
+/* Leaf of draw s: smallest i with cdf_i > floor(b * Q / 2^53), b the low 53
+ * bits of Philox(key = seed, counter = (s lo, s hi, view, 0)) words 1:0. */
+static int64_t draw_leaf(const uint32_t key[2], const double* cdf, int64_t n_leaves, uint64_t Q,
+                         int64_t s, uint32_t view_id) {
+  uint32_t ctr[4] = {(uint32_t)s, (uint32_t)((uint64_t)s >> 32), view_id, 0u};
+  uint32_t r4[4];
+  oracle_philox4x32_10(key, ctr, r4);
+  uint64_t b = ((uint64_t)(r4[1] & 0x1FFFFFu) << 32) | (uint64_t)r4[0];
+  uint64_t r = oracle_scale_draw(b, Q);
+  return oracle_search_cdf(cdf, n_leaves, (double)r);
+}
+
+/* Per-draw leaf indices in draw order (exposed for tests). */
+int oracle_draw_leaves(const double* weights, int64_t n_leaves, uint64_t seed, uint32_t view_id,
+                       int64_t n_samples, int32_t* leaf_of_draw) {
+  double* cdf = (double*)malloc(sizeof(double) * (size_t)(n_leaves > 0 ? n_leaves : 1));
+  if (!cdf) return ORACLE_ERR_NOMEM;
+  double Qd = 0.0;
+  int st = oracle_build_cdf(weights, n_leaves, cdf, &Qd);
+  if (st != ORACLE_OK) { free(cdf); return st; }
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+#pragma omp parallel for schedule(static)
+  for (int64_t s = 0; s < n_samples; ++s)
+    leaf_of_draw[s] = (int32_t)draw_leaf(key, cdf, n_leaves, (uint64_t)Qd, s, view_id);
+  free(cdf);
+  return ORACLE_OK;
+}
+
+/* Full sampling step (Sec. 3.2): N draws with replacement give the per-leaf
+ * counts; the list of leaf indices is emitted in ascending leaf order (leaf
+ * i occupies slots start_i .. start_i + count_i - 1), and the sample in slot
+ * k gets the uniform position c + (u - 1/2) * root_size * 2^-l with
+ * u_d = (word_d >> 8) * 2^-24 from Philox(counter = (k lo, k hi, view, 1)).
+ * pos_out is FP64 and exact (u is a 24-bit dyadic fraction).
+ * counts_out (optional) receives count_i per leaf. */
+int oracle_sample_octree(const float* centers, const int32_t* levels, const double* weights,
+                         int64_t n_leaves, double root_size, uint64_t seed, uint32_t view_id,
+                         int64_t n_samples, int32_t* leaf_out, double* pos_out, int64_t* counts_out) {
+  if (n_samples < 0) return ORACLE_ERR_ARG;
+  int32_t* draws = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_samples > 0 ? n_samples : 1));
+  int64_t* count = (int64_t*)calloc((size_t)(n_leaves > 0 ? n_leaves : 1), sizeof(int64_t));
+  if (!draws || !count) { free(draws); free(count); return ORACLE_ERR_NOMEM; }
+  int st = oracle_draw_leaves(weights, n_leaves, seed, view_id, n_samples, draws);
+  if (st != ORACLE_OK) { free(draws); free(count); return st; }
+  for (int64_t s = 0; s < n_samples; ++s) count[draws[s]]++;
+  free(draws);
+  int64_t k = 0;
+  for (int64_t i = 0; i < n_leaves; ++i)
+    for (int64_t c = 0; c < count[i]; ++c) leaf_out[k++] = (int32_t)i;
+  if (counts_out) for (int64_t i = 0; i < n_leaves; ++i) counts_out[i] = count[i];
+  free(count);
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+#pragma omp parallel for schedule(static)
+  for (int64_t slot = 0; slot < n_samples; ++slot) {
+    int64_t leaf = leaf_out[slot];
+    uint32_t ctr[4] = {(uint32_t)slot, (uint32_t)((uint64_t)slot >> 32), view_id, 1u};
+    uint32_t r4[4];
+    oracle_philox4x32_10(key, ctr, r4);
+    double edge = ldexp(root_size, -levels[leaf]);
+    for (int d = 0; d < 3; ++d) {
+      double u = ldexp((double)(r4[d] >> 8), -24);
+      pos_out[3 * slot + d] = (double)centers[3 * leaf + d] + (u - 0.5) * edge;
+    }
+  }
+  return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Multi-resolution hash grid (Sec. 3.3, App. A.5 / Listing 1).             */
+/* ------------------------------------------------------------------------ */
+
+static int level_is_dense(int64_t res, int64_t T) {
+  int64_t side = res + 1;
+  return side * side * side <= T;
+}
+
+static int64_t level_entries(int64_t res, int64_t T) {
+  int64_t side = res + 1;
+  int64_t dense = side * side * side;
+  return dense <= T ? dense : T;
+}
+
+/* Table rows per level and their level-major offsets; returns the total. */
+int64_t oracle_hash_layout(int32_t n_levels, const int32_t* res, int32_t log2_T, int64_t* offsets) {
+  int64_t T = 1ll << log2_T;
+  int64_t off = 0;
+  for (int l = 0; l < n_levels; ++l) {
+    if (offsets) offsets[l] = off;
+    off += level_entries(res[l], T);
+  }
+  return off;
+}
+
+/* Row of the table (within its level) that holds grid vertex (vx, vy, vz). */
+int64_t oracle_hash_vertex_index(int64_t res, int32_t log2_T, int64_t vx, int64_t vy, int64_t vz) {
+  int64_t T = 1ll << log2_T;
+  if (level_is_dense(res, T)) {
+    int64_t side = res + 1;
+    return vx + vy * side + vz * side * side;
+  }
+  uint32_t h = ((uint32_t)vx * 1u) ^ ((uint32_t)vy * 2654435761u) ^ ((uint32_t)vz * 805459861u);
+  return (int64_t)(h & (uint32_t)(T - 1));
+}
+
+/* Cell and fractional offset of coordinate x on a level of resolution res:
+ * x is clamped to [0,1]; cell = min(floor(x*res), res-1); frac = x*res - cell. */
+static void grid_cell(double x, int64_t res, int64_t* cell, double* frac) {
+  if (!(x >= 0.0)) x = 0.0; /* also maps NaN to 0 */
+  if (x > 1.0) x = 1.0;
+  double s = x * (double)res;
+  double c = floor(s);
+  if (c > (double)(res - 1)) c = (double)(res - 1);
+  *cell = (int64_t)c;
+  *frac = s - c;
+}
+
+/* h[n, l*F + f] = sum over the 8 cell corners of trilinear weight * table[row, f];
+ * abs_out (optional) receives the sum of absolute terms. */
+int oracle_hash_fwd(int32_t n_levels, const int32_t* res, int32_t log2_T, int32_t n_feats,
+                    const double* table, const double* pos, int64_t n, double* h_out, double* abs_out) {
+  int64_t* offsets = (int64_t*)malloc(sizeof(int64_t) * (size_t)n_levels);
+  if (!offsets) return ORACLE_ERR_NOMEM;
+  oracle_hash_layout(n_levels, res, log2_T, offsets);
+  int64_t C = (int64_t)n_levels * n_feats;
+#pragma omp parallel for schedule(static)
+  for (int64_t p = 0; p < n; ++p) {
+    for (int l = 0; l < n_levels; ++l) {
+      int64_t cell[3];
+      double fr[3];
+      for (int d = 0; d < 3; ++d) grid_cell(pos[3 * p + d], res[l], &cell[d], &fr[d]);
+      for (int f = 0; f < n_feats; ++f) h_out[p * C + l * n_feats + f] = 0.0;
+      if (abs_out) for (int f = 0; f < n_feats; ++f) abs_out[p * C + l * n_feats + f] = 0.0;
+      for (int corner = 0; corner < 8; ++corner) {
+        int bx = corner & 1, by = (corner >> 1) & 1, bz = (corner >> 2) & 1;
+        double w = (bx ? fr[0] : 1.0 - fr[0]) * (by ? fr[1] : 1.0 - fr[1]) * (bz ? fr[2] : 1.0 - fr[2]);
+        int64_t row = offsets[l] + oracle_hash_vertex_index(res[l], log2_T, cell[0] + bx, cell[1] + by, cell[2] + bz);
+        for (int f = 0; f < n_feats; ++f) {
+          h_out[p * C + l * n_feats + f] += w * table[row * n_feats + f];
+          if (abs_out) abs_out[p * C + l * n_feats + f] += fabs(w * table[row * n_feats + f]);
+        }
+      }
+    }
+  }
+  free(offsets);
+  return ORACLE_OK;
+}
+
+/* grad_table[row, f] += weight * dh[n, l*F + f]; abs_out (optional) receives
+ * the same sum of absolute terms, used as the condition-aware scale. */
+int oracle_hash_bwd(int32_t n_levels, const int32_t* res, int32_t log2_T, int32_t n_feats,
+                    const double* pos, const double* dh, int64_t n, double* grad_out, double* abs_out) {
+  int64_t* offsets = (int64_t*)malloc(sizeof(int64_t) * (size_t)n_levels);
+  if (!offsets) return ORACLE_ERR_NOMEM;
+  oracle_hash_layout(n_levels, res, log2_T, offsets);
+  int64_t C = (int64_t)n_levels * n_feats;
+  /* levels own disjoint row ranges, so they can be accumulated independently
+   * and in point order (deterministic). */
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int l = 0; l < n_levels; ++l) {
+    for (int64_t p = 0; p < n; ++p) {
+      int64_t cell[3];
+      double fr[3];
+      for (int d = 0; d < 3; ++d) grid_cell(pos[3 * p + d], res[l], &cell[d], &fr[d]);
+      for (int corner = 0; corner < 8; ++corner) {
+        int bx = corner & 1, by = (corner >> 1) & 1, bz = (corner >> 2) & 1;
+        double w = (bx ? fr[0] : 1.0 - fr[0]) * (by ? fr[1] : 1.0 - fr[1]) * (bz ? fr[2] : 1.0 - fr[2]);
+        int64_t row = offsets[l] + oracle_hash_vertex_index(res[l], log2_T, cell[0] + bx, cell[1] + by, cell[2] + bz);
+        for (int f = 0; f < n_feats; ++f) {
+          double term = w * dh[p * C + l * n_feats + f];
+          grad_out[row * n_feats + f] += term;
+          if (abs_out) abs_out[row * n_feats + f] += fabs(term);
+        }
+      }
+    }
+  }
+  free(offsets);
+  return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rasterizer (Sec. 3.4, Eq. 1, Eq. 5, Eq. 6, App. A.6, Algorithm 1).        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float near_plane, far_plane;
+} oracle_camera;
+
+/* Eq. 5 in FP32 with a fixed operation order:
+ *   x_c = fma(R[2], z, fma(R[1], y, fma(R[0], x, t[0])))   (same for y_c, z_c)
+ *   u = fma(fx, x_c / z_c, cx),  v = fma(fy, y_c / z_c, cy),  d = z_c.
+ * Returns 1 if the point lies strictly between the near and far planes. */
+int oracle_project(const oracle_camera* cam, const float* p, float* u, float* v, float* d) {
+  float xc = fmaf(cam->R[2], p[2], fmaf(cam->R[1], p[1], fmaf(cam->R[0], p[0], cam->t[0])));
+  float yc = fmaf(cam->R[5], p[2], fmaf(cam->R[4], p[1], fmaf(cam->R[3], p[0], cam->t[1])));
+  float zc = fmaf(cam->R[8], p[2], fmaf(cam->R[7], p[1], fmaf(cam->R[6], p[0], cam->t[2])));
+  *d = zc;
+  if (!(zc > cam->near_plane && zc < cam->far_plane)) return 0;
+  float qx = xc / zc;
+  float qy = yc / zc;
+  *u = fmaf(cam->fx, qx, cam->cx);
+  *v = fmaf(cam->fy, qy, cam->cy);
+  return 1;
+}
+
+/* The four bilinear splats of a projected point (Eq. 6): pixel centers at
+ * (i + 1/2, j + 1/2); the 2x2 nearest centers are i0 = floor(u - 1/2) + {0,1}
+ * and j0 = floor(v - 1/2) + {0,1}; weight (1 - |u - u_i|)(1 - |v - v_j|).
+ * Writes pixel columns/rows and weights for the four corners (a + 2b order). */
+void oracle_splat_corners(double u, double v, int64_t* pi, int64_t* pj, double* w) {
+  double fu = u - 0.5, fv = v - 0.5;
+  double i0 = floor(fu), j0 = floor(fv);
+  for (int b = 0; b < 2; ++b)
+    for (int a = 0; a < 2; ++a) {
+      int k = a + 2 * b;
+      double uc = i0 + a + 0.5, vc = j0 + b + 0.5;
+      pi[k] = (int64_t)i0 + a;
+      pj[k] = (int64_t)j0 + b;
+      w[k] = (1.0 - fabs(u - uc)) * (1.0 - fabs(v - vc));
+    }
+}
+
+typedef struct {
+  float depth;
+  int32_t id;
+  int32_t corner;
+} frag_rec;
+
+static int frag_cmp(const void* pa, const void* pb) {
+  const frag_rec* a = (const frag_rec*)pa;
+  const frag_rec* b = (const frag_rec*)pb;
+  if (a->depth < b->depth) return -1;
+  if (a->depth > b->depth) return 1;
+  if (a->id < b->id) return -1;
+  if (a->id > b->id) return 1;
+  return 0;
+}
+
+typedef struct {
+  int64_t n_pix;
+  int64_t* start;   /* [n_pix + 1] */
+  frag_rec* frags;  /* sorted per pixel */
+  double* fu;       /* per point projected u, v (FP64 copies of the FP32 values) */
+  double* fv;
+  int8_t* visible;
+} frag_lists;
+
+static void free_lists(frag_lists* L) {
+  free(L->start); free(L->frags); free(L->fu); free(L->fv); free(L->visible);
+}
+
+/* Algorithm 1, ProjectAndCull + BilinearSplatting + per-pixel depth order. */
+static int build_lists(const oracle_camera* cam, const float* pos, int64_t n, frag_lists* L) {
+  int64_t W = cam->width, H = cam->height;
+  L->n_pix = W * H;
+  L->start = (int64_t*)calloc((size_t)(W * H + 1), sizeof(int64_t));
+  L->fu = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  L->fv = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  L->visible = (int8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+  L->frags = NULL;
+  if (!L->start || !L->fu || !L->fv || !L->visible) return ORACLE_ERR_NOMEM;
+  int64_t* count = L->start + 1;
+  for (int64_t p = 0; p < n; ++p) {
+    float u, v, d;
+    if (!oracle_project(cam, pos + 3 * p, &u, &v, &d)) continue;
+    L->visible[p] = 1;
+    L->fu[p] = (double)u;
+    L->fv[p] = (double)v;
+    if (!(L->fu[p] >= -0.5 && L->fu[p] < (double)W + 0.5 && L->fv[p] >= -0.5 && L->fv[p] < (double)H + 0.5)) {
+      L->visible[p] = 0;
+      continue;
+    }
+    int64_t pi[4], pj[4];
+    double w[4];
+    oracle_splat_corners(L->fu[p], L->fv[p], pi, pj, w);
+    for (int k = 0; k < 4; ++k)
+      if (pi[k] >= 0 && pi[k] < W && pj[k] >= 0 && pj[k] < H) count[pj[k] * W + pi[k]]++;
+  }
+  for (int64_t q = 0; q < W * H; ++q) L->start[q + 1] += L->start[q];
+  int64_t total = L->start[W * H];
+  L->frags = (frag_rec*)malloc(sizeof(frag_rec) * (size_t)(total > 0 ? total : 1));
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(W * H > 0 ? W * H : 1));
+  if (!L->frags || !fill) { free(fill); return ORACLE_ERR_NOMEM; }
+  memcpy(fill, L->start, sizeof(int64_t) * (size_t)(W * H));
+  for (int64_t p = 0; p < n; ++p) {
+    if (!L->visible[p]) continue;
+    float u, v, d;
+    oracle_project(cam, pos + 3 * p, &u, &v, &d);
+    int64_t pi[4], pj[4];
+    double w[4];
+    oracle_splat_corners(L->fu[p], L->fv[p], pi, pj, w);
+    for (int k = 0; k < 4; ++k)
+      if (pi[k] >= 0 && pi[k] < W && pj[k] >= 0 && pj[k] < H) {
+        frag_rec r = {d, (int32_t)p, k};
+        L->frags[fill[pj[k] * W + pi[k]]++] = r;
+      }
+  }
+  free(fill);
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t q = 0; q < W * H; ++q) {
+    int64_t m = L->start[q + 1] - L->start[q];
+    if (m > 1) qsort(L->frags + L->start[q], (size_t)m, sizeof(frag_rec), frag_cmp);
+  }
+  return ORACLE_OK;
+}
+
+typedef struct {
+  int32_t opacity_from_ch0; /* 0: opacity given per point; 1: alpha_h = 1 - exp(-exp(feat[:,0])) */
+  int32_t n_channels;
+  double t_min;
+  double alpha_max;
+  double ambiguity_rel;     /* relative band around t_min flagged as ambiguous */
+} oracle_raster_opts;
+
+/* Point opacity alpha_h (Sec. 3.3 activation in head mode). */
+static double point_alpha(const oracle_raster_opts* o, const double* opacity, const double* feat, int64_t p) {
+  if (o->opacity_from_ch0) return 1.0 - exp(-exp(feat[p * o->n_channels]));
+  return opacity[p];
+}
+
+/* Blended color vector of a point: its features, with channel 0 replaced
+ * by 1 in head mode (so image channel 0 carries the accumulated alpha). */
+static double point_color(const oracle_raster_opts* o, const double* feat, int64_t p, int c) {
+  if (o->opacity_from_ch0 && c == 0) return 1.0;
+  return feat[p * o->n_channels + c];
+}
+
+/* Forward: image[H,W,F], T_final[H,W], n_contrib[H,W], n_frags[H,W] (all
+ * fragments of the pixel), flags[H,W] bit 0 = stopping decision within the
+ * ambiguity band of t_min; abs_out[H,W,F] (optional) = sum |T alpha c|. */
+int oracle_raster_fwd(const oracle_camera* cam, const oracle_raster_opts* o, const float* pos,
+                      const double* opacity, const double* feat, int64_t n,
+                      double* image, double* T_final, int32_t* n_contrib, int32_t* n_frags,
+                      uint8_t* flags, double* abs_out) {
+  frag_lists L;
+  int st = build_lists(cam, pos, n, &L);
+  if (st != ORACLE_OK) { free_lists(&L); return st; }
+  int F = o->n_channels;
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t q = 0; q < L.n_pix; ++q) {
+    double* C = image + q * F;
+    for (int c = 0; c < F; ++c) C[c] = 0.0;
+    if (abs_out) for (int c = 0; c < F; ++c) abs_out[q * F + c] = 0.0;
+    double T = 1.0;
+    int32_t cnt = 0;
+    uint8_t flag = 0;
+    double band = o->ambiguity_rel * o->t_min;
+    for (int64_t k = L.start[q]; k < L.start[q + 1]; ++k) {
+      const frag_rec* r = &L.frags[k];
+      int64_t pi[4], pj[4];
+      double w[4];
+      oracle_splat_corners(L.fu[r->id], L.fv[r->id], pi, pj, w);
+      double a = point_alpha(o, opacity, feat, r->id) * w[r->corner];
+      if (a > o->alpha_max) a = o->alpha_max;
+      for (int c = 0; c < F; ++c) {
+        double term = T * a * point_color(o, feat, r->id, c);
+        C[c] += term;
+        if (abs_out) abs_out[q * F + c] += fabs(term);
+      }
+      double Tn = T * (1.0 - a);
+      ++cnt;
+      if (fabs(Tn - o->t_min) <= band) flag |= 1;
+      T = Tn;
+      if (T < o->t_min) break;
+    }
+    T_final[q] = T;
+    n_contrib[q] = cnt;
+    if (n_frags) n_frags[q] = (int32_t)(L.start[q + 1] - L.start[q]);
+    if (flags) flags[q] = flag;
+  }
+  free_lists(&L);
+  return ORACLE_OK;
+}
+
+/* Backward of oracle_raster_fwd for upstream gradient d_image[H,W,F].
+ * Per pixel with blended fragments k = 0..n-1, T_k = prod_{i<k} (1 - alpha_i):
+ *   dL/dc_k     = T_k alpha_k g
+ *   dL/dalpha_k = T_k (c_k . g) - sum_{j>k} [prod_{i<j, i!=k} (1 - alpha_i)] alpha_j (c_j . g)
+ * (the second form is the derivative of T_j with respect to alpha_k written
+ * without division).  Per point: d_feat = sum of its dL/dc_k; d_alpha_h =
+ * sum of w_k dL/dalpha_k over unclamped splats; in head mode d_feat[:,0] =
+ * d_alpha_h * exp(h0) * exp(-exp(h0)) and channel 0 of dL/dc is dropped.
+ * d_opacity (given mode) and d_feat are written (not accumulated);
+ * abs_feat (optional) receives sum |terms| of d_feat for the tolerance. */
+int oracle_raster_bwd(const oracle_camera* cam, const oracle_raster_opts* o, const float* pos,
+                      const double* opacity, const double* feat, int64_t n, const double* d_image,
+                      double* d_opacity, double* d_feat, double* abs_feat, double* abs_opacity) {
+  frag_lists L;
+  int st = build_lists(cam, pos, n, &L);
+  if (st != ORACLE_OK) { free_lists(&L); return st; }
+  int F = o->n_channels;
+  int64_t total = L.start[L.n_pix];
+  /* per-fragment scalars: a_k = T_k alpha_k, da_k = dL/dalpha_k, used flag */
+  double* fa = (double*)calloc((size_t)(total > 0 ? total : 1), sizeof(double));
+  double* fda = (double*)calloc((size_t)(total > 0 ? total : 1), sizeof(double));
+  double* fdaabs = (double*)calloc((size_t)(total > 0 ? total : 1), sizeof(double));
+  if (!fa || !fda || !fdaabs) { free(fa); free(fda); free(fdaabs); free_lists(&L); return ORACLE_ERR_NOMEM; }
+#pragma omp parallel
+  {
+    int64_t cap = 64;
+    double* al = (double*)malloc(sizeof(double) * (size_t)cap);
+    double* dot = (double*)malloc(sizeof(double) * (size_t)cap);
+    double* dotabs = (double*)malloc(sizeof(double) * (size_t)cap);
+#pragma omp for schedule(dynamic, 256)
+    for (int64_t q = 0; q < L.n_pix; ++q) {
+      int64_t b0 = L.start[q], m = L.start[q + 1] - L.start[q];
+      if (m == 0) continue;
+      if (m > cap) {
+        cap = m;
+        al = (double*)realloc(al, sizeof(double) * (size_t)cap);
+        dot = (double*)realloc(dot, sizeof(double) * (size_t)cap);
+        dotabs = (double*)realloc(dotabs, sizeof(double) * (size_t)cap);
+      }
+      const double* g = d_image + q * F;
+      /* forward replay to find the blended prefix */
+      double T = 1.0;
+      int64_t nb = 0;
+      for (int64_t k = 0; k < m; ++k) {
+        const frag_rec* r = &L.frags[b0 + k];
+        int64_t pi[4], pj[4];
+        double w[4];
+        oracle_splat_corners(L.fu[r->id], L.fv[r->id], pi, pj, w);
+        double a = point_alpha(o, opacity, feat, r->id) * w[r->corner];
+        if (a > o->alpha_max) a = o->alpha_max;
+        al[k] = a;
+        double s = 0.0, sa = 0.0;
+        for (int c = 0; c < F; ++c) {
+          double t = point_color(o, feat, r->id, c) * g[c];
+          s += t;
+          sa += fabs(t);
+        }
+        dot[k] = s;
+        dotabs[k] = sa;
+        ++nb;
+        T = T * (1.0 - a);
+        if (T < o->t_min) break;
+      }
+      for (int64_t k = 0; k < nb; ++k) {
+        double Tk = 1.0;
+        for (int64_t i = 0; i < k; ++i) Tk *= (1.0 - al[i]);
+        double da = Tk * dot[k];
+        double daabs = Tk * dotabs[k];
+        /* prod = prod_{i<j, i!=k} (1 - alpha_i), grown one factor per j */
+        double prod = Tk;
+        for (int64_t j = k + 1; j < nb; ++j) {
+          da -= prod * al[j] * dot[j];
+          daabs += prod * al[j] * dotabs[j];
+          prod *= (1.0 - al[j]);
+        }
+        fa[b0 + k] = Tk * al[k];
+        fda[b0 + k] = da;
+        fdaabs[b0 + k] = daabs;
+      }
+    }
+    free(al);
+    free(dot);
+    free(dotabs);
+  }
+  /* per-point accumulation, serial and in (pixel, depth) order */
+  double* dah = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* dahabs = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  if (!dah || !dahabs) { free(dah); free(dahabs); free(fa); free(fda); free(fdaabs); free_lists(&L); return ORACLE_ERR_NOMEM; }
+  for (int64_t p = 0; p < n * F; ++p) d_feat[p] = 0.0;
+  if (abs_feat) for (int64_t p = 0; p < n * F; ++p) abs_feat[p] = 0.0;
+  for (int64_t q = 0; q < L.n_pix; ++q) {
+    const double* g = d_image + q * F;
+    for (int64_t k = L.start[q]; k < L.start[q + 1]; ++k) {
+      const frag_rec* r = &L.frags[k];
+      if (fa[k] == 0.0 && fda[k] == 0.0) continue;
+      for (int c = 0; c < F; ++c) {
+        d_feat[(int64_t)r->id * F + c] += fa[k] * g[c];
+        if (abs_feat) abs_feat[(int64_t)r->id * F + c] += fabs(fa[k] * g[c]);
+      }
+      int64_t pi[4], pj[4];
+      double w[4];
+      oracle_splat_corners(L.fu[r->id], L.fv[r->id], pi, pj, w);
+      double ah = point_alpha(o, opacity, feat, r->id);
+      double dadah = (ah * w[r->corner] > o->alpha_max) ? 0.0 : w[r->corner];
+      dah[r->id] += dadah * fda[k];
+      dahabs[r->id] += fabs(dadah) * fdaabs[k];
+    }
+  }
+  for (int64_t p = 0; p < n; ++p) {
+    if (o->opacity_from_ch0) {
+      double h0 = feat[p * F];
+      double dh0 = exp(h0) * exp(-exp(h0));
+      d_feat[p * F] = dah[p] * dh0;
+      if (abs_feat) abs_feat[p * F] = dahabs[p] * dh0;
+    } else {
+      if (d_opacity) d_opacity[p] = dah[p];
+      if (abs_opacity) abs_opacity[p] = dahabs[p];
+    }
+  }
+  free(dah); free(dahabs); free(fa); free(fda); free(fdaabs);
+  free_lists(&L);
+  return ORACLE_OK;
+}
+
+/* Per-pixel sorted fragment lists, exposed for tests: writes the number of
+ * fragments per pixel (count[H*W]) and, if ids/corners are given, the point
+ * ids and corner indices in blending order (size = total). Returns total. */
+int64_t oracle_fragment_lists(const oracle_camera* cam, const float* pos, int64_t n,
+                              int64_t* count, int32_t* ids, int32_t* corners, float* depths) {
+  frag_lists L;
+  if (build_lists(cam, pos, n, &L) != ORACLE_OK) { free_lists(&L); return -1; }
+  for (int64_t q = 0; q < L.n_pix; ++q) count[q] = L.start[q + 1] - L.start[q];
+  int64_t total = L.start[L.n_pix];
+  for (int64_t k = 0; k < total; ++k) {
+    if (ids) ids[k] = L.frags[k].id;
+    if (corners) corners[k] = L.frags[k].corner;
+    if (depths) depths[k] = L.frags[k].depth;
+  }
+  free_lists(&L);
+  return total;
+}

@@ -1,0 +1,147 @@
+"""Pins of the oracle's sampling step (Sec. 3.2, multinomial sampling with
+replacement and a uniform position in the chosen leaf) against closed forms,
+statistics and brute force.  CPU only."""
+import numpy as np
+import pytest
+from scipy import stats
+
+from paper_2403_16862_gb300 import scenes
+
+
+def _tree(levels, centers, weights, root=1.0):
+    return scenes.Octree(centers=np.asarray(centers, np.float32), levels=np.asarray(levels, np.int32),
+                         weights=np.asarray(weights, np.float64), root_size=root)
+
+
+def test_cdf_quantisation_closed_form(oracle):
+    # q_i = rint(w_i / max w * 2^29); 2^29 / 3 = 178956970.666... -> 178956971
+    cdf, Q = oracle.build_cdf([1.0, 3.0])
+    assert cdf[0] == 178956971.0
+    assert cdf[1] == 178956971.0 + 2.0 ** 29
+    assert Q == cdf[1]
+    # exact integers: partial sums of many leaves stay exact in FP64
+    w = np.random.default_rng(3).lognormal(0, 1.5, size=1 << 16)
+    cdf, Q = oracle.build_cdf(w)
+    q = np.rint(w / w.max() * 2.0 ** 29).astype(np.int64)
+    assert np.array_equal(cdf.astype(np.int64), np.cumsum(q))
+
+
+def test_cdf_rejects_bad_weights(oracle):
+    for bad in ([0.0, 0.0], [1.0, -1.0], [1.0, np.nan], [np.inf, 1.0]):
+        with pytest.raises(oracle.OracleError):
+            oracle.build_cdf(bad)
+
+
+def test_search_thresholds(oracle):
+    # q = (1, 3): r = 0 draws leaf 0, r = 1, 2, 3 draw leaf 1
+    cdf = np.array([1.0, 4.0])
+    assert [oracle.search_cdf(cdf, r) for r in range(4)] == [0, 1, 1, 1]
+    # zero-weight leaves (equal consecutive cdf values) are never returned
+    cdf = np.array([0.0, 2.0, 2.0, 2.0, 5.0, 5.0])
+    got = [oracle.search_cdf(cdf, r) for r in range(5)]
+    assert got == [1, 1, 4, 4, 4]
+    # brute force: smallest i with cdf_i > r
+    rng = np.random.default_rng(0)
+    q = rng.integers(0, 4, size=50).astype(np.float64)
+    q[-1] = 1.0
+    cdf = np.cumsum(q)
+    for r in range(int(cdf[-1])):
+        assert oracle.search_cdf(cdf, r) == int(np.nonzero(cdf > r)[0][0])
+
+
+def test_scale_draw_exact(oracle):
+    Q = (1 << 53) - 12345
+    assert oracle.scale_draw(0, Q) == 0
+    assert oracle.scale_draw((1 << 53) - 1, Q) == Q - 1
+    assert oracle.scale_draw(1 << 52, Q) == Q // 2
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        b = int(rng.integers(0, 1 << 53, dtype=np.uint64))
+        q = int(rng.integers(1, 1 << 53, dtype=np.uint64))
+        assert oracle.scale_draw(b, q) == (b * q) >> 53
+
+
+def test_one_leaf_tree(oracle):
+    t = _tree([3], [[0.3125, 0.5625, 0.0625]], [0.7])
+    leaf, pos, counts = oracle.sample_octree(t, seed=5, view_id=2, n_samples=5000)
+    assert np.all(leaf == 0) and counts[0] == 5000
+    half = 0.5 * 2.0 ** -3
+    assert np.all(pos >= t.centers[0] - half) and np.all(pos < t.centers[0] + half)
+
+
+def test_zero_weight_leaves_never_drawn(oracle):
+    w = np.array([0.0, 1.0, 0.0, 2.0, 0.0])
+    d = oracle.draw_leaves(w, seed=11, view_id=0, n_samples=20000)
+    assert set(np.unique(d).tolist()) <= {1, 3}
+
+
+def test_leaf_histogram_matches_probabilities(oracle):
+    # chi^2 of 10^7 draws against q_i / Q (Sec. 3.2: sampling with replacement)
+    w = np.random.default_rng(7).lognormal(0, 1.5, size=64)
+    cdf, Q = oracle.build_cdf(w)
+    q = np.diff(np.concatenate([[0.0], cdf]))
+    n = 10_000_000
+    d = oracle.draw_leaves(w, seed=123, view_id=0, n_samples=n)
+    hist = np.bincount(d, minlength=64)
+    exp = n * q / Q
+    chi2, p = stats.chisquare(hist, exp)
+    assert p > 1e-4, (chi2, p)
+    # the empirical frequencies approach the weights (quantisation error < 2^-29 relative)
+    np.testing.assert_allclose(hist / n, w / w.sum(), atol=5e-4)
+
+
+def test_grouping_and_counts(oracle):
+    t = scenes.make_octree(2, 4096 + 7 * 50)
+    leaf, pos, counts = oracle.sample_octree(t, seed=9, view_id=3, n_samples=200000)
+    assert np.all(np.diff(leaf) >= 0), "samples are grouped by leaf in ascending order"
+    d = oracle.draw_leaves(t.weights, seed=9, view_id=3, n_samples=200000)
+    assert np.array_equal(np.bincount(d, minlength=t.n_leaves), counts)
+    assert np.array_equal(np.bincount(leaf, minlength=t.n_leaves), counts)
+
+
+def test_positions_inside_leaf_and_uniform(oracle):
+    t = scenes.make_octree(4, 4096 + 7 * 100)
+    leaf, pos, counts = oracle.sample_octree(t, seed=1, view_id=0, n_samples=400000)
+    edge = t.root_size * np.exp2(-t.levels[leaf].astype(np.float64))[:, None]
+    rel = (pos - t.centers[leaf].astype(np.float64)) / edge + 0.5
+    assert np.all(rel >= 0.0) and np.all(rel < 1.0), "half-open leaf extent"
+    for d in range(3):
+        ks = stats.kstest(rel[:, d], "uniform")
+        assert ks.pvalue > 1e-4, ks
+    # axes independent: correlation near zero
+    c = np.corrcoef(rel.T)
+    assert np.max(np.abs(c - np.eye(3))) < 0.01
+    # the FP64 positions are exact: the in-leaf offset is a 24-bit dyadic
+    # fraction of the (power-of-two) leaf edge
+    assert np.array_equal(np.rint(rel * 2.0 ** 24), rel * 2.0 ** 24)
+
+
+def test_views_and_seeds_give_different_streams(oracle):
+    w = np.ones(1000)
+    a = oracle.draw_leaves(w, 1, 0, 10000)
+    b = oracle.draw_leaves(w, 1, 1, 10000)
+    c = oracle.draw_leaves(w, 2, 0, 10000)
+    assert np.mean(a == b) < 0.01 and np.mean(a == c) < 0.01
+    assert np.array_equal(a, oracle.draw_leaves(w, 1, 0, 10000)), "deterministic"
+
+
+def test_philox_statistics(oracle):
+    # uniformity of every output word (top byte chi^2) and avalanche on
+    # single counter-bit flips: properties the generator is published with
+    out = oracle.philox_stream(seed=0x1234ABCD5678EF01, n=1 << 18)
+    for wi in range(4):
+        hist = np.bincount((out[:, wi] >> 24).astype(np.int64), minlength=256)
+        _, p = stats.chisquare(hist)
+        assert p > 1e-4
+    rng = np.random.default_rng(0)
+    flips = []
+    for _ in range(400):
+        key = rng.integers(0, 2 ** 32, size=2, dtype=np.uint64).astype(np.uint32)
+        ctr = rng.integers(0, 2 ** 32, size=4, dtype=np.uint64).astype(np.uint32)
+        base = oracle.philox4x32_10(key, ctr)
+        bit = int(rng.integers(0, 128))
+        c2 = ctr.copy()
+        c2[bit // 32] ^= np.uint32(1 << (bit % 32))
+        o2 = oracle.philox4x32_10(key, c2)
+        flips.append(sum(bin(int(x) ^ int(y)).count("1") for x, y in zip(base, o2)))
+    assert 60 < np.mean(flips) < 68, np.mean(flips)
