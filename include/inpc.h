@@ -1,0 +1,231 @@
+/*
+ * inpc.h -- C ABI of the GB300 (sm_103a) hot path of INPC's implicit point
+ * cloud: octree point sampling, multi-resolution hash-grid query, and the
+ * differentiable bilinear point rasterizer (forward and backward).
+ *
+ * Conventions for every entry point
+ *   - All array pointers are DEVICE pointers owned by the caller, unless a
+ *     parameter says otherwise.  Nothing here allocates device memory: work
+ *     buffers are caller-provided ("workspace"), sized by the matching
+ *     *_workspace_size query, aligned to 256 bytes.
+ *   - Every compute call is asynchronous on the caller's stream (a
+ *     cudaStream_t passed as inpc_stream_t; NULL = legacy default stream)
+ *     and returns once its kernels are enqueued.  Host-detectable errors
+ *     (null pointers, bad sizes, misalignment, unsupported options) return a
+ *     non-zero inpc_status before anything is enqueued; a failed launch
+ *     returns INPC_ERR_CUDA.  Neither aborts nor traps; inpc_last_error()
+ *     gives a thread-local message for the last failure.
+ *   - Problems that only the device can see (for example a negative or NaN
+ *     leaf weight) set bits in a status word at the start of the workspace
+ *     instead of faulting; read it with inpc_read_device_status().
+ *   - Arrays are dense, row-major, with no padding between rows.
+ */
+#ifndef INPC_H
+#define INPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* inpc_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+  INPC_OK = 0,
+  INPC_ERR_INVALID_ARG = 1,  /* null pointer, bad size, misaligned buffer, workspace too small */
+  INPC_ERR_CUDA = 2,         /* a CUDA runtime call or kernel launch failed */
+  INPC_ERR_CAPACITY = 3,     /* a problem size exceeds a documented limit */
+  INPC_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+  INPC_ERR_UNSUPPORTED = 5   /* an option combination without a kernel */
+} inpc_status;
+
+/* Device status bits (inpc_read_device_status). */
+#define INPC_DEV_BAD_WEIGHT 0x1u   /* a leaf weight was negative, NaN or infinite */
+#define INPC_DEV_NO_WEIGHT 0x2u    /* no leaf weight was positive */
+
+typedef enum { INPC_F32 = 0, INPC_BF16 = 1 } inpc_dtype;
+
+/* Thread-local description of the last error returned on this thread. */
+const char* inpc_last_error(void);
+/* Library version string. */
+const char* inpc_version(void);
+/* Number of kernels this library has launched in this process (all devices,
+ * all threads); a diagnostic for benchmarks.  Memset/memcpy are not counted. */
+uint64_t inpc_kernel_launches(void);
+/* Copies the device status word at the start of `workspace` (any workspace
+ * of this library) to *status_out after synchronising `stream`. */
+inpc_status inpc_read_device_status(const void* workspace, inpc_stream_t stream, uint32_t* status_out);
+
+/* ======================================================================== */
+/* (a) Octree point sampling                                                */
+/* ======================================================================== */
+/* Sparse point-probability octree (Sec. 3.1; leaf arrays of App. A.4):
+ *   centers  float32 [n_leaves, 3]  world-space leaf centers
+ *   levels   int32   [n_leaves]     subdivision level l_i; edge root_size * 2^-l
+ *   weights  float64 [n_leaves]     non-negative sampling weights p_i
+ * n_leaves must be in [1, 2^24] (the paper's 256^3 leaf cap, Sec. 3.1). */
+typedef struct {
+  const float* centers;
+  const int32_t* levels;
+  const double* weights;
+  float root_size;
+  int64_t n_leaves;
+} inpc_octree;
+
+inpc_status inpc_sample_workspace_size(int64_t n_leaves, int64_t n_samples, size_t* bytes);
+
+/* Multinomial sampling with replacement over the leaves, then a uniform
+ * position inside each chosen leaf (Sec. 3.2, "Viewpoint-Specific Sampling",
+ * the sampling and positioning steps).
+ *
+ * Definition (integer-exact; bit-identical on any conforming implementation):
+ *   q_i   = rint(w_i / max_j w_j * 2^29)      (FP64, round half to even)
+ *   cdf_i = q_0 + ... + q_i,  Q = cdf_{L-1}   (exact integers held in FP64)
+ *   draw s in [0, n_samples): (r0..r3) = Philox4x32-10(key = (seed lo, seed hi),
+ *         counter = (s lo, s hi, view_id, 0)); b = (r1 & 0x1FFFFF) << 32 | r0;
+ *         leaf(s) = min{ i : cdf_i > floor(b * Q / 2^53) }
+ *   count_i = #{ s : leaf(s) = i }
+ *   output slot k in [0, n_samples) holds leaf i for
+ *         count_0 + .. + count_{i-1} <= k < count_0 + .. + count_i
+ *         (samples grouped by leaf, ascending), and position
+ *         pos_k = fl32(c_i + (u - 1/2) * root_size * 2^-l_i),
+ *         u_d = (r_d >> 8) * 2^-24 from Philox(counter = (k lo, k hi, view_id, 1)),
+ *         rounded once to FP32.
+ * Outputs:
+ *   leaf_idx_out     int32   [n_samples]
+ *   pos_out          float32 [n_samples, 3]
+ *   leaf_counts_out  int32   [n_leaves], optional (NULL to skip)
+ * n_samples in [0, 2^31 - 1].  Bad weights set INPC_DEV_BAD_WEIGHT /
+ * INPC_DEV_NO_WEIGHT in the workspace status; the outputs are then undefined
+ * but every write stays in bounds. */
+inpc_status inpc_sample_octree(const inpc_octree* tree, uint64_t seed, uint32_t view_id, int64_t n_samples,
+                               int32_t* leaf_idx_out, float* pos_out, int32_t* leaf_counts_out,
+                               void* workspace, size_t workspace_bytes, inpc_stream_t stream);
+
+/* ======================================================================== */
+/* (b) Multi-resolution hash-grid query                                     */
+/* ======================================================================== */
+/* Grid description (Sec. 3.3; configuration space of Listing 1, App. A.5).
+ *   n_levels    1..32
+ *   n_feats     features per level; 4 is the supported value
+ *   log2_T      per-level entry budget T = 2^log2_T, 4 <= log2_T <= 24
+ *   res[l]      grid resolution N_l >= 1 of level l (host integers)
+ *   table_dtype INPC_F32 or INPC_BF16 (dtype of the parameter table)
+ *   out_dtype   INPC_F32 or INPC_BF16 (dtype of the query output h)
+ * Table layout: level-major; level l has E_l = min(T, (N_l+1)^3) rows of
+ * n_feats values; level l is stored densely iff (N_l+1)^3 <= T (row =
+ * x + y (N_l+1) + z (N_l+1)^2), otherwise through the spatial hash
+ * row = (x * 1 ^ y * 2654435761 ^ z * 805459861) mod T (uint32 arithmetic). */
+typedef struct {
+  int32_t n_levels;
+  int32_t n_feats;
+  int32_t log2_T;
+  int32_t res[32];
+  int32_t table_dtype;
+  int32_t out_dtype;
+} inpc_hashgrid_desc;
+
+/* Total table rows (sum of E_l). */
+inpc_status inpc_hashgrid_n_entries(const inpc_hashgrid_desc* g, int64_t* n_entries);
+
+/* h[p, l * n_feats + f] = sum over the 8 corners of the level-l cell holding
+ * x = clamp(pos[p], 0, 1) of the trilinear weight times table[row, f]
+ * (cell = min(floor(x N_l), N_l - 1) per axis; the fraction x N_l - cell is
+ * formed exactly).  pos: float32 [n, 3]; table: [n_entries, n_feats] of
+ * table_dtype; h_out: [n, n_levels * n_feats] of out_dtype.  Arithmetic is
+ * FP32.  n in [0, 2^31 - 1]. */
+inpc_status inpc_query_hashgrid(const inpc_hashgrid_desc* g, const void* table, const float* pos, int64_t n,
+                                void* h_out, inpc_stream_t stream);
+
+/* Adjoint of inpc_query_hashgrid: grad_table[row, f] += weight * dh[p, l * n_feats + f]
+ * for every point, level and corner.  dh: float32 [n, n_levels * n_feats];
+ * grad_table: float32 [n_entries, n_feats], accumulated (not cleared), FP32
+ * even for BF16 tables.  Summation order is unspecified (atomic adds). */
+inpc_status inpc_query_hashgrid_bwd(const inpc_hashgrid_desc* g, const float* pos, const float* dh, int64_t n,
+                                    float* grad_table, inpc_stream_t stream);
+
+/* ======================================================================== */
+/* (c) Differentiable bilinear point rasterizer                             */
+/* ======================================================================== */
+/* Pinhole camera (Eq. 5): x_c = R x_w + t (R row-major), then
+ *   u = fx * (x_c / z_c) + cx,  v = fy * (y_c / z_c) + cy,  depth d = z_c,
+ * evaluated in FP32 in exactly this order: each camera coordinate is
+ * fma(R[3r+2], z, fma(R[3r+1], y, fma(R[3r], x, t[r]))), the quotient is
+ * IEEE-rounded, and u, v are fma(fx, x_c / z_c, cx).  Points with
+ * d <= near_plane or d >= far_plane (or NaN) are culled.  Pixel (i, j)
+ * covers [i, i+1) x [j, j+1), center (i + 0.5, j + 0.5). */
+typedef struct {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float near_plane, far_plane;
+} inpc_camera;
+
+typedef enum {
+  INPC_OPACITY_GIVEN = 0,    /* alpha_h = opacity[p] */
+  INPC_OPACITY_FROM_CH0 = 1  /* alpha_h = 1 - exp(-exp(feat[p, 0])) (Sec. 3.3 activation);
+                                the blended color is (1, feat[p, 1:]) */
+} inpc_opacity_mode;
+
+/*   opacity_mode  inpc_opacity_mode
+ *   n_channels    F, 1..128 (F/4 <= 32 when F % 4 == 0, else F <= 32)
+ *   feat_dtype    INPC_F32 (INPC_BF16 reserved)
+ *   image_dtype   INPC_F32 (INPC_BF16 reserved)
+ *   t_min         blending stops after the fragment that takes T below it (1e-4)
+ *   alpha_max     splat opacity clamp, alpha = min(alpha_h w, alpha_max), < 1 (0.99)
+ *   tile_w/tile_h screen tile in pixels, tile_w * tile_h <= 256; 0 = default 16 x 16 */
+typedef struct {
+  int32_t opacity_mode;
+  int32_t n_channels;
+  int32_t feat_dtype;
+  int32_t image_dtype;
+  float t_min;
+  float alpha_max;
+  int32_t tile_w;
+  int32_t tile_h;
+} inpc_raster_opts;
+
+inpc_status inpc_rasterize_workspace_size(const inpc_camera* cam, const inpc_raster_opts* opts, int64_t n,
+                                          size_t* bytes);
+
+/* Forward (Algorithm 1: ProjectAndCull, BilinearSplatting, order, blend).
+ * Each visible point p splats to the 2x2 pixels whose centers are nearest to
+ * (u, v) (i0 = floor(u - 1/2), j0 = floor(v - 1/2)) with alpha =
+ * min(alpha_h (1 - |u - u_i|)(1 - |v - v_j|), alpha_max) (Eq. 6); off-image
+ * pixels are dropped.  Per pixel, fragments are ordered by (FP32 depth,
+ * point index) ascending and blended front to back (Eq. 1): C += T alpha c,
+ * T *= 1 - alpha, stopping after the fragment that takes T below t_min.
+ *   pos      float32 [n, 3]
+ *   opacity  float32 [n] (INPC_OPACITY_GIVEN only; NULL otherwise)
+ *   feat     [n, F] of feat_dtype
+ *   image    [H, W, F] of image_dtype;  T_final float32 [H, W];
+ *   n_contrib int32 [H, W] (fragments blended per pixel)
+ * The workspace must stay untouched until the matching inpc_rasterize_bwd.
+ * n in [0, 2^25] (point indices are packed into 25 bits of the sort key). */
+inpc_status inpc_rasterize_fwd(const inpc_camera* cam, const inpc_raster_opts* opts, const float* pos,
+                               const float* opacity, const void* feat, int64_t n, void* image, float* T_final,
+                               int32_t* n_contrib, void* workspace, size_t workspace_bytes, inpc_stream_t stream);
+
+/* Backward of inpc_rasterize_fwd (App. A.6) for upstream d_image [H, W, F]
+ * (float32).  Per pixel the blended fragments are revisited back to front,
+ * recovering T_k = T_{k+1} / (1 - alpha_k) from T_final (no per-fragment
+ * storage).  Writes (does not accumulate):
+ *   d_feat     float32 [n, F]: sum of the point's splat gradients T_k alpha_k g;
+ *              in FROM_CH0 mode column 0 is d alpha_h * exp(h0) exp(-exp(h0))
+ *   d_opacity  float32 [n] (GIVEN mode; may be NULL in FROM_CH0 mode):
+ *              sum over splats of w_k dL/dalpha_k (0 where alpha was clamped)
+ * Culled points get zero rows.  Inputs must be those of the forward call,
+ * with its T_final, n_contrib and unmodified workspace. */
+inpc_status inpc_rasterize_bwd(const inpc_camera* cam, const inpc_raster_opts* opts, const float* pos,
+                               const float* opacity, const void* feat, int64_t n, const float* T_final,
+                               const int32_t* n_contrib, const float* d_image, float* d_opacity, float* d_feat,
+                               void* workspace, size_t workspace_bytes, inpc_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* INPC_H */

@@ -1,0 +1,171 @@
+"""ctypes binding of the C ABI in ``include/inpc.h`` (argument marshalling
+only; every computation runs in the CUDA library).
+
+Loading fails loudly when ``_lib/libinpc.so`` has not been built: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libinpc.so")
+
+INPC_OK = 0
+INPC_ERR_INVALID_ARG = 1
+INPC_ERR_CUDA = 2
+INPC_ERR_CAPACITY = 3
+INPC_ERR_TIMEOUT = 4
+INPC_ERR_UNSUPPORTED = 5
+STATUS_NAMES = {0: "INPC_OK", 1: "INPC_ERR_INVALID_ARG", 2: "INPC_ERR_CUDA", 3: "INPC_ERR_CAPACITY",
+                4: "INPC_ERR_TIMEOUT", 5: "INPC_ERR_UNSUPPORTED"}
+
+INPC_DEV_BAD_WEIGHT = 0x1
+INPC_DEV_NO_WEIGHT = 0x2
+
+INPC_F32 = 0
+INPC_BF16 = 1
+INPC_OPACITY_GIVEN = 0
+INPC_OPACITY_FROM_CH0 = 1
+
+# Every symbol the header declares; tests check the library exports them.
+DECLARED = [
+    "inpc_last_error", "inpc_version", "inpc_kernel_launches", "inpc_read_device_status",
+    "inpc_sample_workspace_size", "inpc_sample_octree",
+    "inpc_hashgrid_n_entries", "inpc_query_hashgrid", "inpc_query_hashgrid_bwd",
+    "inpc_rasterize_workspace_size", "inpc_rasterize_fwd", "inpc_rasterize_bwd",
+]
+
+
+class InpcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class InpcOctree(C.Structure):
+    _fields_ = [("centers", C.c_void_p), ("levels", C.c_void_p), ("weights", C.c_void_p),
+                ("root_size", C.c_float), ("n_leaves", C.c_int64)]
+
+
+class InpcHashgridDesc(C.Structure):
+    _fields_ = [("n_levels", C.c_int32), ("n_feats", C.c_int32), ("log2_T", C.c_int32),
+                ("res", C.c_int32 * 32), ("table_dtype", C.c_int32), ("out_dtype", C.c_int32)]
+
+
+class InpcCamera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("near_plane", C.c_float), ("far_plane", C.c_float)]
+
+
+class InpcRasterOpts(C.Structure):
+    _fields_ = [("opacity_mode", C.c_int32), ("n_channels", C.c_int32), ("feat_dtype", C.c_int32),
+                ("image_dtype", C.c_int32), ("t_min", C.c_float), ("alpha_max", C.c_float),
+                ("tile_w", C.c_int32), ("tile_h", C.c_int32)]
+
+
+_P = C.c_void_p
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libinpc.so (built by ``paper_2403_16862_gb300.build.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError("libinpc.so is not built (%s); run paper_2403_16862_gb300.build.build() "
+                              "or __graft_entry__.build() first" % path)
+        L = C.CDLL(path)
+        L.inpc_last_error.restype = C.c_char_p
+        L.inpc_version.restype = C.c_char_p
+        L.inpc_kernel_launches.restype = C.c_uint64
+        L.inpc_read_device_status.argtypes = [_P, _P, C.POINTER(C.c_uint32)]
+        L.inpc_sample_workspace_size.argtypes = [C.c_int64, C.c_int64, C.POINTER(C.c_size_t)]
+        L.inpc_sample_octree.argtypes = [C.POINTER(InpcOctree), C.c_uint64, C.c_uint32, C.c_int64, _P, _P, _P, _P,
+                                         C.c_size_t, _P]
+        L.inpc_hashgrid_n_entries.argtypes = [C.POINTER(InpcHashgridDesc), C.POINTER(C.c_int64)]
+        L.inpc_query_hashgrid.argtypes = [C.POINTER(InpcHashgridDesc), _P, _P, C.c_int64, _P, _P]
+        L.inpc_query_hashgrid_bwd.argtypes = [C.POINTER(InpcHashgridDesc), _P, _P, C.c_int64, _P, _P]
+        L.inpc_rasterize_workspace_size.argtypes = [C.POINTER(InpcCamera), C.POINTER(InpcRasterOpts), C.c_int64,
+                                                    C.POINTER(C.c_size_t)]
+        L.inpc_rasterize_fwd.argtypes = [C.POINTER(InpcCamera), C.POINTER(InpcRasterOpts), _P, _P, _P, C.c_int64,
+                                         _P, _P, _P, _P, C.c_size_t, _P]
+        L.inpc_rasterize_bwd.argtypes = [C.POINTER(InpcCamera), C.POINTER(InpcRasterOpts), _P, _P, _P, C.c_int64,
+                                         _P, _P, _P, _P, _P, _P, C.c_size_t, _P]
+        for name in DECLARED:
+            if name not in ("inpc_last_error", "inpc_version", "inpc_kernel_launches"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+        return L
+
+
+def check(status: int):
+    if status != INPC_OK:
+        msg = load().inpc_last_error()
+        raise InpcError(status, msg.decode() if msg else "")
+
+
+def version() -> str:
+    return load().inpc_version().decode()
+
+
+def inpc_kernel_launches() -> int:
+    return int(load().inpc_kernel_launches())
+
+
+# --------------------------------------------------- same names as the ABI ---
+def inpc_read_device_status(workspace: int, stream: int) -> int:
+    out = C.c_uint32(0)
+    check(load().inpc_read_device_status(workspace, stream, C.byref(out)))
+    return int(out.value)
+
+
+def inpc_sample_workspace_size(n_leaves: int, n_samples: int) -> int:
+    out = C.c_size_t(0)
+    check(load().inpc_sample_workspace_size(n_leaves, n_samples, C.byref(out)))
+    return int(out.value)
+
+
+def inpc_sample_octree(tree: InpcOctree, seed: int, view_id: int, n_samples: int, leaf_idx_out: int,
+                       pos_out: int, leaf_counts_out, workspace: int, workspace_bytes: int, stream: int):
+    check(load().inpc_sample_octree(C.byref(tree), C.c_uint64(seed), C.c_uint32(view_id), n_samples, leaf_idx_out,
+                                    pos_out, leaf_counts_out, workspace, workspace_bytes, stream))
+
+
+def inpc_hashgrid_n_entries(desc: InpcHashgridDesc) -> int:
+    out = C.c_int64(0)
+    check(load().inpc_hashgrid_n_entries(C.byref(desc), C.byref(out)))
+    return int(out.value)
+
+
+def inpc_query_hashgrid(desc: InpcHashgridDesc, table: int, pos: int, n: int, h_out: int, stream: int):
+    check(load().inpc_query_hashgrid(C.byref(desc), table, pos, n, h_out, stream))
+
+
+def inpc_query_hashgrid_bwd(desc: InpcHashgridDesc, pos: int, dh: int, n: int, grad_table: int, stream: int):
+    check(load().inpc_query_hashgrid_bwd(C.byref(desc), pos, dh, n, grad_table, stream))
+
+
+def inpc_rasterize_workspace_size(cam: InpcCamera, opts: InpcRasterOpts, n: int) -> int:
+    out = C.c_size_t(0)
+    check(load().inpc_rasterize_workspace_size(C.byref(cam), C.byref(opts), n, C.byref(out)))
+    return int(out.value)
+
+
+def inpc_rasterize_fwd(cam: InpcCamera, opts: InpcRasterOpts, pos: int, opacity, feat: int, n: int, image: int,
+                       T_final: int, n_contrib: int, workspace: int, workspace_bytes: int, stream: int):
+    check(load().inpc_rasterize_fwd(C.byref(cam), C.byref(opts), pos, opacity, feat, n, image, T_final, n_contrib,
+                                    workspace, workspace_bytes, stream))
+
+
+def inpc_rasterize_bwd(cam: InpcCamera, opts: InpcRasterOpts, pos: int, opacity, feat: int, n: int, T_final: int,
+                       n_contrib: int, d_image: int, d_opacity, d_feat: int, workspace: int, workspace_bytes: int,
+                       stream: int):
+    check(load().inpc_rasterize_bwd(C.byref(cam), C.byref(opts), pos, opacity, feat, n, T_final, n_contrib, d_image,
+                                    d_opacity, d_feat, workspace, workspace_bytes, stream))

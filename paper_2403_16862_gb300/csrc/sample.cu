@@ -1,0 +1,350 @@
+// sample.cu -- octree point sampling (Sec. 3.2): exact quantised FP64 CDF,
+// Philox4x32-10 draws with a two-level CDF search, per-leaf counts, and
+// leaf-grouped output slots with uniform in-leaf positions.
+//
+// Kernel sequence per call (one stream, no host synchronisation):
+//   k_wmax        max weight + validation (atomicMax on the FP64 bit pattern)
+//   k_scan_local  per-block inclusive scan of q_i = rint(w_i / wmax * 2^29)
+//   k_scan_tops   exclusive scan of the block totals (one CTA)
+//   k_scan_add    add block offsets -> cdf (exact integers in FP64)
+//   k_draw_count  draws -> leaf, per-CTA shared-memory histogram -> counts
+//   k_scan_*      exclusive scan of counts -> first output slot of each leaf
+//   k_place       slot -> leaf (two-level search), Philox position
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace inpc {
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanBlock = kScanThreads * kScanItems;  // 2048 items per CTA
+constexpr int kCoarse = 2048;                          // coarse search table entries (shared memory)
+constexpr int kDrawThreads = 256;
+constexpr int kDrawPerThread = 8;
+constexpr int kDrawPerCta = kDrawThreads * kDrawPerThread;
+constexpr int kHashSlots = 4096;                       // per-CTA leaf histogram (open addressing)
+
+struct SampleWs {
+  uint32_t* status;          // header word 0
+  unsigned long long* wmax;  // header word 1 (FP64 bit pattern)
+  double* cdf;               // [L]
+  double* cdf_tops;          // [nb]
+  uint32_t* counts;          // [L]
+  uint32_t* starts;          // [L]
+  uint32_t* count_tops;      // [nb]
+  size_t bytes;
+};
+
+SampleWs carve(void* base, int64_t L) {
+  Carver c(base);
+  SampleWs w;
+  w.status = reinterpret_cast<uint32_t*>(base);
+  w.wmax = base ? reinterpret_cast<unsigned long long*>(static_cast<char*>(base) + 8) : nullptr;
+  const int64_t nb = ceil_div(L, kScanBlock);
+  w.cdf = c.take<double>(L);
+  w.cdf_tops = c.take<double>(nb);
+  w.counts = c.take<uint32_t>(L);
+  w.starts = c.take<uint32_t>(L);
+  w.count_tops = c.take<uint32_t>(nb);
+  w.bytes = c.bytes();
+  return w;
+}
+
+__global__ void k_wmax(const double* __restrict__ w, int64_t L, unsigned long long* wmax, uint32_t* status) {
+  double m = 0.0;
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = w[i];
+    if (!(x >= 0.0) || isinf(x)) bad = true;
+    else m = fmax(m, x);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_status(status, INPC_DEV_BAD_WEIGHT);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(wmax, (unsigned long long)__double_as_longlong(m));
+}
+
+// Loaders for the block scan: quantised weights, or plain counts.
+struct QuantLoad {
+  const double* w;
+  const unsigned long long* wmax;
+  __device__ double operator()(int64_t i) const {
+    const double m = __longlong_as_double((long long)*wmax);
+    if (!(m > 0.0)) return 0.0;
+    const double x = w[i];
+    if (!(x >= 0.0) || isinf(x)) return 0.0;
+    return rint(ldexp(__ddiv_rn(x, m), 29));
+  }
+};
+
+struct CountLoad {
+  const uint32_t* c;
+  __device__ uint32_t operator()(int64_t i) const { return c[i]; }
+};
+
+template <class T>
+__device__ T block_exclusive_scan(T v, T* warp_sums, T* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const T n = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += n;
+  }
+  if (lane == 31) warp_sums[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    T s = lane < nw ? warp_sums[lane] : T(0);
+    T si = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      const T n = __shfl_up_sync(0xffffffffu, si, o);
+      if (lane >= o) si += n;
+    }
+    if (lane < nw) warp_sums[lane] = si - s;
+    if (lane == nw - 1) *total = si;
+  }
+  __syncthreads();
+  const T r = warp_sums[wid] + incl - v;
+  __syncthreads();
+  return r;
+}
+
+// Per-block scan (inclusive or exclusive) of loader values into out[],
+// block totals into tops[].
+template <class T, class Load, bool kInclusive>
+__global__ void __launch_bounds__(kScanThreads) k_scan_local(Load ld, int64_t L, T* __restrict__ out,
+                                                             T* __restrict__ tops) {
+  __shared__ T warp_sums[32];
+  __shared__ T total;
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+  T v[kScanItems];
+  T run = T(0);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (base + k < L) ? ld(base + k) : T(0);
+    run += v[k];
+  }
+  const T pre = block_exclusive_scan<T>(run, warp_sums, &total);
+  T acc = pre;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (kInclusive) acc += v[k];
+    if (base + k < L) out[base + k] = acc;
+    if (!kInclusive) acc += v[k];
+  }
+  if (threadIdx.x == 0) tops[blockIdx.x] = total;
+}
+
+// Exclusive scan of the (at most kScanBlock * kScanBlock / kScanBlock) block totals in one CTA.
+template <class T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_tops(T* tops, int64_t nb) {
+  __shared__ T warp_sums[32];
+  __shared__ T total;
+  T carry = T(0);
+  for (int64_t b0 = 0; b0 < nb; b0 += kScanThreads) {
+    const int64_t i = b0 + threadIdx.x;
+    const T v = i < nb ? tops[i] : T(0);
+    const T ex = block_exclusive_scan<T>(v, warp_sums, &total);
+    if (i < nb) tops[i] = carry + ex;
+    carry += total;
+    __syncthreads();
+  }
+}
+
+template <class T>
+__global__ void k_scan_add(T* __restrict__ out, const T* __restrict__ tops, int64_t L) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < L) out[i] += tops[i / kScanBlock];
+}
+
+template <class T, class Load, bool kInclusive>
+inpc_status scan(Load ld, int64_t L, T* out, T* tops, cudaStream_t s) {
+  const int64_t nb = ceil_div(L, kScanBlock);
+  k_scan_local<T, Load, kInclusive><<<(unsigned)nb, kScanThreads, 0, s>>>(ld, L, out, tops);
+  k_scan_tops<T><<<1, kScanThreads, 0, s>>>(tops, nb);
+  if (nb > 1) k_scan_add<T><<<(unsigned)ceil_div(L, 256), 256, 0, s>>>(out, tops, L);
+  return check_launch("sample scan", nb > 1 ? 3 : 2);
+}
+
+// Two-level search tables: the last element of every stride-sized block
+// sits in shared memory, the rest is searched in global memory (L2).
+template <class T>
+__device__ __forceinline__ void load_coarse(const T* __restrict__ arr, int64_t L, int stride_log2, T* coarse,
+                                            int& n_coarse) {
+  n_coarse = (int)ceil_div(L, (int64_t)1 << stride_log2);
+  for (int j = threadIdx.x; j < n_coarse; j += blockDim.x) {
+    int64_t e = (((int64_t)j + 1) << stride_log2) - 1;
+    coarse[j] = arr[e < L ? e : L - 1];
+  }
+  __syncthreads();
+}
+
+// Smallest i with arr[i] > key (arr non-decreasing); L when none.
+template <class T>
+__device__ __forceinline__ int64_t upper_bound2(const T* __restrict__ arr, int64_t L, const T* coarse, int n_coarse,
+                                                int stride_log2, T key) {
+  int lo = 0, hi = n_coarse;  // first coarse block whose last element exceeds key
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (coarse[mid] > key) hi = mid; else lo = mid + 1;
+  }
+  if (lo == n_coarse) return L;
+  int64_t a = (int64_t)lo << stride_log2;
+  int64_t b = a + ((int64_t)1 << stride_log2) - 1;
+  if (b > L - 1) b = L - 1;
+  while (a < b) {  // arr[b] > key holds
+    const int64_t mid = (a + b) >> 1;
+    if (arr[mid] > key) b = mid; else a = mid + 1;
+  }
+  return a;
+}
+
+__device__ __forceinline__ uint32_t slot_hash(uint32_t k) {
+  k *= 0x9E3779B1u;
+  return k >> (32 - 12);  // kHashSlots = 4096
+}
+
+__global__ void __launch_bounds__(kDrawThreads) k_draw_count(const double* __restrict__ cdf, int64_t L,
+                                                             int stride_log2, int64_t n_draws, uint32_t k0,
+                                                             uint32_t k1, uint32_t view_id,
+                                                             uint32_t* __restrict__ counts) {
+  __shared__ double coarse[kCoarse];
+  __shared__ int keys[kHashSlots];
+  __shared__ uint32_t vals[kHashSlots];
+  int n_coarse;
+  for (int j = threadIdx.x; j < kHashSlots; j += blockDim.x) {
+    keys[j] = -1;
+    vals[j] = 0;
+  }
+  load_coarse<double>(cdf, L, stride_log2, coarse, n_coarse);
+  const double Q = cdf[L - 1];
+  const uint64_t Qi = (uint64_t)Q;
+  const int64_t base = (int64_t)blockIdx.x * kDrawPerCta;
+  for (int k = 0; k < kDrawPerThread; ++k) {
+    const int64_t s = base + (int64_t)k * kDrawThreads + threadIdx.x;
+    int leaf = -1;
+    if (s < n_draws) {
+      const U32x4 r = philox4x32_10((uint32_t)s, (uint32_t)((uint64_t)s >> 32), view_id, 0u, k0, k1);
+      const uint64_t b = ((uint64_t)(r.y & 0x1FFFFFu) << 32) | (uint64_t)r.x;
+      // floor(b * Q / 2^53) from the exact 106-bit product
+      const uint64_t lo = b * Qi;
+      const uint64_t hi = __umul64hi(b, Qi);
+      const uint64_t rr = (hi << 11) | (lo >> 53);
+      int64_t i = upper_bound2<double>(cdf, L, coarse, n_coarse, stride_log2, (double)rr);
+      if (i >= L) i = L - 1;  // only reachable when Q == 0 (flagged as a device status)
+      leaf = (int)i;
+    }
+    // warp pre-aggregation of equal leaves, then the shared-memory table
+    const unsigned peers = __match_any_sync(0xffffffffu, leaf);
+    const int lane = threadIdx.x & 31;
+    if (leaf >= 0 && lane == __ffs(peers) - 1) {
+      const uint32_t add = __popc(peers);
+      uint32_t h = slot_hash((uint32_t)leaf);
+      for (int probe = 0; probe < kHashSlots; ++probe) {
+        const int prev = atomicCAS(&keys[h], -1, leaf);
+        if (prev == -1 || prev == leaf) {
+          atomicAdd(&vals[h], add);
+          break;
+        }
+        h = (h + 1) & (kHashSlots - 1);
+      }
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < kHashSlots; j += blockDim.x)
+    if (keys[j] >= 0) atomicAdd(&counts[keys[j]], vals[j]);
+}
+
+__global__ void __launch_bounds__(256) k_place(const uint32_t* __restrict__ starts, int64_t L, int stride_log2,
+                                               int64_t n, uint32_t k0, uint32_t k1, uint32_t view_id,
+                                               const float* __restrict__ centers,
+                                               const int32_t* __restrict__ levels, float root_size,
+                                               int32_t* __restrict__ leaf_out, float* __restrict__ pos_out) {
+  __shared__ uint32_t coarse[kCoarse];
+  int n_coarse;
+  load_coarse<uint32_t>(starts, L, stride_log2, coarse, n_coarse);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    // leaf = (number of leaves whose first slot is <= k) - 1
+    int64_t leaf = upper_bound2<uint32_t>(starts, L, coarse, n_coarse, stride_log2, (uint32_t)k) - 1;
+    if (leaf < 0) leaf = 0;
+    const U32x4 r = philox4x32_10((uint32_t)k, (uint32_t)((uint64_t)k >> 32), view_id, 1u, k0, k1);
+    const float edge = ldexpf(root_size, -levels[leaf]);
+    const float u0 = __fsub_rn((float)(r.x >> 8) * 0x1p-24f, 0.5f);
+    const float u1 = __fsub_rn((float)(r.y >> 8) * 0x1p-24f, 0.5f);
+    const float u2 = __fsub_rn((float)(r.z >> 8) * 0x1p-24f, 0.5f);
+    leaf_out[k] = (int32_t)leaf;
+    pos_out[3 * k + 0] = __fmaf_rn(u0, edge, centers[3 * leaf + 0]);
+    pos_out[3 * k + 1] = __fmaf_rn(u1, edge, centers[3 * leaf + 1]);
+    pos_out[3 * k + 2] = __fmaf_rn(u2, edge, centers[3 * leaf + 2]);
+  }
+}
+
+__global__ void k_check_total(const double* cdf, int64_t L, uint32_t* status) {
+  if (threadIdx.x == 0 && !(cdf[L - 1] > 0.0)) raise_status(status, INPC_DEV_NO_WEIGHT);
+}
+
+int coarse_stride_log2(int64_t L) {
+  int s = 0;
+  while (ceil_div(L, (int64_t)1 << s) > kCoarse) ++s;
+  return s;
+}
+
+}  // namespace
+}  // namespace inpc
+
+using namespace inpc;
+
+extern "C" inpc_status inpc_sample_workspace_size(int64_t n_leaves, int64_t n_samples, size_t* bytes) {
+  if (!bytes) return fail(INPC_ERR_INVALID_ARG, "inpc_sample_workspace_size: bytes is null");
+  if (n_leaves < 1 || n_leaves > (int64_t(1) << 24))
+    return fail(INPC_ERR_CAPACITY, "n_leaves must be in [1, 2^24], got %lld", (long long)n_leaves);
+  if (n_samples < 0 || n_samples > INT32_MAX) return fail(INPC_ERR_CAPACITY, "n_samples out of range");
+  *bytes = carve(nullptr, n_leaves).bytes;
+  return INPC_OK;
+}
+
+extern "C" inpc_status inpc_sample_octree(const inpc_octree* tree, uint64_t seed, uint32_t view_id,
+                                          int64_t n_samples, int32_t* leaf_idx_out, float* pos_out,
+                                          int32_t* leaf_counts_out, void* workspace, size_t workspace_bytes,
+                                          inpc_stream_t stream) {
+  if (!tree) return fail(INPC_ERR_INVALID_ARG, "inpc_sample_octree: tree is null");
+  const int64_t L = tree->n_leaves;
+  size_t need = 0;
+  INPC_TRY(inpc_sample_workspace_size(L, n_samples, &need));
+  if (!tree->centers || !tree->levels || !tree->weights)
+    return fail(INPC_ERR_INVALID_ARG, "inpc_sample_octree: null octree array");
+  if (!workspace || workspace_bytes < need || !aligned(workspace, 256))
+    return fail(INPC_ERR_INVALID_ARG, "inpc_sample_octree: workspace null, unaligned or smaller than %zu bytes", need);
+  if (n_samples > 0 && (!leaf_idx_out || !pos_out))
+    return fail(INPC_ERR_INVALID_ARG, "inpc_sample_octree: null output");
+  if (!(tree->root_size > 0.0f)) return fail(INPC_ERR_INVALID_ARG, "root_size must be positive");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  SampleWs ws = carve(workspace, L);
+  INPC_CUDA(cudaMemsetAsync(workspace, 0, kHeaderBytes, s), "clear header");
+  INPC_CUDA(cudaMemsetAsync(ws.counts, 0, sizeof(uint32_t) * L, s), "clear counts");
+  const int sms = device_sm_count();
+  k_wmax<<<(unsigned)std::min<int64_t>(ceil_div(L, 256), sms * 4), 256, 0, s>>>(tree->weights, L, ws.wmax, ws.status);
+  INPC_TRY(check_launch("k_wmax"));
+  INPC_TRY((scan<double, QuantLoad, true>(QuantLoad{tree->weights, ws.wmax}, L, ws.cdf, ws.cdf_tops, s)));
+  k_check_total<<<1, 32, 0, s>>>(ws.cdf, L, ws.status);
+  INPC_TRY(check_launch("k_check_total"));
+  const int sl = coarse_stride_log2(L);
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  if (n_samples > 0) {
+    k_draw_count<<<(unsigned)ceil_div(n_samples, kDrawPerCta), kDrawThreads, 0, s>>>(ws.cdf, L, sl, n_samples, k0,
+                                                                                      k1, view_id, ws.counts);
+    INPC_TRY(check_launch("k_draw_count"));
+  }
+  INPC_TRY((scan<uint32_t, CountLoad, false>(CountLoad{ws.counts}, L, ws.starts, ws.count_tops, s)));
+  if (n_samples > 0) {
+    const int64_t grid = std::min<int64_t>(ceil_div(n_samples, 256), (int64_t)sms * 16);
+    k_place<<<(unsigned)grid, 256, 0, s>>>(ws.starts, L, sl, n_samples, k0, k1, view_id, tree->centers,
+                                           tree->levels, tree->root_size, leaf_idx_out, pos_out);
+    INPC_TRY(check_launch("k_place"));
+  }
+  if (leaf_counts_out)
+    INPC_CUDA(cudaMemcpyAsync(leaf_counts_out, ws.counts, sizeof(uint32_t) * L, cudaMemcpyDeviceToDevice, s),
+              "copy counts");
+  return INPC_OK;
+}

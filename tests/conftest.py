@@ -24,3 +24,17 @@ def oracle():
     from oracle import oracle as O
     O.build()
     return O
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """The compiled library plus torch on cuda:0 (GPU tests only)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2403_16862_gb300 import build
+    build.build()
+    from paper_2403_16862_gb300 import _binding
+    _binding.load()
+    torch.cuda.set_device(0)
+    return torch.device("cuda:0")

@@ -1,0 +1,94 @@
+"""The C-ABI library loads and exports every symbol include/inpc.h declares,
+and its host-only entry points (size queries, argument validation) behave
+as documented.  No compute calls: runs without a GPU."""
+import os
+import re
+
+import pytest
+
+from paper_2403_16862_gb300 import build, scenes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    build.build()
+    from paper_2403_16862_gb300 import _binding
+    _binding.load()
+    return _binding
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "inpc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(inpc_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(B):
+    import ctypes
+    declared = _declared_functions()
+    assert sorted(B.DECLARED) == declared
+    lib = ctypes.CDLL(B.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert "sm_103a" in B.version()
+
+
+def test_hashgrid_entries_match_layout_rule(B, oracle):
+    from paper_2403_16862_gb300 import api
+    for log2_T in (12, 19, 21):
+        res = scenes.geometric_resolutions(16, 16, 4096)
+        assert api.hashgrid_n_entries(res, log2_T) == oracle.hash_entries(res, log2_T)
+    assert api.hashgrid_n_entries([1, 2, 3], 10) == oracle.hash_entries([1, 2, 3], 10)
+
+
+def test_workspace_sizes(B):
+    from paper_2403_16862_gb300 import api
+    s1 = B.inpc_sample_workspace_size(65536, 1 << 22)
+    s2 = B.inpc_sample_workspace_size(1 << 20, 1 << 24)
+    assert 65536 * 16 <= s1 < s2
+    cam = scenes.make_camera((0.5, 0.5, -1.2), 900, 900, 640, 416, 1280, 832)
+    opts = api.RasterOptions(n_channels=64, head_mode=True)
+    w = api.rasterize_workspace_size(cam, opts, 1 << 22)
+    assert w >= (1 << 22) * 4 * 8
+    assert s1 % 256 == 0 and w % 256 == 0
+
+
+def test_argument_errors_are_reported(B):
+    from paper_2403_16862_gb300 import api
+    with pytest.raises(B.InpcError) as e:
+        B.inpc_sample_workspace_size(0, 10)
+    assert e.value.status == B.INPC_ERR_CAPACITY
+    with pytest.raises(B.InpcError) as e:
+        B.inpc_sample_workspace_size(1 << 25, 10)
+    assert e.value.status == B.INPC_ERR_CAPACITY
+    d = api.hashgrid_desc([16, 32], 10, n_feats=2)
+    with pytest.raises(B.InpcError) as e:
+        B.inpc_hashgrid_n_entries(d)
+    assert e.value.status == B.INPC_ERR_UNSUPPORTED
+    d = api.hashgrid_desc([16, 32], 30)
+    with pytest.raises(B.InpcError) as e:
+        B.inpc_hashgrid_n_entries(d)
+    assert e.value.status == B.INPC_ERR_INVALID_ARG
+    # null pointers are rejected before anything touches a device
+    d = api.hashgrid_desc([16, 32], 10)
+    with pytest.raises(B.InpcError) as e:
+        B.inpc_query_hashgrid(d, None, None, 5, None, None)
+    assert e.value.status == B.INPC_ERR_INVALID_ARG
+    cam = scenes.make_camera((0, 0, -3), 10, 10, 5, 5, 10, 10)
+    cc = api.camera(cam)
+    with pytest.raises(B.InpcError) as e:
+        B.inpc_rasterize_workspace_size(cc, api.RasterOptions(n_channels=200).c(), 10)
+    assert e.value.status == B.INPC_ERR_UNSUPPORTED
+    with pytest.raises(B.InpcError) as e:
+        B.inpc_rasterize_workspace_size(cc, api.RasterOptions(n_channels=4, tile_w=32, tile_h=16).c(), 10)
+    assert e.value.status == B.INPC_ERR_INVALID_ARG
+    with pytest.raises(B.InpcError) as e:
+        B.inpc_rasterize_workspace_size(cc, api.RasterOptions(n_channels=4).c(), (1 << 25) + 1)
+    assert e.value.status == B.INPC_ERR_CAPACITY
+    with pytest.raises(B.InpcError) as e:
+        B.inpc_rasterize_fwd(cc, api.RasterOptions(n_channels=4).c(), None, None, None, 10, None, None, None,
+                             None, 0, None)
+    assert e.value.status == B.INPC_ERR_INVALID_ARG
+    assert "workspace" in str(e.value)

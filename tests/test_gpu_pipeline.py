@@ -1,0 +1,94 @@
+"""The whole hot path on the GPU against the oracle's own pipeline: octree
+sampling -> hash-grid query -> head-mode rasterizer forward and backward ->
+table gradient.  The full-size case is the benchmark's workload
+(65,536-leaf octree, 4,194,304 samples, 16-level 2^19 grid, 1280x832), in
+the benchmark's launch configuration.  The oracle side never sees a GPU
+value: it samples its own positions (exact FP64, rounded once to the FP32
+interface type) and runs every stage itself."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2403_16862_gb300 import api, scenes
+from tests._parity import assert_cond_close
+from tests.test_gpu_raster import _excluded_points
+
+pytestmark = pytest.mark.gpu
+
+RES16 = scenes.geometric_resolutions(16, 16, 4096)
+
+
+def _pipeline(gpu, oracle, n_leaves, n_samples, log2_T, cam, seed=0, graph_check=False):
+    tree = scenes.make_octree(seed, n_leaves)
+    grid = scenes.make_hashgrid(seed + 1, oracle.hash_entries(RES16, log2_T), RES16, log2_T)
+    g_img = scenes.upstream_grad(seed + 2, (cam.height, cam.width, 64))
+
+    # ---- GPU
+    c = torch.from_numpy(tree.centers).to(gpu)
+    l = torch.from_numpy(tree.levels).to(gpu)
+    w = torch.from_numpy(tree.weights).to(gpu)
+    table = torch.from_numpy(grid.table).to(gpu)
+    desc = api.hashgrid_desc(RES16, log2_T)
+    opts = api.RasterOptions(n_channels=64, head_mode=True)
+    leaf, pos = api.sample_octree(c, l, w, tree.root_size, seed, 0, n_samples)
+    h = api.query_hashgrid(desc, table, pos)
+    img, T, n, ws = api.rasterize_fwd(cam, opts, pos, h)
+    _, dh = api.rasterize_bwd(cam, opts, pos, h, None, T, n, torch.from_numpy(g_img).to(gpu), ws)
+    gt = torch.zeros_like(table)
+    api.query_hashgrid_bwd(desc, pos, dh, gt)
+    torch.cuda.synchronize()
+
+    # ---- oracle
+    o_leaf, o_pos64, _ = oracle.sample_octree(tree, seed, 0, n_samples)
+    o_pos = o_pos64.astype(np.float32)
+    o_h, o_hab = oracle.hash_fwd(RES16, log2_T, grid.table, o_pos, with_abs=True)
+    ref = oracle.raster_fwd(cam, o_pos, o_h, head_mode=True, with_abs=True)
+    rb = oracle.raster_bwd(cam, o_pos, o_h, g_img, head_mode=True, with_abs=True)
+    o_gt, o_gab = oracle.hash_bwd(RES16, log2_T, 4, o_pos, rb["d_feat"], with_abs=True)
+
+    # ---- parity
+    assert np.array_equal(leaf.cpu().numpy(), o_leaf)
+    assert np.array_equal(pos.cpu().numpy(), o_pos)
+    assert_cond_close(h.cpu().numpy(), o_h, o_hab, what="h")
+    ok = ref["flags"] == 0
+    assert (~ok).sum() <= max(2, 1e-4 * ok.size)
+    assert np.array_equal(n.cpu().numpy()[ok], ref["n_contrib"][ok])
+    assert_cond_close(img.cpu().numpy(), ref["image"], ref["abs"], mask=ok[..., None], what="image")
+    assert_cond_close(T.cpu().numpy(), ref["T_final"], ref["T_final"], mask=ok, what="T_final")
+    keep = ~_excluded_points(oracle, cam, o_pos, ref["flags"])
+    assert_cond_close(dh.cpu().numpy(), rb["d_feat"], rb["abs_feat"], mask=keep[:, None], what="dh")
+    if keep.all():
+        assert_cond_close(gt.cpu().numpy(), o_gt, o_gab, what="grad_table")
+    print("pipeline: %d samples, %d fragments, max blended per pixel %d, flagged pixels %d"
+          % (n_samples, int(ref["n_frags"].sum()), int(ref["n_contrib"].max()), int((~ok).sum())))
+
+    if graph_check:
+        # the same sequence captured in a CUDA graph replays identically
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        graph = torch.cuda.CUDAGraph()
+        outs = {}
+        with torch.cuda.stream(s):
+            gd = torch.from_numpy(g_img).to(gpu)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(graph, stream=s):
+                lf, ps = api.sample_octree(c, l, w, tree.root_size, seed, 0, n_samples)
+                hh = api.query_hashgrid(desc, table, ps)
+                im, TT, nn, ww = api.rasterize_fwd(cam, opts, ps, hh)
+                outs["img"] = im
+                outs["dh"] = api.rasterize_bwd(cam, opts, ps, hh, None, TT, nn, gd, ww)[1]
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(outs["img"], img)
+        assert torch.allclose(outs["dh"], dh, rtol=0, atol=1e-5 * float(dh.abs().max()))
+
+
+def test_pipeline_small(gpu, oracle):
+    cam = scenes.make_camera((0.5, 0.5, -1.2), 900 * 0.25, 900 * 0.25, 160, 104, 320, 208)
+    _pipeline(gpu, oracle, 4096 + 7 * 300, 200_000, 16, cam, seed=3, graph_check=True)
+
+
+def test_pipeline_full_size(gpu, oracle):
+    """65,536 leaves, 4,194,304 samples, 2^19 grid, 1280x832, fwd + bwd."""
+    cam = scenes.make_camera((0.5, 0.5, -1.2), 900, 900, 640, 416, 1280, 832)
+    _pipeline(gpu, oracle, 65536, 4_194_304, 19, cam, seed=0)

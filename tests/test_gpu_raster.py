@@ -1,0 +1,139 @@
+"""GPU rasterizer forward/backward against the oracle.
+
+Images, T_final and gradients follow the condition-aware 1e-5 rule; the
+per-pixel blended counts are exact.  Pixels whose stopping decision falls
+within 1e-5 (relative) of t_min are excluded and counted (their count must
+stay below 1e-4 of the pixels); gradients of points with a fragment in such
+a pixel are excluded likewise."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2403_16862_gb300 import api, scenes
+from tests._parity import assert_cond_close
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(gpu, cam, pos, feat, opacity, head, tile=(0, 0), g=None):
+    opts = api.RasterOptions(n_channels=feat.shape[1], head_mode=head, tile_w=tile[0], tile_h=tile[1])
+    P = torch.from_numpy(pos).to(gpu)
+    Fe = torch.from_numpy(np.ascontiguousarray(feat, dtype=np.float32)).to(gpu)
+    O = None if head else torch.from_numpy(opacity.astype(np.float32)).to(gpu)
+    img, T, n, ws = api.rasterize_fwd(cam, opts, P, Fe, O)
+    out = dict(image=img.cpu().numpy(), T_final=T.cpu().numpy(), n_contrib=n.cpu().numpy())
+    if g is not None:
+        d_op, d_feat = api.rasterize_bwd(cam, opts, P, Fe, O, T, n, torch.from_numpy(g).to(gpu), ws)
+        out["d_feat"] = d_feat.cpu().numpy()
+        if d_op is not None:
+            out["d_opacity"] = d_op.cpu().numpy()
+    torch.cuda.synchronize()
+    return out
+
+
+def _excluded_points(oracle, cam, pos, flags):
+    cnt, ids, _, _ = oracle.fragment_lists(cam, pos)
+    start = np.concatenate([[0], np.cumsum(cnt.ravel())])
+    bad = np.zeros(pos.shape[0], bool)
+    for q in np.flatnonzero(flags.ravel()):
+        bad[ids[start[q]:start[q + 1]]] = True
+    return bad
+
+
+def _compare(gpu, oracle, cam, pos, feat, opacity, head, tile=(0, 0), with_bwd=True, seed=0):
+    g = np.random.default_rng(seed + 100).normal(size=(cam.height, cam.width, feat.shape[1])).astype(np.float32) \
+        if with_bwd else None
+    got = _run(gpu, cam, pos, feat, opacity, head, tile, g)
+    ref = oracle.raster_fwd(cam, pos, feat, opacity=opacity, head_mode=head, with_abs=True)
+    ok = ref["flags"] == 0
+    n_flag = int((~ok).sum())
+    assert n_flag <= max(2, 1e-4 * ok.size), "too many threshold-ambiguous pixels: %d" % n_flag
+    assert np.array_equal(got["n_contrib"][ok], ref["n_contrib"][ok]), "blended counts"
+    assert_cond_close(got["image"], ref["image"], ref["abs"], mask=ok[..., None], what="image")
+    assert_cond_close(got["T_final"], ref["T_final"], ref["T_final"], mask=ok, what="T_final")
+    if with_bwd:
+        rb = oracle.raster_bwd(cam, pos, feat, g, opacity=opacity, head_mode=head, with_abs=True)
+        keep = ~_excluded_points(oracle, cam, pos, ref["flags"])
+        assert_cond_close(got["d_feat"], rb["d_feat"], rb["abs_feat"], mask=keep[:, None], what="d_feat")
+        if not head:
+            assert_cond_close(got["d_opacity"], rb["d_opacity"], rb["abs_opacity"], mask=keep, what="d_opacity")
+    return got, ref
+
+
+def test_plain_rasterizer_workload(gpu, oracle):
+    """65,536 points in [-1,1]^3, 8 features, 256x256, forward and backward."""
+    pts, cam = scenes.raster_points_scene(seed=0)
+    _compare(gpu, oracle, cam, pts.pos, pts.feat, pts.opacity, head=False)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (16, 8), (32, 8), (5, 7)])
+def test_tile_shapes_and_ragged_image(gpu, oracle, tile):
+    pts, cam = scenes.raster_points_scene(seed=1, n=20000, n_feat=4, size=100, focal=100.0)
+    cam.width = 97  # ragged: not a multiple of any tile width
+    cam.cx = 48.5
+    _compare(gpu, oracle, cam, pts.pos, pts.feat, pts.opacity, head=False, tile=tile, seed=1)
+
+
+@pytest.mark.parametrize("F", [1, 3, 4, 12, 64, 128])
+def test_channel_counts(gpu, oracle, F):
+    pts, cam = scenes.raster_points_scene(seed=2, n=8000, n_feat=F, size=48, focal=48.0)
+    _compare(gpu, oracle, cam, pts.pos, pts.feat, pts.opacity, head=False, seed=F)
+
+
+def test_head_mode(gpu, oracle):
+    pts, cam = scenes.raster_points_scene(seed=3, n=30000, n_feat=64, size=128, focal=128.0)
+    h = np.random.default_rng(4).normal(0.0, 0.6, size=(30000, 64)).astype(np.float32)
+    got, ref = _compare(gpu, oracle, cam, pts.pos, h, None, head=True, seed=3)
+    np.testing.assert_allclose(got["image"][..., 0], 1 - got["T_final"], atol=2e-6)
+
+
+def test_overfull_tiles_take_the_global_sort(gpu, oracle):
+    """Dense clusters: tiles far above the shared-memory capacity (8192
+    forward, 4096 backward) and single pixels with thousands of fragments."""
+    rng = np.random.default_rng(5)
+    base, cam = scenes.raster_points_scene(seed=5, n=6000, n_feat=8, size=64, focal=64.0)
+    cl1 = (np.array([0.1, -0.05, 0.0]) + rng.normal(0, 0.004, size=(15000, 3))).astype(np.float32)
+    cl2 = (np.array([-0.4, 0.3, 0.2]) + rng.normal(0, 0.03, size=(6000, 3))).astype(np.float32)
+    pos = np.concatenate([base.pos, cl1, cl2])
+    n = pos.shape[0]
+    opacity = rng.uniform(0.001, 0.02, size=n).astype(np.float32)  # long lists before T < 1e-4
+    feat = rng.normal(size=(n, 8)).astype(np.float32)
+    got, ref = _compare(gpu, oracle, cam, pos, feat, opacity, head=False, seed=5)
+    assert ref["n_frags"].max() > 8192 // 4
+
+
+def test_empty_and_culled(gpu, oracle):
+    pts, cam = scenes.raster_points_scene(seed=6, n=1000, n_feat=4, size=32, focal=32.0)
+    got = _run(gpu, cam, pts.pos[:0], pts.feat[:0], pts.opacity[:0], False)
+    assert np.all(got["image"] == 0) and np.all(got["T_final"] == 1) and np.all(got["n_contrib"] == 0)
+    pos = pts.pos.copy()
+    pos[:, 2] = -3.5  # all behind the camera
+    g = np.ones((32, 32, 4), np.float32)
+    got = _run(gpu, cam, pos, pts.feat, pts.opacity, False, g=g)
+    assert np.all(got["n_contrib"] == 0) and np.all(got["d_feat"] == 0) and np.all(got["d_opacity"] == 0)
+    pos = pts.pos.copy()
+    pos[::2, 0] += 50.0  # half of them far outside the image
+    _compare(gpu, oracle, cam, pos, pts.feat, pts.opacity, head=False, seed=6)
+
+
+def test_duplicate_points_tie_break(gpu, oracle):
+    pts, cam = scenes.raster_points_scene(seed=7, n=3000, n_feat=4, size=32, focal=32.0)
+    pos = np.concatenate([pts.pos, pts.pos[:1500]])
+    op = np.concatenate([pts.opacity, pts.opacity[:1500] * 0.5])
+    fe = np.concatenate([pts.feat, -pts.feat[:1500]])
+    _compare(gpu, oracle, cam, pos, fe, op, head=False, seed=7)
+
+
+def test_autograd_wrapper(gpu):
+    pts, cam = scenes.raster_points_scene(seed=8, n=5000, n_feat=4, size=32, focal=32.0)
+    P = torch.from_numpy(pts.pos).to(gpu)
+    Fe = torch.from_numpy(pts.feat).to(gpu).requires_grad_(True)
+    O = torch.from_numpy(pts.opacity).to(gpu).requires_grad_(True)
+    opts = api.RasterOptions(n_channels=4)
+    img, T, n = api.Rasterize.apply(P, Fe, O, cam, opts)
+    g = torch.randn_like(img)
+    (img * g).sum().backward()
+    img2, T2, n2, ws = api.rasterize_fwd(cam, opts, P, Fe.detach(), O.detach())
+    d_op, d_feat = api.rasterize_bwd(cam, opts, P, Fe.detach(), O.detach(), T2, n2, g, ws)
+    assert torch.equal(img, img2)
+    assert torch.allclose(Fe.grad, d_feat, atol=1e-6) and torch.allclose(O.grad, d_op, atol=1e-6)
