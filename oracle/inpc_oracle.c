@@ -298,9 +298,11 @@ int oracle_hash_fwd(int32_t n_levels, const int32_t* res, int32_t log2_T, int32_
 }
 
 /* grad_table[row, f] += weight * dh[n, l*F + f]; abs_out (optional) receives
- * the same sum of absolute terms, used as the condition-aware scale. */
+ * the sum of weight * |dh| (or weight * dh_abs, the caller's own absolute-term
+ * sums for dh, when given), used as the condition-aware scale. */
 int oracle_hash_bwd(int32_t n_levels, const int32_t* res, int32_t log2_T, int32_t n_feats,
-                    const double* pos, const double* dh, int64_t n, double* grad_out, double* abs_out) {
+                    const double* pos, const double* dh, int64_t n, double* grad_out, double* abs_out,
+                    const double* dh_abs) {
   int64_t* offsets = (int64_t*)malloc(sizeof(int64_t) * (size_t)n_levels);
   if (!offsets) return ORACLE_ERR_NOMEM;
   oracle_hash_layout(n_levels, res, log2_T, offsets);
@@ -320,7 +322,7 @@ int oracle_hash_bwd(int32_t n_levels, const int32_t* res, int32_t log2_T, int32_
         for (int f = 0; f < n_feats; ++f) {
           double term = w * dh[p * C + l * n_feats + f];
           grad_out[row * n_feats + f] += term;
-          if (abs_out) abs_out[row * n_feats + f] += fabs(term);
+          if (abs_out) abs_out[row * n_feats + f] += w * (dh_abs ? dh_abs[p * C + l * n_feats + f] : fabs(dh[p * C + l * n_feats + f]));
         }
       }
     }
@@ -480,13 +482,24 @@ static double point_color(const oracle_raster_opts* o, const double* feat, int64
   return feat[p * o->n_channels + c];
 }
 
+/* Magnitude of a blended color channel for the condition-aware tolerance:
+ * |c|, or feat_abs (the caller's own sum of absolute terms that produced the
+ * feature, e.g. the grid query's sum |w t|) when given; 1 for the constant
+ * channel 0 in head mode. */
+static double color_scale(const oracle_raster_opts* o, const double* feat, const double* feat_abs, int64_t p, int c) {
+  if (o->opacity_from_ch0 && c == 0) return 1.0;
+  if (feat_abs) return feat_abs[p * o->n_channels + c];
+  return fabs(feat[p * o->n_channels + c]);
+}
+
 /* Forward: image[H,W,F], T_final[H,W], n_contrib[H,W], n_frags[H,W] (all
  * fragments of the pixel), flags[H,W] bit 0 = stopping decision within the
- * ambiguity band of t_min; abs_out[H,W,F] (optional) = sum |T alpha c|. */
+ * ambiguity band of t_min; abs_out[H,W,F] (optional) = sum T alpha |c|
+ * (|c| from feat_abs when given). */
 int oracle_raster_fwd(const oracle_camera* cam, const oracle_raster_opts* o, const float* pos,
                       const double* opacity, const double* feat, int64_t n,
                       double* image, double* T_final, int32_t* n_contrib, int32_t* n_frags,
-                      uint8_t* flags, double* abs_out) {
+                      uint8_t* flags, double* abs_out, const double* feat_abs) {
   frag_lists L;
   int st = build_lists(cam, pos, n, &L);
   if (st != ORACLE_OK) { free_lists(&L); return st; }
@@ -510,7 +523,7 @@ int oracle_raster_fwd(const oracle_camera* cam, const oracle_raster_opts* o, con
       for (int c = 0; c < F; ++c) {
         double term = T * a * point_color(o, feat, r->id, c);
         C[c] += term;
-        if (abs_out) abs_out[q * F + c] += fabs(term);
+        if (abs_out) abs_out[q * F + c] += T * a * color_scale(o, feat, feat_abs, r->id, c);
       }
       double Tn = T * (1.0 - a);
       ++cnt;
@@ -539,7 +552,8 @@ int oracle_raster_fwd(const oracle_camera* cam, const oracle_raster_opts* o, con
  * abs_feat (optional) receives sum |terms| of d_feat for the tolerance. */
 int oracle_raster_bwd(const oracle_camera* cam, const oracle_raster_opts* o, const float* pos,
                       const double* opacity, const double* feat, int64_t n, const double* d_image,
-                      double* d_opacity, double* d_feat, double* abs_feat, double* abs_opacity) {
+                      double* d_opacity, double* d_feat, double* abs_feat, double* abs_opacity,
+                      const double* feat_abs) {
   frag_lists L;
   int st = build_lists(cam, pos, n, &L);
   if (st != ORACLE_OK) { free_lists(&L); return st; }
@@ -580,9 +594,8 @@ int oracle_raster_bwd(const oracle_camera* cam, const oracle_raster_opts* o, con
         al[k] = a;
         double s = 0.0, sa = 0.0;
         for (int c = 0; c < F; ++c) {
-          double t = point_color(o, feat, r->id, c) * g[c];
-          s += t;
-          sa += fabs(t);
+          s += point_color(o, feat, r->id, c) * g[c];
+          sa += color_scale(o, feat, feat_abs, r->id, c) * fabs(g[c]);
         }
         dot[k] = s;
         dotabs[k] = sa;

@@ -82,16 +82,16 @@ def lib():
             L.oracle_hash_vertex_index.restype = C.c_int64
             L.oracle_hash_fwd.argtypes = [C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, C.c_int64, _P, _P]
             L.oracle_hash_fwd.restype = C.c_int
-            L.oracle_hash_bwd.argtypes = [C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, C.c_int64, _P, _P]
+            L.oracle_hash_bwd.argtypes = [C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, C.c_int64, _P, _P, _P]
             L.oracle_hash_bwd.restype = C.c_int
             L.oracle_project.argtypes = [C.POINTER(OracleCamera), _P, _P, _P, _P]
             L.oracle_project.restype = C.c_int
             L.oracle_splat_corners.argtypes = [C.c_double, C.c_double, _P, _P, _P]
             L.oracle_raster_fwd.argtypes = [C.POINTER(OracleCamera), C.POINTER(OracleRasterOpts), _P, _P, _P,
-                                            C.c_int64, _P, _P, _P, _P, _P, _P]
+                                            C.c_int64, _P, _P, _P, _P, _P, _P, _P]
             L.oracle_raster_fwd.restype = C.c_int
             L.oracle_raster_bwd.argtypes = [C.POINTER(OracleCamera), C.POINTER(OracleRasterOpts), _P, _P, _P,
-                                            C.c_int64, _P, _P, _P, _P, _P]
+                                            C.c_int64, _P, _P, _P, _P, _P, _P]
             L.oracle_raster_bwd.restype = C.c_int
             L.oracle_fragment_lists.argtypes = [C.POINTER(OracleCamera), _P, C.c_int64, _P, _P, _P, _P]
             L.oracle_fragment_lists.restype = C.c_int64
@@ -215,7 +215,7 @@ def hash_fwd(res, log2_T: int, table, pos, with_abs: bool = False):
     return (h, ab) if with_abs else h
 
 
-def hash_bwd(res, log2_T: int, n_feats: int, pos, dh, with_abs: bool = False):
+def hash_bwd(res, log2_T: int, n_feats: int, pos, dh, with_abs: bool = False, dh_abs=None):
     r = _i32(res)
     p = _f64(pos)
     g = _f64(dh)
@@ -223,7 +223,9 @@ def hash_bwd(res, log2_T: int, n_feats: int, pos, dh, with_abs: bool = False):
     total, _ = hash_layout(res, log2_T)
     grad = np.zeros((total, n_feats), dtype=np.float64)
     ab = np.zeros_like(grad) if with_abs else None
-    st = lib().oracle_hash_bwd(len(res), _ptr(r), log2_T, n_feats, _ptr(p), _ptr(g), n, _ptr(grad), _ptr(ab))
+    da = _f64(dh_abs) if dh_abs is not None else None
+    st = lib().oracle_hash_bwd(len(res), _ptr(r), log2_T, n_feats, _ptr(p), _ptr(g), n, _ptr(grad), _ptr(ab),
+                               _ptr(da))
     if st != 0:
         raise OracleError("hash_bwd failed (%d)" % st)
     return (grad, ab) if with_abs else grad
@@ -276,8 +278,10 @@ def splat_corners(u: float, v: float):
 
 
 def raster_fwd(cam, pos, feat, opacity=None, head_mode=False, t_min=1e-4, alpha_max=0.99,
-               ambiguity_rel=1e-5, with_abs=False):
-    """Returns dict with image [H,W,F], T_final, n_contrib, n_frags, flags (and abs)."""
+               ambiguity_rel=1e-5, with_abs=False, feat_abs=None):
+    """Returns dict with image [H,W,F], T_final, n_contrib, n_frags, flags (and abs).
+    ``feat_abs`` (optional, [N,F]) replaces |feat| as the channel magnitude in
+    the absolute-term sums (the tolerance scale), e.g. a grid query's sum |w t|."""
     p = _f32(pos)
     f = _f64(feat)
     n, F = f.shape
@@ -293,8 +297,9 @@ def raster_fwd(cam, pos, feat, opacity=None, head_mode=False, t_min=1e-4, alpha_
     ab = np.zeros((H, W, F), np.float64) if with_abs else None
     cs = camera_struct(cam)
     o = _opts(F, head_mode, t_min, alpha_max, ambiguity_rel)
+    fa = _f64(feat_abs) if feat_abs is not None else None
     st = lib().oracle_raster_fwd(C.byref(cs), C.byref(o), _ptr(p), _ptr(op), _ptr(f), n, _ptr(image), _ptr(T),
-                                 _ptr(nc), _ptr(nf), _ptr(flags), _ptr(ab))
+                                 _ptr(nc), _ptr(nf), _ptr(flags), _ptr(ab), _ptr(fa))
     if st != 0:
         raise OracleError("raster_fwd failed (%d)" % st)
     out = dict(image=image, T_final=T, n_contrib=nc, n_frags=nf, flags=flags)
@@ -304,7 +309,7 @@ def raster_fwd(cam, pos, feat, opacity=None, head_mode=False, t_min=1e-4, alpha_
 
 
 def raster_bwd(cam, pos, feat, d_image, opacity=None, head_mode=False, t_min=1e-4, alpha_max=0.99,
-               with_abs=False):
+               with_abs=False, feat_abs=None):
     """Returns dict with d_feat [N,F] (and d_opacity [N] in given-opacity mode)."""
     p = _f32(pos)
     f = _f64(feat)
@@ -317,8 +322,9 @@ def raster_bwd(cam, pos, feat, d_image, opacity=None, head_mode=False, t_min=1e-
     ab_o = np.zeros(n, np.float64) if with_abs else None
     cs = camera_struct(cam)
     o = _opts(F, head_mode, t_min, alpha_max, 0.0)
+    fa = _f64(feat_abs) if feat_abs is not None else None
     st = lib().oracle_raster_bwd(C.byref(cs), C.byref(o), _ptr(p), _ptr(op), _ptr(f), n, _ptr(g),
-                                 _ptr(d_op), _ptr(d_feat), _ptr(ab_f), _ptr(ab_o))
+                                 _ptr(d_op), _ptr(d_feat), _ptr(ab_f), _ptr(ab_o), _ptr(fa))
     if st != 0:
         raise OracleError("raster_bwd failed (%d)" % st)
     out = dict(d_feat=d_feat)

@@ -1,9 +1,9 @@
 // hashgrid.cu -- multi-resolution hash-grid query (Sec. 3.3, App. A.5) and
 // its adjoint (the table gradient).
 //
-// One thread per (point, level), point-major, so a warp covers two points x
-// 16 levels: the float4 outputs of a warp form 512 contiguous bytes, and the
-// point's position is a broadcast load.  The 8 corner rows of a level are
+// One thread per (point, level); levels go in groups of two along grid y so
+// that the rows in use at any time fit in L2, and within a group a warp
+// covers 16 points x 2 levels (32-byte output pieces, one sector each).  The 8 corner rows of a level are
 // gathered as 16-byte vectors (FP32) or 8-byte vectors (BF16); for the x
 // neighbours the hash (multiplier 1 on x) keeps rows adjacent, so a corner
 // pair usually shares one 32-byte sector.  The output is written with
@@ -62,26 +62,23 @@ inpc_status make_params(const inpc_hashgrid_desc* g, GridParams& p, int64_t* tot
   return INPC_OK;
 }
 
-// Cell index and exact-then-rounded fraction of x in [0, 1] at resolution N:
-// s = fl(x N) and e = x N - s exactly (FMA), so frac = (s - cell) + e is
-// rounded once, and the cell is floor of the exact product.
-__device__ __forceinline__ void cell_frac(float x, int N, uint32_t& cell, float& frac) {
+// Cell of x in [0, 1] at resolution N and both linear weights of that cell:
+// with s = fl(x N) and e = x N - s exactly (FMA), the upper-corner weight
+// f1 = x N - cell and the lower-corner weight f0 = cell + 1 - x N are each
+// formed from exact terms and rounded once, so each keeps full relative
+// accuracy even when the other is close to 1; the cell is the floor of the
+// exact product.
+__device__ __forceinline__ void cell_frac(float x, int N, uint32_t& cell, float& f0, float& f1) {
   x = fminf(fmaxf(x, 0.0f), 1.0f);
   const float Nf = (float)N;
   const float s = __fmul_rn(x, Nf);
   const float e = __fmaf_rn(x, Nf, -s);
   float c = floorf(s);
-  float f = __fadd_rn(__fsub_rn(s, c), e);
-  if (f < 0.0f) {
-    c -= 1.0f;
-    f = __fadd_rn(f, 1.0f);
-  }
-  if (c > Nf - 1.0f) {
-    c = Nf - 1.0f;
-    f = __fadd_rn(__fsub_rn(s, c), e);
-  }
+  if (__fadd_rn(__fsub_rn(s, c), e) < 0.0f) c -= 1.0f;  // exact product just below the integer s
+  if (c > Nf - 1.0f) c = Nf - 1.0f;
   cell = (uint32_t)c;
-  frac = f;
+  f1 = __fadd_rn(__fsub_rn(s, c), e);
+  f0 = __fsub_rn(__fsub_rn(c + 1.0f, s), e);
 }
 
 __device__ __forceinline__ uint32_t vertex_row(const GridParams& P, int l, uint32_t x, uint32_t y, uint32_t z) {
@@ -126,36 +123,41 @@ __device__ __forceinline__ void store_out<__nv_bfloat16>(__nv_bfloat16* __restri
   __stcs(reinterpret_cast<uint2*>(out) + idx4, raw);
 }
 
+// Levels are processed in groups of kLevelGroup along grid y: blocks are
+// dispatched in linear order, so all points visit one group of levels
+// before the next, and the rows touched at a time (one or two 8 MB levels)
+// stay resident in L2 instead of the whole table.
+constexpr int kLevelGroup = 2;
+
 template <class TT, class OT>
 __global__ void __launch_bounds__(256) k_hash_fwd(GridParams P, const TT* __restrict__ table,
                                                   const float* __restrict__ pos, long long n, OT* __restrict__ h) {
-  const long long total = n * P.n_levels;
+  const int l0 = blockIdx.y * kLevelGroup;
+  const int gl = min(kLevelGroup, P.n_levels - l0);
+  const long long total = n * gl;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i / P.n_levels;
-    const int l = (int)(i - p * P.n_levels);
+    const long long p = i / gl;
+    const int l = l0 + (int)(i - p * gl);
     uint32_t cx, cy, cz;
-    float fx, fy, fz;
+    float gx[2], gy[2], gz[2];
     const int N = P.res[l];
-    cell_frac(__ldg(pos + 3 * p + 0), N, cx, fx);
-    cell_frac(__ldg(pos + 3 * p + 1), N, cy, fy);
-    cell_frac(__ldg(pos + 3 * p + 2), N, cz, fz);
+    cell_frac(__ldg(pos + 3 * p + 0), N, cx, gx[0], gx[1]);
+    cell_frac(__ldg(pos + 3 * p + 1), N, cy, gy[0], gy[1]);
+    cell_frac(__ldg(pos + 3 * p + 2), N, cz, gz[0], gz[1]);
     const TT* tab = table + 4 * P.offset[l];
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
-      const float wx = bx ? fx : __fsub_rn(1.0f, fx);
-      const float wy = by ? fy : __fsub_rn(1.0f, fy);
-      const float wz = bz ? fz : __fsub_rn(1.0f, fz);
-      const float w = wx * wy * wz;
+      const float w = gx[bx] * gy[by] * gz[bz];
       const float4 t = load_row<TT>(tab, vertex_row(P, l, cx + bx, cy + by, cz + bz));
       acc.x = fmaf(w, t.x, acc.x);
       acc.y = fmaf(w, t.y, acc.y);
       acc.z = fmaf(w, t.z, acc.z);
       acc.w = fmaf(w, t.w, acc.w);
     }
-    store_out<OT>(h, i, acc);
+    store_out<OT>(h, p * P.n_levels + l, acc);
   }
 }
 
@@ -167,37 +169,38 @@ __device__ __forceinline__ void red_add_v4(float* addr, float4 v) {
 __global__ void __launch_bounds__(256) k_hash_bwd(GridParams P, const float* __restrict__ pos,
                                                   const float* __restrict__ dh, long long n,
                                                   float* __restrict__ grad) {
-  const long long total = n * P.n_levels;
+  const int l0 = blockIdx.y * kLevelGroup;
+  const int gl = min(kLevelGroup, P.n_levels - l0);
+  const long long total = n * gl;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i / P.n_levels;
-    const int l = (int)(i - p * P.n_levels);
-    const float4 g = __ldcs(reinterpret_cast<const float4*>(dh) + i);
+    const long long p = i / gl;
+    const int l = l0 + (int)(i - p * gl);
+    const float4 g = __ldcs(reinterpret_cast<const float4*>(dh) + p * P.n_levels + l);
     if (g.x == 0.f && g.y == 0.f && g.z == 0.f && g.w == 0.f) continue;
     uint32_t cx, cy, cz;
-    float fx, fy, fz;
+    float gx[2], gy[2], gz[2];
     const int N = P.res[l];
-    cell_frac(__ldg(pos + 3 * p + 0), N, cx, fx);
-    cell_frac(__ldg(pos + 3 * p + 1), N, cy, fy);
-    cell_frac(__ldg(pos + 3 * p + 2), N, cz, fz);
-    float* gl = grad + 4 * P.offset[l];
+    cell_frac(__ldg(pos + 3 * p + 0), N, cx, gx[0], gx[1]);
+    cell_frac(__ldg(pos + 3 * p + 1), N, cy, gy[0], gy[1]);
+    cell_frac(__ldg(pos + 3 * p + 2), N, cz, gz[0], gz[1]);
+    float* gl_ = grad + 4 * P.offset[l];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
-      const float wx = bx ? fx : __fsub_rn(1.0f, fx);
-      const float wy = by ? fy : __fsub_rn(1.0f, fy);
-      const float wz = bz ? fz : __fsub_rn(1.0f, fz);
-      const float w = wx * wy * wz;
+      const float w = gx[bx] * gy[by] * gz[bz];
       const uint32_t row = vertex_row(P, l, cx + bx, cy + by, cz + bz);
-      red_add_v4(gl + 4ull * row, make_float4(w * g.x, w * g.y, w * g.z, w * g.w));
+      red_add_v4(gl_ + 4ull * row, make_float4(w * g.x, w * g.y, w * g.z, w * g.w));
     }
   }
 }
 
-unsigned grid_for(long long work, int threads) {
-  const long long cap = (long long)device_sm_count() * 64;
+dim3 grid_for(long long n, int n_levels, int threads) {
+  const int groups = (n_levels + kLevelGroup - 1) / kLevelGroup;
+  const long long work = n * std::min(kLevelGroup, n_levels);
+  const long long cap = (long long)device_sm_count() * 16;
   long long g = ceil_div(work, threads);
-  return (unsigned)std::max<long long>(1, std::min(g, cap));
+  return dim3((unsigned)std::max<long long>(1, std::min(g, cap)), (unsigned)groups, 1);
 }
 
 }  // namespace
@@ -224,8 +227,7 @@ extern "C" inpc_status inpc_query_hashgrid(const inpc_hashgrid_desc* g, const vo
   if (!aligned(table, ta) || !aligned(h_out, oa) || !aligned(pos, 4))
     return fail(INPC_ERR_INVALID_ARG, "inpc_query_hashgrid: misaligned table/output/pos");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const long long work = (long long)n * P.n_levels;
-  const unsigned grid = grid_for(work, 256);
+  const dim3 grid = grid_for(n, P.n_levels, 256);
   if (g->table_dtype == INPC_F32 && g->out_dtype == INPC_F32)
     k_hash_fwd<float, float><<<grid, 256, 0, s>>>(P, (const float*)table, pos, n, (float*)h_out);
   else if (g->table_dtype == INPC_F32)
@@ -249,7 +251,6 @@ extern "C" inpc_status inpc_query_hashgrid_bwd(const inpc_hashgrid_desc* g, cons
   if (!aligned(grad_table, 16) || !aligned(dh, 16) || !aligned(pos, 4))
     return fail(INPC_ERR_INVALID_ARG, "inpc_query_hashgrid_bwd: misaligned buffer");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const long long work = (long long)n * P.n_levels;
-  k_hash_bwd<<<grid_for(work, 256), 256, 0, s>>>(P, pos, dh, n, grad_table);
+  k_hash_bwd<<<grid_for(n, P.n_levels, 256), 256, 0, s>>>(P, pos, dh, n, grad_table);
   return check_launch("k_hash_bwd");
 }

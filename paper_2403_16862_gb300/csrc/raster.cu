@@ -1,30 +1,35 @@
 // raster.cu -- differentiable bilinear point rasterizer (Sec. 3.4, Eq. 1,
 // Eq. 5, Eq. 6, App. A.6, Algorithm 1), forward and backward.
 //
-// Algorithm 1's global "RadixSortPairs" over (pixel, depth) keys is replaced
-// by a two-level radix ordering:
-//   1. k_bin_count / k_scan_tiles / k_bin_scatter: a counting sort of the
-//      fragments by screen tile (the most significant digit).  Each point's
-//      fragments in one tile land in consecutive slots (point-grouped).
-//      Fragment record: 64-bit key = pixel-in-tile (8 bits) | FP32 depth
-//      bits (31, depth > 0) | point index (25).
-//   2. per tile, one CTA orders its bucket by the remaining key bits:
-//      fast path -- the bucket fits in shared memory: counting sort by
-//      pixel, then an all-ascending bitonic network per pixel segment;
-//      fallback -- a stable 8-bit LSD radix sort of the bucket in global
-//      memory by the same CTA (digits that are constant in the bucket are
-//      skipped).  Both give the (pixel, depth, point) order exactly.
-// Blending runs in the same CTA: a group of GA lanes owns one pixel, each
-// lane V contiguous channels (float4 loads of the point's feature row).
-// The backward revisits each pixel's blended fragments back to front,
-// recovering T_k = T_{k+1} / (1 - alpha_k) from T_final, and stores two
-// scalars per fragment (T_k alpha_k and dL/dalpha_k) in shared memory; the
-// per-point gradient is then assembled from the point-grouped bucket order
-// with plain stores (atomics only for points whose footprint spans tiles).
+// Ordering.  Algorithm 1 sorts all splats globally by (pixel, depth).  Here
+// the pixel is the most significant radix digit and is handled by a
+// counting sort into per-pixel buckets (k_pix_count, prefix sum,
+// k_pix_scatter); each bucket is then ordered by the remaining key
+// (FP32 depth bits << 25 | point index) in shared memory by the lanes that
+// blend it: a group of GA lanes per pixel for buckets of at most CG
+// fragments, a whole CTA (bitonic network in shared memory) for larger ones,
+// and a stable LSD radix sort in global memory beyond the shared-memory
+// capacity.  Every path yields the exact (depth, point) order.
+//
+// Blending.  alpha_k needs only the fragment's own point, so it is computed
+// for GA fragments at once; the transmittance T_k = prod_{j<k} (1 - alpha_j)
+// is a product scan across lanes, the stopping fragment (first with
+// T_{k+1} < t_min) comes from a ballot, and the color sum_k T_k alpha_k c_k is
+// an independent gather-reduce over the fragments' feature rows (V channels
+// per lane, float4 loads), so no dependent load chain limits a pixel.
+//
+// Backward.  Per pixel, T_k is recomputed by the forward's own scan (same
+// rounding, no per-fragment storage between the passes) and the suffix
+// sums S_k = sum_{j>k} T_j alpha_j (c_j . g) run back to front, chunk by
+// chunk.  Each fragment's two scalars (T_k alpha_k, dL/dalpha_k) go to its
+// bucket slot; a per-point kernel then gathers its (at most four) slots and
+// the matching upstream-gradient rows and writes the point's gradient with
+// plain stores -- no atomics, no zero-fill pass.
 #include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
+#include "scan.cuh"
 
 namespace inpc {
 namespace {
@@ -33,8 +38,9 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kIdBits = 25;
 constexpr unsigned long long kIdMask = (1ull << kIdBits) - 1;
-constexpr int kCapFwd = 8192;  // fragments per tile on the shared-memory path (forward)
-constexpr int kCapBwd = 4096;  // ... (backward: key + index + two scalars per fragment)
+constexpr int kGroupKeys = 8192;   // shared-memory keys per CTA on the group path (split among groups)
+constexpr int kHeavyKeys = 16384;  // shared-memory keys of the CTA path
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 
 struct RP {
   Cam cam;
@@ -43,36 +49,43 @@ struct RP {
   int head;
   float t_min, alpha_max;
   long long n;
+  long long n_pix;
 };
 
 struct RasterWs {
   uint32_t* status;
-  uint32_t* tile_count;   // [n_tiles]
-  uint32_t* tile_offset;  // [n_tiles + 1]
-  uint32_t* tile_cursor;  // [n_tiles]
-  unsigned long long* keys;  // [4n] binned fragments
-  unsigned long long* ka;    // [4n] per-tile sorted keys (fallback path)
-  uint32_t* va;              // [4n] their bucket positions
-  unsigned long long* kb;    // [4n] scratch
-  uint32_t* vb;              // [4n] scratch
-  float2* fscal;             // [4n] backward per-fragment scalars (fallback path)
+  uint32_t* heavy_count;  // header word 1
+  uint32_t* pix_count;    // [n_pix]
+  uint32_t* pix_start;    // [n_pix + 1]
+  uint32_t* tops;         // prefix-sum block totals
+  uint32_t* heavy;        // [n_pix] pixels on the CTA path
+  unsigned long long* keys;  // [4n] bucketed fragment keys
+  uint32_t* pslot;        // [4n] bucket slot of each point corner (kNoSlot off-image)
+  float2* fscal;          // [4n] backward per-fragment scalars
+  unsigned long long* ka;    // [4n] global-sort result (largest buckets only)
+  uint32_t* va;
+  unsigned long long* kb;    // [4n] global-sort scratch
+  uint32_t* vb;
   size_t bytes;
 };
 
-RasterWs carve(void* base, int n_tiles, long long n) {
+RasterWs carve(void* base, long long n_pix, long long n) {
   Carver c(base);
   RasterWs w;
   w.status = reinterpret_cast<uint32_t*>(base);
+  w.heavy_count = base ? reinterpret_cast<uint32_t*>(base) + 1 : nullptr;
   const long long nf = std::max<long long>(4 * n, 1);
-  w.tile_count = c.take<uint32_t>(n_tiles);
-  w.tile_offset = c.take<uint32_t>(n_tiles + 1);
-  w.tile_cursor = c.take<uint32_t>(n_tiles);
+  w.pix_count = c.take<uint32_t>(n_pix);
+  w.pix_start = c.take<uint32_t>(n_pix + 1);
+  w.tops = c.take<uint32_t>(scan::n_tops(n_pix));
+  w.heavy = c.take<uint32_t>(n_pix);
   w.keys = c.take<unsigned long long>(nf);
+  w.pslot = c.take<uint32_t>(nf);
+  w.fscal = c.take<float2>(nf);
   w.ka = c.take<unsigned long long>(nf);
   w.va = c.take<uint32_t>(nf);
   w.kb = c.take<unsigned long long>(nf);
   w.vb = c.take<uint32_t>(nf);
-  w.fscal = c.take<float2>(nf);
   w.bytes = c.bytes();
   return w;
 }
@@ -90,12 +103,12 @@ __device__ __forceinline__ bool splat_point(const RP& P, const float* __restrict
   return footprint(P.cam, u, v, s.f);
 }
 
-// Tile of corner k (= a + 2b) of a footprint, or -1 if the pixel is off-image.
-__device__ __forceinline__ int corner_tile(const RP& P, const Footprint& f, int k, int& px, int& py) {
-  px = f.i0 + (k & 1);
-  py = f.j0 + (k >> 1);
+// Pixel of corner k (= a + 2b) of a footprint, or -1 if off-image.
+__device__ __forceinline__ long long corner_pixel(const RP& P, const Footprint& f, int k) {
+  const int px = f.i0 + (k & 1);
+  const int py = f.j0 + (k >> 1);
   if (px < 0 || px >= P.cam.W || py < 0 || py >= P.cam.H) return -1;
-  return (py / P.TH) * P.tiles_x + (px / P.TW);
+  return (long long)py * P.cam.W + px;
 }
 
 __device__ __forceinline__ float point_alpha_h(const RP& P, const float* __restrict__ opacity,
@@ -108,146 +121,144 @@ __device__ __forceinline__ float point_alpha_h(const RP& P, const float* __restr
   return __ldg(opacity + id);
 }
 
-__device__ __forceinline__ float splat_alpha(const RP& P, float ah, float w) {
-  return fminf(__fmul_rn(ah, w), P.alpha_max);
+// alpha of the fragment of point `id` at pixel (px, py) (Eq. 6 with the clamp).
+__device__ __forceinline__ float frag_alpha(const RP& P, const float* __restrict__ pos,
+                                            const float* __restrict__ opacity, const float* __restrict__ feat,
+                                            long long id, int px, int py) {
+  Splat s;
+  splat_point(P, pos, id, s);
+  const float w = corner_weight(s.f, px - s.f.i0, py - s.f.j0);
+  return fminf(__fmul_rn(point_alpha_h(P, opacity, feat, id, nullptr), w), P.alpha_max);
 }
 
 // ---------------------------------------------------------------- binning ---
-__global__ void __launch_bounds__(256) k_bin_count(RP P, const float* __restrict__ pos, uint32_t* tile_count) {
+// Per-point corner pixels (or -1).
+__device__ __forceinline__ void point_pixels(const RP& P, const float* __restrict__ pos, long long id,
+                                             long long q[4], float& d) {
+  Splat s;
+  q[0] = q[1] = q[2] = q[3] = -1;
+  d = 0.f;
+  if (id < P.n && splat_point(P, pos, id, s)) {
+    d = s.d;
+    for (int k = 0; k < 4; ++k) q[k] = corner_pixel(P, s.f, k);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_pix_count(RP P, const float* __restrict__ pos,
+                                                   uint32_t* __restrict__ pix_count) {
   const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   for (long long base = blockIdx.x * (long long)blockDim.x; base < P.n; base += (long long)gridDim.x * blockDim.x) {
-    const long long id = base + threadIdx.x;
-    int tile[4] = {-1, -1, -1, -1};
-    Splat s;
-    if (id < P.n && splat_point(P, pos, id, s)) {
-      for (int k = 0; k < 4; ++k) {
-        int px, py;
-        tile[k] = corner_tile(P, s.f, k, px, py);
-      }
-    }
-    // distinct tiles of this point with their corner counts; warp-aggregate
+    long long q[4];
+    float d;
+    point_pixels(P, pos, base + threadIdx.x, q, d);
     for (int k = 0; k < 4; ++k) {
-      int t = tile[k];
-      uint32_t cnt = 0;
-      if (t >= 0) {
-        bool first = true;
-        for (int q = 0; q < k; ++q) first &= (tile[q] != t);
-        if (first)
-          for (int q = k; q < 4; ++q) cnt += (tile[q] == t);
-        else
-          t = -1;
-      }
-      const unsigned peers = __match_any_sync(full, t);
-      const uint32_t sum = __reduce_add_sync(peers, cnt);
-      if (t >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(tile_count + t, sum);
+      // leaf-grouped points are spatially coherent: aggregate equal pixels per warp
+      const unsigned peers = __match_any_sync(full, q[k]);
+      if (q[k] >= 0 && lane == __ffs(peers) - 1) atomicAdd(pix_count + q[k], (uint32_t)__popc(peers));
     }
   }
 }
 
-__global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t* __restrict__ cnt, int n_tiles,
-                                                     uint32_t* __restrict__ offset, uint32_t* __restrict__ cursor) {
-  __shared__ uint32_t warp_sums[32];
-  __shared__ uint32_t chunk_total;
-  uint32_t carry = 0;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int b0 = 0; b0 < n_tiles; b0 += 1024) {
-    const int i = b0 + threadIdx.x;
-    const uint32_t v = i < n_tiles ? cnt[i] : 0u;
-    uint32_t incl = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    if (lane == 31) warp_sums[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-      const uint32_t s = warp_sums[lane];
-      uint32_t si = s;
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, si, o);
-        if (lane >= o) si += t;
-      }
-      warp_sums[lane] = si - s;
-      if (lane == 31) chunk_total = si;
-    }
-    __syncthreads();
-    if (i < n_tiles) {
-      offset[i] = carry + warp_sums[wid] + incl - v;
-      cursor[i] = 0;
-    }
-    carry += chunk_total;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) offset[n_tiles] = carry;
-}
-
-__global__ void __launch_bounds__(256) k_bin_scatter(RP P, const float* __restrict__ pos,
-                                                     const uint32_t* __restrict__ tile_offset,
-                                                     uint32_t* __restrict__ tile_cursor,
-                                                     unsigned long long* __restrict__ keys) {
+__global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restrict__ pos,
+                                                     const uint32_t* __restrict__ pix_start,
+                                                     uint32_t* __restrict__ pix_count,
+                                                     unsigned long long* __restrict__ keys,
+                                                     uint32_t* __restrict__ pslot) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   for (long long base = blockIdx.x * (long long)blockDim.x; base < P.n; base += (long long)gridDim.x * blockDim.x) {
     const long long id = base + threadIdx.x;
-    int tile[4] = {-1, -1, -1, -1};
-    int pix[4] = {0, 0, 0, 0};
-    Splat s;
-    s.d = 0.f;
-    if (id < P.n && splat_point(P, pos, id, s)) {
-      for (int k = 0; k < 4; ++k) {
-        int px, py;
-        tile[k] = corner_tile(P, s.f, k, px, py);
-        pix[k] = (py % P.TH) * P.TW + (px % P.TW);
+    long long q[4];
+    float d;
+    point_pixels(P, pos, id, q, d);
+    const unsigned long long key = ((unsigned long long)__float_as_uint(d) << kIdBits) | (unsigned long long)id;
+    uint32_t slots[4];
+    for (int k = 0; k < 4; ++k) {
+      const unsigned peers = __match_any_sync(full, q[k]);
+      const int leader = __ffs(peers) - 1;
+      uint32_t top = 0;
+      // counts run down from the bucket size, so the buckets fill back to front
+      if (q[k] >= 0 && lane == leader) top = atomicSub(pix_count + q[k], (uint32_t)__popc(peers));
+      top = __shfl_sync(peers, top, leader);
+      slots[k] = kNoSlot;
+      if (q[k] >= 0) {
+        const uint32_t local = top - 1 - __popc(peers & ((1u << lane) - 1));
+        slots[k] = pix_start[q[k]] + local;
+        keys[slots[k]] = key;
       }
     }
-    const unsigned long long hi = ((unsigned long long)__float_as_uint(s.d) << kIdBits) | (unsigned long long)id;
-    for (int k = 0; k < 4; ++k) {
-      int t = tile[k];
-      uint32_t cnt = 0;
-      if (t >= 0) {
-        bool first = true;
-        for (int q = 0; q < k; ++q) first &= (tile[q] != t);
-        if (first)
-          for (int q = k; q < 4; ++q) cnt += (tile[q] == t);
-        else
-          t = -1;
+    if (id < P.n) reinterpret_cast<uint4*>(pslot)[id] = make_uint4(slots[0], slots[1], slots[2], slots[3]);
+  }
+}
+
+struct CountLoad {
+  const uint32_t* c;
+  __device__ uint32_t operator()(int64_t i) const { return c[i]; }
+};
+
+// Pixels whose bucket exceeds the group capacity go to the CTA path.
+__global__ void k_heavy_list(const uint32_t* __restrict__ pix_start, long long n_pix, const uint32_t* __restrict__ tops,
+                             long long nb, uint32_t cap, uint32_t* __restrict__ heavy, uint32_t* heavy_count,
+                             uint32_t* __restrict__ pix_start_w) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q == 0) pix_start_w[n_pix] = tops[nb];
+  if (q >= n_pix) return;
+  const uint32_t end = q + 1 < n_pix ? pix_start[q + 1] : tops[nb];
+  if (end - pix_start[q] > cap) heavy[atomicAdd(heavy_count, 1u)] = (uint32_t)q;
+}
+
+// ------------------------------------------------------------- ordering ---
+// Ascending sort of idx[0..m) by K[idx[.]] with an all-ascending bitonic
+// network (every comparator puts the minimum at the lower index), so the
+// virtual +infinity padding beyond m is never touched.  `lg`/`nl`: this
+// thread's index and the number of cooperating threads; `sync` orders them.
+template <class Sync>
+__device__ void bitonic_sort_idx(const unsigned long long* K, uint16_t* idx, int m, int lg, int nl, Sync sync) {
+  if (m < 2) return;
+  int P2 = 1;
+  while (P2 < m) P2 <<= 1;
+  for (int k = 2; k <= P2; k <<= 1) {
+    const int half = k >> 1;
+    for (int q = lg; q < (P2 >> 1); q += nl) {
+      const int i = (q / half) * k + (q % half);
+      const int j = i ^ (k - 1);
+      if (j < m) {
+        const uint16_t a = idx[i], b = idx[j];
+        if (K[a] > K[b]) {
+          idx[i] = b;
+          idx[j] = a;
+        }
       }
-      const unsigned peers = __match_any_sync(full, t);
-      // exclusive prefix of cnt among the peers (lane order), one atomic per group
-      uint32_t pre = 0, sum = 0;
-      for (unsigned m = peers; m; m &= m - 1) {
-        const int src = __ffs(m) - 1;
-        const uint32_t c = __shfl_sync(peers, cnt, src);
-        if (src < lane) pre += c;
-        sum += c;
+    }
+    sync();
+    for (int jj = k >> 2; jj >= 1; jj >>= 1) {
+      for (int q = lg; q < (P2 >> 1); q += nl) {
+        const int i = (q / jj) * (2 * jj) + (q % jj);
+        const int j = i + jj;
+        if (j < m) {
+          const uint16_t a = idx[i], b = idx[j];
+          if (K[a] > K[b]) {
+            idx[i] = b;
+            idx[j] = a;
+          }
+        }
       }
-      const int leader = __ffs(peers) - 1;
-      uint32_t slot = 0;
-      if (t >= 0 && lane == leader) slot = atomicAdd(tile_cursor + t, sum);
-      slot = __shfl_sync(peers, slot, leader);
-      if (t >= 0) {
-        unsigned long long* dst = keys + tile_offset[t] + slot + pre;
-        int w = 0;
-        for (int q = k; q < 4; ++q)
-          if (tile[q] == t) dst[w++] = ((unsigned long long)pix[q] << 56) | hi;
-      }
+      sync();
     }
   }
 }
 
-// ------------------------------------------------------- tile ordering ---
-struct TileSmem {
-  uint32_t pixcnt[256];
-  uint32_t pixbeg[257];
-  uint32_t pixcur[256];
-  uint16_t wcnt[kWarps][256];
+struct SortSmem {
+  uint32_t hist[256];
   uint32_t dbase[256];
   uint32_t ctot[256];
+  uint16_t wcnt[kWarps][256];
   unsigned long long red64[kWarps];
+  uint32_t warp_sums[32];
 };
 
-// Exclusive scan of 256 values (one per thread of a 256-thread CTA).
-__device__ __forceinline__ uint32_t cta_excl_scan256(uint32_t v, uint32_t* warp_sums, uint32_t* total) {
+__device__ __forceinline__ uint32_t cta_excl_scan256(uint32_t v, uint32_t* warp_sums) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t incl = v;
   for (int o = 1; o < 32; o <<= 1) {
@@ -264,30 +275,16 @@ __device__ __forceinline__ uint32_t cta_excl_scan256(uint32_t v, uint32_t* warp_
       warp_sums[w] = run;
       run += t;
     }
-    if (total) *total = run;
   }
   __syncthreads();
   return warp_sums[wid] + incl - v;
 }
 
-// Per-pixel segments of a key sequence sorted or bucketed by the pixel byte.
-template <class KeyAt>
-__device__ void pixel_segments(KeyAt key_at, int n, TileSmem& S) {
-  S.pixcnt[threadIdx.x] = 0;
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += kThreads) atomicAdd(&S.pixcnt[(int)(key_at(i) >> 56)], 1u);
-  __syncthreads();
-  const uint32_t ex = cta_excl_scan256(S.pixcnt[threadIdx.x], S.ctot, nullptr);
-  S.pixbeg[threadIdx.x] = ex;
-  S.pixcur[threadIdx.x] = ex;
-  if (threadIdx.x == kThreads - 1) S.pixbeg[256] = ex + S.pixcnt[kThreads - 1];
-  __syncthreads();
-}
-
-// Stable 8-bit LSD radix sort of one tile's bucket in global memory by one
-// CTA: in[0..n) -> ka (keys), va (bucket positions); kb/vb are scratch.
+// Stable 8-bit LSD radix sort of one bucket in global memory by one CTA:
+// in[0..n) -> ka (keys), va (positions within the bucket); kb/vb scratch.
+// Digits that are equal across the bucket are skipped.
 __device__ void cta_sort_global(const unsigned long long* __restrict__ in, int n, unsigned long long* ka,
-                                uint32_t* va, unsigned long long* kb, uint32_t* vb, TileSmem& S) {
+                                uint32_t* va, unsigned long long* kb, uint32_t* vb, SortSmem& S) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned long long k0 = in[0];
   unsigned long long diff = 0;
@@ -310,11 +307,11 @@ __device__ void cta_sort_global(const unsigned long long* __restrict__ in, int n
     uint32_t* sv = in_a ? va : vb;
     unsigned long long* dk = in_a ? kb : ka;
     uint32_t* dv = in_a ? vb : va;
-    S.pixcnt[threadIdx.x] = 0;
+    S.hist[threadIdx.x] = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += kThreads) atomicAdd(&S.pixcnt[(int)((sk[i] >> sh) & 0xFF)], 1u);
+    for (int i = threadIdx.x; i < n; i += kThreads) atomicAdd(&S.hist[(int)((sk[i] >> sh) & 0xFF)], 1u);
     __syncthreads();
-    S.dbase[threadIdx.x] = cta_excl_scan256(S.pixcnt[threadIdx.x], S.ctot, nullptr);
+    S.dbase[threadIdx.x] = cta_excl_scan256(S.hist[threadIdx.x], S.warp_sums);
     __syncthreads();
     for (int c0 = 0; c0 < n; c0 += kThreads) {
       const int i = c0 + threadIdx.x;
@@ -363,49 +360,58 @@ __device__ void cta_sort_global(const unsigned long long* __restrict__ in, int n
   __syncthreads();
 }
 
+// ---------------------------------------------------------- lane groups ---
 template <int GA>
-__device__ __forceinline__ void gsync(unsigned mask) {
-  if (GA > 1) __syncwarp(mask);
-}
-
-// Ascending sort of the index segment idx[0..m) by key K[idx[.]] with an
-// all-ascending bitonic network (every comparator puts the minimum at the
-// lower index), so indices >= m act as +infinity and are never touched.
-template <int GA>
-__device__ void group_sort(const unsigned long long* K, uint16_t* idx, int m, int lg, unsigned gmask) {
-  if (m < 2) return;
-  int P = 1;
-  while (P < m) P <<= 1;
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int q = lg; q < (P >> 1); q += GA) {
-      const int half = k >> 1;
-      const int i = (q / half) * k + (q % half);
-      const int j = i ^ (k - 1);
-      if (j < m) {
-        const uint16_t a = idx[i], b = idx[j];
-        if (K[a] > K[b]) {
-          idx[i] = b;
-          idx[j] = a;
-        }
-      }
-    }
-    gsync<GA>(gmask);
-    for (int jj = k >> 2; jj >= 1; jj >>= 1) {
-      for (int q = lg; q < (P >> 1); q += GA) {
-        const int i = (q / jj) * (2 * jj) + (q % jj);
-        const int j = i + jj;
-        if (j < m) {
-          const uint16_t a = idx[i], b = idx[j];
-          if (K[a] > K[b]) {
-            idx[i] = b;
-            idx[j] = a;
-          }
-        }
-      }
-      gsync<GA>(gmask);
-    }
+struct Group {
+  int lg;          // lane within the group
+  int base_lane;   // first lane of the group within its warp
+  unsigned mask;   // the group's lanes
+  __device__ Group() {
+    const int lane = threadIdx.x & 31;
+    lg = lane % GA;
+    base_lane = lane - lg;
+    mask = GA == 32 ? 0xffffffffu : (((1u << GA) - 1u) << base_lane);
   }
-}
+  __device__ void sync() const {
+    if (GA > 1) __syncwarp(mask);
+  }
+  template <class T>
+  __device__ T bcast(T v, int src) const {
+    return GA > 1 ? __shfl_sync(mask, v, src, GA) : v;
+  }
+  __device__ float sum(float x) const {
+#pragma unroll
+    for (int o = GA / 2; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o, GA);
+    return x;
+  }
+  // Inclusive product scan over the group's lanes.
+  __device__ float prod_scan(float x) const {
+#pragma unroll
+    for (int o = 1; o < GA; o <<= 1) {
+      const float t = __shfl_up_sync(mask, x, o, GA);
+      if (lg >= o) x = __fmul_rn(x, t);
+    }
+    return x;
+  }
+  // Inclusive suffix-sum scan over the group's lanes (lane j gets sum_{i>=j}).
+  __device__ float suffix_scan(float x) const {
+#pragma unroll
+    for (int o = 1; o < GA; o <<= 1) {
+      const float t = __shfl_down_sync(mask, x, o, GA);
+      if (lg + o < GA) x += t;
+    }
+    return x;
+  }
+  // Value of the next lane of the group (0 for the last lane).
+  __device__ float shift_down(float x) const {
+    if (GA == 1) return 0.f;
+    const float t = __shfl_down_sync(mask, x, 1, GA);
+    return lg + 1 < GA ? t : 0.f;
+  }
+  __device__ unsigned ballot(bool p) const {
+    return (__ballot_sync(mask, p) >> base_lane) & (GA == 32 ? 0xffffffffu : ((1u << GA) - 1u));
+  }
+};
 
 template <int V>
 __device__ __forceinline__ void load_vec(const float* __restrict__ p, float* c) {
@@ -418,45 +424,75 @@ __device__ __forceinline__ void load_vec(const float* __restrict__ p, float* c) 
   }
 }
 
+// Transmittance bookkeeping of one chunk of GA fragments [b, b + GA) of a
+// pixel: lane j holds fragment b + j.  Returns the number of fragments of the
+// chunk that are blended (the stopping fragment included) and sets `stop`.
 template <int GA>
-__device__ __forceinline__ float group_sum(float x, unsigned gmask) {
-#pragma unroll
-  for (int o = GA / 2; o > 0; o >>= 1) x += __shfl_xor_sync(gmask, x, o);
-  return x;
+struct ChunkT {
+  float a;      // alpha of this lane's fragment (0 beyond the list)
+  float Tk;     // transmittance in front of it
+  float Tn;     // transmittance behind it
+  int take;     // fragments of the chunk that are blended
+  bool stop;
+};
+
+template <int GA, class KeyAt>
+__device__ __forceinline__ ChunkT<GA> chunk_transmittance(const Group<GA>& G, const RP& P, KeyAt key_at, int b, int m,
+                                                          float T, int px, int py, const float* __restrict__ pos,
+                                                          const float* __restrict__ opacity,
+                                                          const float* __restrict__ feat, long long& id) {
+  ChunkT<GA> r;
+  const int k = b + G.lg;
+  r.a = 0.f;
+  id = 0;
+  if (k < m) {
+    id = (long long)(key_at(k) & kIdMask);
+    r.a = frag_alpha(P, pos, opacity, feat, id, px, py);
+  }
+  const float incl = G.prod_scan(__fsub_rn(1.0f, r.a));
+  float excl = G.bcast(incl, G.lg > 0 ? G.lg - 1 : 0);
+  if (G.lg == 0) excl = 1.0f;
+  r.Tk = __fmul_rn(T, excl);
+  r.Tn = __fmul_rn(T, incl);
+  const unsigned st = G.ballot(k < m && r.Tn < P.t_min);
+  const int avail = min(GA, m - b);
+  r.stop = st != 0;
+  r.take = r.stop ? __ffs(st) : avail;
+  return r;
 }
 
 // ------------------------------------------------------------- forward ---
 template <int V, int GA, class KeyAt>
-__device__ void blend_fwd(const RP& P, KeyAt key_at, int m, int px, int py, const float* __restrict__ pos,
-                          const float* __restrict__ opacity, const float* __restrict__ feat,
-                          float* __restrict__ image, float* __restrict__ T_final, int32_t* __restrict__ n_contrib,
-                          int lg) {
-  const int ch = lg * V;
+__device__ void blend_fwd(const Group<GA>& G, const RP& P, KeyAt key_at, int m, int px, int py,
+                          const float* __restrict__ pos, const float* __restrict__ opacity,
+                          const float* __restrict__ feat, float* __restrict__ image, float* __restrict__ T_final,
+                          int32_t* __restrict__ n_contrib) {
+  const int ch = G.lg * V;
   const bool active = ch < P.F;
-  float T = 1.0f;
   float C[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) C[v] = 0.f;
+  float T = 1.0f;
   int cnt = 0;
-  for (int k = 0; k < m; ++k) {
-    const unsigned long long key = key_at(k);
-    const long long id = (long long)(key & kIdMask);
-    Splat s;
-    splat_point(P, pos, id, s);
-    const float w = corner_weight(s.f, px - s.f.i0, py - s.f.j0);
-    const float a = splat_alpha(P, point_alpha_h(P, opacity, feat, id, nullptr), w);
-    float c[V];
-    if (active) load_vec<V>(feat + (long long)P.F * id + ch, c);
-    else
+  for (int b = 0; b < m; b += GA) {
+    long long id;
+    const ChunkT<GA> r = chunk_transmittance<GA>(G, P, key_at, b, m, T, px, py, pos, opacity, feat, id);
+    const float wk = __fmul_rn(r.Tk, r.a);
+#pragma unroll 4
+    for (int j = 0; j < r.take; ++j) {
+      const long long idj = G.bcast(id, j);
+      const float wj = G.bcast(wk, j);
+      if (active) {
+        float c[V];
+        load_vec<V>(feat + (long long)P.F * idj + ch, c);
+        if (P.head && G.lg == 0) c[0] = 1.0f;
 #pragma unroll
-      for (int v = 0; v < V; ++v) c[v] = 0.f;
-    if (P.head && lg == 0) c[0] = 1.0f;
-    const float ta = __fmul_rn(T, a);
-#pragma unroll
-    for (int v = 0; v < V; ++v) C[v] = __fmaf_rn(ta, c[v], C[v]);
-    T = __fmul_rn(T, __fsub_rn(1.0f, a));
-    ++cnt;
-    if (T < P.t_min) break;
+        for (int v = 0; v < V; ++v) C[v] = __fmaf_rn(wj, c[v], C[v]);
+      }
+    }
+    cnt += r.take;
+    T = G.bcast(r.Tn, r.take - 1);
+    if (r.stop) break;
   }
   const long long pix = (long long)py * P.cam.W + px;
   if (active) {
@@ -466,275 +502,281 @@ __device__ void blend_fwd(const RP& P, KeyAt key_at, int m, int px, int py, cons
 #pragma unroll
       for (int v = 0; v < V; ++v) __stcs(o + v, C[v]);
   }
-  if (lg == 0) {
+  if (G.lg == 0) {
     T_final[pix] = T;
     n_contrib[pix] = cnt;
   }
 }
 
 template <int V, int GA>
-__global__ void __launch_bounds__(kThreads) k_raster_fwd(RP P, const float* __restrict__ pos,
-                                                          const float* __restrict__ opacity,
-                                                          const float* __restrict__ feat, RasterWs ws,
-                                                          float* __restrict__ image, float* __restrict__ T_final,
-                                                          int32_t* __restrict__ n_contrib) {
+__global__ void __launch_bounds__(kThreads) k_blend_fwd(RP P, const float* __restrict__ pos,
+                                                         const float* __restrict__ opacity,
+                                                         const float* __restrict__ feat, RasterWs ws,
+                                                         float* __restrict__ image, float* __restrict__ T_final,
+                                                         int32_t* __restrict__ n_contrib) {
+  constexpr int kGroups = kThreads / GA;
+  constexpr int CG = kGroupKeys / kGroups;
   extern __shared__ __align__(16) unsigned char dyn[];
-  __shared__ TileSmem S;
+  const Group<GA> G;
+  const int group = threadIdx.x / GA;
+  unsigned long long* K = reinterpret_cast<unsigned long long*>(dyn) + group * CG;
+  uint16_t* idx = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned long long*>(dyn) + kGroupKeys) + group * CG;
   const int t = blockIdx.x;
   const int tx = t % P.tiles_x, ty = t / P.tiles_x;
-  const int n_t = (int)ws.tile_count[t];
-  const uint32_t base = ws.tile_offset[t];
-  const int lane = threadIdx.x & 31;
-  const int lg = lane % GA;
-  const int group = threadIdx.x / GA;
-  constexpr int kGroups = kThreads / GA;
-  const unsigned gmask = GA == 32 ? 0xffffffffu : (((1u << GA) - 1u) << (lane - lg));
-  const int npix = P.TW * P.TH;
-  if (n_t <= kCapFwd) {
-    unsigned long long* K = reinterpret_cast<unsigned long long*>(dyn);
-    uint16_t* idx = reinterpret_cast<uint16_t*>(K + kCapFwd);
-    for (int i = threadIdx.x; i < n_t; i += kThreads) K[i] = ws.keys[base + i];
-    __syncthreads();
-    pixel_segments([&](int i) { return K[i]; }, n_t, S);
-    for (int i = threadIdx.x; i < n_t; i += kThreads) {
-      const uint32_t dst = atomicAdd(&S.pixcur[(int)(K[i] >> 56)], 1u);
-      idx[dst] = (uint16_t)i;
+  for (int p = group; p < P.TW * P.TH; p += kGroups) {
+    const int px = tx * P.TW + p % P.TW, py = ty * P.TH + p / P.TW;
+    if (px >= P.cam.W || py >= P.cam.H) continue;
+    const long long q = (long long)py * P.cam.W + px;
+    const uint32_t s0 = ws.pix_start[q];
+    const int m = (int)(ws.pix_start[q + 1] - s0);
+    if (m > CG) continue;  // CTA path
+    for (int j = G.lg; j < m; j += GA) {
+      K[j] = ws.keys[s0 + j];
+      idx[j] = (uint16_t)j;
+    }
+    G.sync();
+    bitonic_sort_idx(K, idx, m, G.lg, GA, [&] { G.sync(); });
+    blend_fwd<V, GA>(G, P, [&](int k) { return K[idx[k]]; }, m, px, py, pos, opacity, feat, image, T_final,
+                     n_contrib);
+    G.sync();
+  }
+}
+
+template <int V, int GA>
+__global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const float* __restrict__ pos,
+                                                               const float* __restrict__ opacity,
+                                                               const float* __restrict__ feat, RasterWs ws,
+                                                               float* __restrict__ image, float* __restrict__ T_final,
+                                                               int32_t* __restrict__ n_contrib) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ SortSmem S;
+  unsigned long long* K = reinterpret_cast<unsigned long long*>(dyn);
+  uint16_t* idx = reinterpret_cast<uint16_t*>(K + kHeavyKeys);
+  const Group<GA> G;
+  const uint32_t n_heavy = *ws.heavy_count;
+  for (uint32_t h = blockIdx.x; h < n_heavy; h += gridDim.x) {
+    const long long q = ws.heavy[h];
+    const int px = (int)(q % P.cam.W), py = (int)(q / P.cam.W);
+    const uint32_t s0 = ws.pix_start[q];
+    const int m = (int)(ws.pix_start[q + 1] - s0);
+    if (m <= kHeavyKeys) {
+      for (int j = threadIdx.x; j < m; j += kThreads) {
+        K[j] = ws.keys[s0 + j];
+        idx[j] = (uint16_t)j;
+      }
+      __syncthreads();
+      bitonic_sort_idx(K, idx, m, threadIdx.x, kThreads, [] { __syncthreads(); });
+      if (threadIdx.x < GA)
+        blend_fwd<V, GA>(G, P, [&](int k) { return K[idx[k]]; }, m, px, py, pos, opacity, feat, image, T_final,
+                         n_contrib);
+    } else {
+      unsigned long long* ka = ws.ka + s0;
+      cta_sort_global(ws.keys + s0, m, ka, ws.va + s0, ws.kb + s0, ws.vb + s0, S);
+      if (threadIdx.x < GA)
+        blend_fwd<V, GA>(G, P, [&](int k) { return ka[k]; }, m, px, py, pos, opacity, feat, image, T_final,
+                         n_contrib);
     }
     __syncthreads();
-    for (int p = group; p < npix; p += kGroups) {
-      const int px = tx * P.TW + p % P.TW, py = ty * P.TH + p / P.TW;
-      if (px >= P.cam.W || py >= P.cam.H) continue;
-      const int b = (int)S.pixbeg[p], m = (int)(S.pixbeg[p + 1] - S.pixbeg[p]);
-      group_sort<GA>(K, idx + b, m, lg, gmask);
-      blend_fwd<V, GA>(P, [&](int k) { return K[idx[b + k]]; }, m, px, py, pos, opacity, feat, image, T_final,
-                       n_contrib, lg);
-    }
-  } else {
-    unsigned long long* ka = ws.ka + base;
-    cta_sort_global(ws.keys + base, n_t, ka, ws.va + base, ws.kb + base, ws.vb + base, S);
-    pixel_segments([&](int i) { return ka[i]; }, n_t, S);
-    for (int p = group; p < npix; p += kGroups) {
-      const int px = tx * P.TW + p % P.TW, py = ty * P.TH + p / P.TW;
-      if (px >= P.cam.W || py >= P.cam.H) continue;
-      const int b = (int)S.pixbeg[p], m = (int)(S.pixbeg[p + 1] - S.pixbeg[p]);
-      blend_fwd<V, GA>(P, [&](int k) { return ka[b + k]; }, m, px, py, pos, opacity, feat, image, T_final,
-                       n_contrib, lg);
-    }
   }
 }
 
 // ------------------------------------------------------------ backward ---
-// Phase 1: one pixel, back to front.  Writes (T_k alpha_k, dL/dalpha_k) for
-// each of its blended fragments at the fragment's bucket position.
-template <int V, int GA, class KeyAt, class PosAt, class ScalAt>
-__device__ void blend_bwd_pixel(const RP& P, KeyAt key_at, PosAt bucket_pos, ScalAt scal, int n_blend, int px,
-                                int py, const float* __restrict__ pos, const float* __restrict__ opacity,
-                                const float* __restrict__ feat, const float* __restrict__ T_final,
-                                const float* __restrict__ d_image, int lg, unsigned gmask) {
-  const int ch = lg * V;
+// One pixel: recompute alpha_k and T_k with the forward's chunked scan, then
+// walk the blended chunks back to front accumulating
+// S_k = sum_{j>k} T_j alpha_j (c_j . g) and write
+//   fscal[slot_k] = (T_k alpha_k, dL/dalpha_k = T_k (c_k . g) - S_k / (1 - alpha_k)).
+// chunkT[c] keeps the transmittance in front of chunk c between the passes.
+template <int V, int GA, class KeyAt, class SlotAt>
+__device__ void blend_bwd(const Group<GA>& G, const RP& P, KeyAt key_at, SlotAt slot_at, int m, int nb, int px,
+                          int py, const float* __restrict__ pos, const float* __restrict__ opacity,
+                          const float* __restrict__ feat, const float* __restrict__ d_image,
+                          float2* __restrict__ fscal, float* chunkT) {
+  const int ch = G.lg * V;
   const bool active = ch < P.F;
   const long long pix = (long long)py * P.cam.W + px;
+  // fragments behind the stopping point get zero scalars
+  for (int k = nb + G.lg; k < m; k += GA) fscal[slot_at(k)] = make_float2(0.f, 0.f);
+  if (nb == 0) return;
+  // pass 1: chunk-start transmittances
+  float T = 1.0f;
+  const int n_chunks = (nb + GA - 1) / GA;
+  for (int c = 0; c < n_chunks; ++c) {
+    if (G.lg == 0) chunkT[c] = T;
+    long long id;
+    const ChunkT<GA> r = chunk_transmittance<GA>(G, P, key_at, c * GA, nb, T, px, py, pos, opacity, feat, id);
+    T = G.bcast(r.Tn, r.take - 1);
+  }
+  G.sync();
   float g[V];
   if (active) load_vec<V>(d_image + pix * P.F + ch, g);
   else
 #pragma unroll
     for (int v = 0; v < V; ++v) g[v] = 0.f;
-  float T = T_final[pix];
+  // pass 2: back to front
   float S = 0.f;
-  for (int k = n_blend - 1; k >= 0; --k) {
-    const unsigned long long key = key_at(k);
-    const long long id = (long long)(key & kIdMask);
-    Splat s;
-    splat_point(P, pos, id, s);
-    const float w = corner_weight(s.f, px - s.f.i0, py - s.f.j0);
-    const float a = splat_alpha(P, point_alpha_h(P, opacity, feat, id, nullptr), w);
-    const float om = __fsub_rn(1.0f, a);
-    const float Tk = __fdiv_rn(T, om);
-    float c[V];
-    if (active) load_vec<V>(feat + (long long)P.F * id + ch, c);
-    else
+  for (int c = n_chunks - 1; c >= 0; --c) {
+    long long id;
+    const ChunkT<GA> r = chunk_transmittance<GA>(G, P, key_at, c * GA, nb, chunkT[c], px, py, pos, opacity, feat, id);
+    // c_k . g for each fragment of the chunk (rows spread over the lanes)
+    float mydot = 0.f;
+#pragma unroll 4
+    for (int j = 0; j < r.take; ++j) {
+      const long long idj = G.bcast(id, j);
+      float part = 0.f;
+      if (active) {
+        float cc[V];
+        load_vec<V>(feat + (long long)P.F * idj + ch, cc);
+        if (P.head && G.lg == 0) cc[0] = 1.0f;
 #pragma unroll
-      for (int v = 0; v < V; ++v) c[v] = 0.f;
-    if (P.head && lg == 0) c[0] = 1.0f;
-    float dot = 0.f;
-#pragma unroll
-    for (int v = 0; v < V; ++v) dot = __fmaf_rn(c[v], g[v], dot);
-    dot = group_sum<GA>(dot, gmask);
-    const float aw = __fmul_rn(Tk, a);
-    const float da = __fsub_rn(__fmul_rn(Tk, dot), __fdiv_rn(S, om));
-    S = __fmaf_rn(aw, dot, S);
-    T = Tk;
-    if (lg == 0) scal(bucket_pos(k)) = make_float2(aw, da);
-  }
-}
-
-// Phase 2: one point's fragments in this tile (consecutive bucket entries
-// [i, i + c)).  d_feat row = sum_k (T_k alpha_k) g_pixel(k); d alpha_h =
-// sum_k w_k [unclamped] dL/dalpha_k.
-template <int V, int GA, class KeyAt, class ScalAt>
-__device__ void point_grad(const RP& P, KeyAt key_at, ScalAt scal, int i, int c, int tx, int ty,
-                           const float* __restrict__ pos, const float* __restrict__ opacity,
-                           const float* __restrict__ feat, const float* __restrict__ d_image,
-                           float* __restrict__ d_opacity, float* __restrict__ d_feat, int lg) {
-  const int ch = lg * V;
-  const bool active = ch < P.F;
-  const long long id = (long long)(key_at(i) & kIdMask);
-  Splat s;
-  splat_point(P, pos, id, s);
-  int on_image = 0;
-  for (int k = 0; k < 4; ++k) {
-    int px, py;
-    on_image += corner_tile(P, s.f, k, px, py) >= 0;
-  }
-  const bool straddle = c < on_image;
-  float e_h0 = 0.f;
-  const float ah = point_alpha_h(P, opacity, feat, id, &e_h0);
-  float dc[V];
-#pragma unroll
-  for (int v = 0; v < V; ++v) dc[v] = 0.f;
-  float dah = 0.f;
-  for (int j = 0; j < c; ++j) {
-    const unsigned long long key = key_at(i + j);
-    const int p = (int)(key >> 56);
-    const int px = tx * P.TW + p % P.TW, py = ty * P.TH + p / P.TW;
-    const float2 sc = scal(i + j);
-    const float w = corner_weight(s.f, px - s.f.i0, py - s.f.j0);
-    if (__fmul_rn(ah, w) <= P.alpha_max) dah = __fmaf_rn(w, sc.y, dah);
-    if (active) {
-      float g[V];
-      load_vec<V>(d_image + ((long long)py * P.cam.W + px) * P.F + ch, g);
-#pragma unroll
-      for (int v = 0; v < V; ++v) dc[v] = __fmaf_rn(sc.x, g[v], dc[v]);
+        for (int v = 0; v < V; ++v) part = __fmaf_rn(cc[v], g[v], part);
+      }
+      const float dj = G.sum(part);
+      if (G.lg == j) mydot = dj;
     }
-  }
-  if (P.head && lg == 0) dc[0] = dah * e_h0 * (1.0f - ah);
-  if (active) {
-    float* o = d_feat + id * P.F + ch;
-    if (straddle) {
-#pragma unroll
-      for (int v = 0; v < V; ++v) atomicAdd(o + v, dc[v]);
-    } else if (V == 4) {
-      *reinterpret_cast<float4*>(o) = make_float4(dc[0], dc[1], dc[2], dc[3]);
-    } else {
-#pragma unroll
-      for (int v = 0; v < V; ++v) o[v] = dc[v];
-    }
-  }
-  if (!P.head && lg == 0) {
-    if (straddle) atomicAdd(d_opacity + id, dah);
-    else d_opacity[id] = dah;
+    const bool mine = G.lg < r.take;
+    const float wk = mine ? __fmul_rn(r.Tk, r.a) : 0.f;
+    const float term = __fmul_rn(wk, mydot);
+    const float suf = G.suffix_scan(term);  // sum over this chunk's fragments at or behind k
+    float behind = G.shift_down(suf);        // ... strictly behind k
+    const float Sk = __fadd_rn(S, behind);
+    const float om = __fsub_rn(1.0f, r.a);
+    const float da = __fsub_rn(__fmul_rn(r.Tk, mydot), __fdiv_rn(Sk, om));
+    if (mine) fscal[slot_at(c * GA + G.lg)] = make_float2(wk, da);
+    S = __fadd_rn(S, G.bcast(suf, 0));
   }
 }
 
 template <int V, int GA>
-__global__ void __launch_bounds__(kThreads) k_raster_bwd(RP P, const float* __restrict__ pos,
-                                                          const float* __restrict__ opacity,
-                                                          const float* __restrict__ feat,
-                                                          const float* __restrict__ T_final,
-                                                          const int32_t* __restrict__ n_contrib,
-                                                          const float* __restrict__ d_image, RasterWs ws,
-                                                          float* __restrict__ d_opacity, float* __restrict__ d_feat) {
+__global__ void __launch_bounds__(kThreads) k_blend_bwd(RP P, const float* __restrict__ pos,
+                                                         const float* __restrict__ opacity,
+                                                         const float* __restrict__ feat,
+                                                         const int32_t* __restrict__ n_contrib,
+                                                         const float* __restrict__ d_image, RasterWs ws) {
+  constexpr int kGroups = kThreads / GA;
+  constexpr int CG = kGroupKeys / kGroups;
   extern __shared__ __align__(16) unsigned char dyn[];
-  __shared__ TileSmem S;
+  const Group<GA> G;
+  const int group = threadIdx.x / GA;
+  unsigned long long* K = reinterpret_cast<unsigned long long*>(dyn) + group * CG;
+  uint16_t* idx = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned long long*>(dyn) + kGroupKeys) + group * CG;
+  float* chunkT = reinterpret_cast<float*>(reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned long long*>(dyn) +
+                                                                       kGroupKeys) + kGroupKeys) +
+                  group * (CG / GA + 1);
   const int t = blockIdx.x;
   const int tx = t % P.tiles_x, ty = t / P.tiles_x;
-  const int n_t = (int)ws.tile_count[t];
-  if (n_t == 0) return;
-  const uint32_t base = ws.tile_offset[t];
-  const int lane = threadIdx.x & 31;
-  const int lg = lane % GA;
-  const int group = threadIdx.x / GA;
-  constexpr int kGroups = kThreads / GA;
-  const unsigned gmask = GA == 32 ? 0xffffffffu : (((1u << GA) - 1u) << (lane - lg));
-  const int npix = P.TW * P.TH;
-  if (n_t <= kCapBwd) {
-    unsigned long long* K = reinterpret_cast<unsigned long long*>(dyn);
-    float2* sc = reinterpret_cast<float2*>(K + kCapBwd);
-    uint16_t* idx = reinterpret_cast<uint16_t*>(sc + kCapBwd);
-    for (int i = threadIdx.x; i < n_t; i += kThreads) {
-      K[i] = ws.keys[base + i];
-      sc[i] = make_float2(0.f, 0.f);
+  for (int p = group; p < P.TW * P.TH; p += kGroups) {
+    const int px = tx * P.TW + p % P.TW, py = ty * P.TH + p / P.TW;
+    if (px >= P.cam.W || py >= P.cam.H) continue;
+    const long long q = (long long)py * P.cam.W + px;
+    const uint32_t s0 = ws.pix_start[q];
+    const int m = (int)(ws.pix_start[q + 1] - s0);
+    if (m > CG || m == 0) continue;
+    for (int j = G.lg; j < m; j += GA) {
+      K[j] = ws.keys[s0 + j];
+      idx[j] = (uint16_t)j;
     }
-    __syncthreads();
-    pixel_segments([&](int i) { return K[i]; }, n_t, S);
-    for (int i = threadIdx.x; i < n_t; i += kThreads) {
-      const uint32_t dst = atomicAdd(&S.pixcur[(int)(K[i] >> 56)], 1u);
-      idx[dst] = (uint16_t)i;
-    }
-    __syncthreads();
-    for (int p = group; p < npix; p += kGroups) {
-      const int px = tx * P.TW + p % P.TW, py = ty * P.TH + p / P.TW;
-      if (px >= P.cam.W || py >= P.cam.H) continue;
-      const int b = (int)S.pixbeg[p], m = (int)(S.pixbeg[p + 1] - S.pixbeg[p]);
-      group_sort<GA>(K, idx + b, m, lg, gmask);
-      const int nb = min(m, (int)n_contrib[(long long)py * P.cam.W + px]);
-      blend_bwd_pixel<V, GA>(
-          P, [&](int k) { return K[idx[b + k]]; }, [&](int k) { return (int)idx[b + k]; },
-          [&](int q) -> float2& { return sc[q]; }, nb, px, py, pos, opacity, feat, T_final, d_image, lg, gmask);
-    }
-    __syncthreads();
-    for (int i = group; i < n_t; i += kGroups) {
-      const long long id = (long long)(K[i] & kIdMask);
-      if (i > 0 && (long long)(K[i - 1] & kIdMask) == id) continue;
-      int c = 1;
-      while (i + c < n_t && c < 4 && (long long)(K[i + c] & kIdMask) == id) ++c;
-      point_grad<V, GA>(P, [&](int q) { return K[q]; }, [&](int q) { return sc[q]; }, i, c, tx, ty, pos, opacity,
-                        feat, d_image, d_opacity, d_feat, lg);
-    }
-  } else {
-    unsigned long long* ka = ws.ka + base;
-    uint32_t* va = ws.va + base;
-    float2* fs = ws.fscal + base;
-    const unsigned long long* kin = ws.keys + base;
-    for (int i = threadIdx.x; i < n_t; i += kThreads) fs[i] = make_float2(0.f, 0.f);
-    cta_sort_global(kin, n_t, ka, va, ws.kb + base, ws.vb + base, S);
-    pixel_segments([&](int i) { return ka[i]; }, n_t, S);
-    for (int p = group; p < npix; p += kGroups) {
-      const int px = tx * P.TW + p % P.TW, py = ty * P.TH + p / P.TW;
-      if (px >= P.cam.W || py >= P.cam.H) continue;
-      const int b = (int)S.pixbeg[p], m = (int)(S.pixbeg[p + 1] - S.pixbeg[p]);
-      const int nb = min(m, (int)n_contrib[(long long)py * P.cam.W + px]);
-      blend_bwd_pixel<V, GA>(
-          P, [&](int k) { return ka[b + k]; }, [&](int k) { return (int)va[b + k]; },
-          [&](int q) -> float2& { return fs[q]; }, nb, px, py, pos, opacity, feat, T_final, d_image, lg, gmask);
-    }
-    __syncthreads();
-    for (int i = group; i < n_t; i += kGroups) {
-      const long long id = (long long)(kin[i] & kIdMask);
-      if (i > 0 && (long long)(kin[i - 1] & kIdMask) == id) continue;
-      int c = 1;
-      while (i + c < n_t && c < 4 && (long long)(kin[i + c] & kIdMask) == id) ++c;
-      point_grad<V, GA>(P, [&](int q) { return kin[q]; }, [&](int q) { return fs[q]; }, i, c, tx, ty, pos,
-                        opacity, feat, d_image, d_opacity, d_feat, lg);
-    }
+    G.sync();
+    bitonic_sort_idx(K, idx, m, G.lg, GA, [&] { G.sync(); });
+    const int nb = min(m, (int)n_contrib[q]);
+    blend_bwd<V, GA>(G, P, [&](int k) { return K[idx[k]]; }, [&](int k) { return s0 + idx[k]; }, m, nb, px, py, pos,
+                     opacity, feat, d_image, ws.fscal, chunkT);
+    G.sync();
   }
 }
 
-// Zero the gradient rows that the tile kernels will not overwrite: culled
-// points (no fragment) and points whose fragments span several tiles (those
-// receive per-tile partial sums through atomics).
-__global__ void __launch_bounds__(256) k_bwd_prep(RP P, const float* __restrict__ pos, float* __restrict__ d_opacity,
-                                                  float* __restrict__ d_feat) {
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < P.n;
-       id += (long long)gridDim.x * blockDim.x) {
-    Splat s;
-    int first = -1;
-    bool zero = true;
-    if (splat_point(P, pos, id, s)) {
-      bool multi = false;
-      for (int k = 0; k < 4; ++k) {
-        int px, py;
-        const int t = corner_tile(P, s.f, k, px, py);
-        if (t < 0) continue;
-        if (first < 0) first = t;
-        else if (t != first) multi = true;
+template <int V, int GA>
+__global__ void __launch_bounds__(kThreads) k_blend_bwd_heavy(RP P, const float* __restrict__ pos,
+                                                               const float* __restrict__ opacity,
+                                                               const float* __restrict__ feat,
+                                                               const int32_t* __restrict__ n_contrib,
+                                                               const float* __restrict__ d_image, RasterWs ws) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ SortSmem S;
+  unsigned long long* K = reinterpret_cast<unsigned long long*>(dyn);
+  uint16_t* idx = reinterpret_cast<uint16_t*>(K + kHeavyKeys);
+  const Group<GA> G;
+  const uint32_t n_heavy = *ws.heavy_count;
+  for (uint32_t h = blockIdx.x; h < n_heavy; h += gridDim.x) {
+    const long long q = ws.heavy[h];
+    const int px = (int)(q % P.cam.W), py = (int)(q / P.cam.W);
+    const uint32_t s0 = ws.pix_start[q];
+    const int m = (int)(ws.pix_start[q + 1] - s0);
+    const int nb = min(m, (int)n_contrib[q]);
+    if (m <= kHeavyKeys) {
+      for (int j = threadIdx.x; j < m; j += kThreads) {
+        K[j] = ws.keys[s0 + j];
+        idx[j] = (uint16_t)j;
       }
-      zero = first < 0 || multi;
+      __syncthreads();
+      bitonic_sort_idx(K, idx, m, threadIdx.x, kThreads, [] { __syncthreads(); });
+      // the bucket's global-sort scratch holds the chunk transmittances
+      if (threadIdx.x < GA)
+        blend_bwd<V, GA>(G, P, [&](int k) { return K[idx[k]]; }, [&](int k) { return s0 + idx[k]; }, m, nb, px, py,
+                         pos, opacity, feat, d_image, ws.fscal, reinterpret_cast<float*>(ws.kb + s0));
+    } else {
+      unsigned long long* ka = ws.ka + s0;
+      uint32_t* va = ws.va + s0;
+      cta_sort_global(ws.keys + s0, m, ka, va, ws.kb + s0, ws.vb + s0, S);
+      // the sort's scratch keys hold the chunk transmittances of this pixel
+      if (threadIdx.x < GA)
+        blend_bwd<V, GA>(G, P, [&](int k) { return ka[k]; }, [&](int k) { return s0 + va[k]; }, m, nb, px, py, pos,
+                         opacity, feat, d_image, ws.fscal, reinterpret_cast<float*>(ws.kb + s0));
     }
-    if (!zero) continue;
-    float* row = d_feat + id * P.F;
-    for (int c = 0; c < P.F; ++c) row[c] = 0.f;
-    if (d_opacity) d_opacity[id] = 0.f;
+    __syncthreads();
+  }
+}
+
+// Per point: gather the scalars of its (at most four) splats and the
+// upstream-gradient rows of their pixels.  d_feat row = sum_k (T_k alpha_k) g_k;
+// d alpha_h = sum_k w_k [unclamped] dL/dalpha_k.
+template <int V, int GA>
+__global__ void __launch_bounds__(kThreads) k_point_grad(RP P, const float* __restrict__ pos,
+                                                          const float* __restrict__ opacity,
+                                                          const float* __restrict__ feat,
+                                                          const float* __restrict__ d_image, RasterWs ws,
+                                                          float* __restrict__ d_opacity, float* __restrict__ d_feat) {
+  constexpr int kGroups = kThreads / GA;
+  const Group<GA> G;
+  const int ch = G.lg * V;
+  const bool active = ch < P.F;
+  const long long g0 = (long long)blockIdx.x * kGroups + threadIdx.x / GA;
+  for (long long id = g0; id < P.n; id += (long long)gridDim.x * kGroups) {
+    const uint4 sl = __ldg(reinterpret_cast<const uint4*>(ws.pslot) + id);
+    const uint32_t slots[4] = {sl.x, sl.y, sl.z, sl.w};
+    float dc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) dc[v] = 0.f;
+    float dah = 0.f, e_h0 = 0.f;
+    Splat s;
+    if ((sl.x & sl.y & sl.z & sl.w) != kNoSlot) {
+      splat_point(P, pos, id, s);
+      const float ah = point_alpha_h(P, opacity, feat, id, &e_h0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (slots[k] == kNoSlot) continue;
+        const float2 sc = __ldg(ws.fscal + slots[k]);
+        const float w = corner_weight(s.f, k & 1, k >> 1);
+        if (__fmul_rn(ah, w) <= P.alpha_max) dah = __fmaf_rn(w, sc.y, dah);
+        if (active) {
+          const long long pix = (long long)(s.f.j0 + (k >> 1)) * P.cam.W + (s.f.i0 + (k & 1));
+          float g[V];
+          load_vec<V>(d_image + pix * P.F + ch, g);
+#pragma unroll
+          for (int v = 0; v < V; ++v) dc[v] = __fmaf_rn(sc.x, g[v], dc[v]);
+        }
+      }
+    }
+    // head mode: channel 0 of the blended color is the constant 1; the
+    // opacity gradient reaches h0 through alpha_h = 1 - exp(-exp(h0))
+    if (P.head && G.lg == 0) dc[0] = dah * (e_h0 * expf(-e_h0));
+    if (active) {
+      float* o = d_feat + id * P.F + ch;
+      if (V == 4) *reinterpret_cast<float4*>(o) = make_float4(dc[0], dc[1], dc[2], dc[3]);
+      else
+#pragma unroll
+        for (int v = 0; v < V; ++v) o[v] = dc[v];
+    }
+    if (!P.head && G.lg == 0) d_opacity[id] = dah;
   }
 }
 
@@ -757,7 +799,7 @@ inpc_status make_rp(const inpc_camera* cam, const inpc_raster_opts* o, int64_t n
   if (!(o->alpha_max > 0.0f && o->alpha_max < 1.0f)) return fail(INPC_ERR_INVALID_ARG, "alpha_max must be in (0, 1)");
   P.cam = to_cam(*cam);
   P.TW = o->tile_w > 0 ? o->tile_w : 16;
-  P.TH = o->tile_h > 0 ? o->tile_h : 16;
+  P.TH = o->tile_h > 0 ? o->tile_h : 8;
   if (P.TW * P.TH > 256) return fail(INPC_ERR_INVALID_ARG, "tile_w * tile_h must be <= 256");
   P.tiles_x = (int)ceil_div(cam->width, P.TW);
   P.tiles_y = (int)ceil_div(cam->height, P.TH);
@@ -767,6 +809,8 @@ inpc_status make_rp(const inpc_camera* cam, const inpc_raster_opts* o, int64_t n
   P.t_min = o->t_min;
   P.alpha_max = o->alpha_max;
   P.n = n;
+  P.n_pix = (long long)cam->width * cam->height;
+  if (4 * n > (int64_t)UINT32_MAX - 1) return fail(INPC_ERR_CAPACITY, "too many fragments");
   return INPC_OK;
 }
 
@@ -776,33 +820,6 @@ int next_pow2(int x) {
   return p;
 }
 
-template <int V, int GA>
-inpc_status launch_fwd(const RP& P, const float* pos, const float* opacity, const float* feat, const RasterWs& ws,
-                       float* image, float* T_final, int32_t* n_contrib, cudaStream_t s) {
-  const size_t dyn = (size_t)kCapFwd * (8 + 2);
-  static std::once_flag once;
-  std::call_once(once, [&] {
-    cudaFuncSetAttribute(k_raster_fwd<V, GA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-  });
-  k_raster_fwd<V, GA><<<P.n_tiles, kThreads, dyn, s>>>(P, pos, opacity, feat, ws, image, T_final, n_contrib);
-  return check_launch("k_raster_fwd");
-}
-
-template <int V, int GA>
-inpc_status launch_bwd(const RP& P, const float* pos, const float* opacity, const float* feat, const float* T_final,
-                       const int32_t* n_contrib, const float* d_image, const RasterWs& ws, float* d_opacity,
-                       float* d_feat, cudaStream_t s) {
-  const size_t dyn = (size_t)kCapBwd * (8 + 8 + 2);
-  static std::once_flag once;
-  std::call_once(once, [&] {
-    cudaFuncSetAttribute(k_raster_bwd<V, GA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-  });
-  k_raster_bwd<V, GA><<<P.n_tiles, kThreads, dyn, s>>>(P, pos, opacity, feat, T_final, n_contrib, d_image, ws,
-                                                        d_opacity, d_feat);
-  return check_launch("k_raster_bwd");
-}
-
-// (V, GA): V channels per lane, GA lanes per pixel.
 template <class Fn>
 inpc_status dispatch(int F, Fn&& fn) {
   if (F % 4 == 0) {
@@ -832,6 +849,76 @@ unsigned point_grid(long long n) {
   return (unsigned)std::max<long long>(1, std::min<long long>(ceil_div(n, 256), cap));
 }
 
+template <class K>
+void set_smem(K kernel, size_t bytes, std::once_flag& once) {
+  std::call_once(once, [&] { cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); });
+}
+
+constexpr size_t kGroupSmemFwd = (size_t)kGroupKeys * (8 + 2);
+constexpr size_t kHeavySmemFwd = (size_t)kHeavyKeys * (8 + 2);
+
+template <int V, int GA>
+size_t group_smem_bwd() {
+  constexpr int kGroups = kThreads / GA;
+  return (size_t)kGroupKeys * (8 + 2) + (size_t)kGroups * (kGroupKeys / kGroups / GA + 1) * 4;
+}
+constexpr size_t kHeavySmemBwd = (size_t)kHeavyKeys * (8 + 2);
+
+// Forward binning: per-pixel counts, offsets, buckets, per-point slots and
+// the list of pixels for the CTA path (kept in the workspace for the backward).
+inpc_status bin_fragments(const RP& P, const float* pos, const RasterWs& ws, uint32_t cap_group, cudaStream_t s) {
+  INPC_CUDA(cudaMemsetAsync(ws.pix_count, 0, sizeof(uint32_t) * P.n_pix, s), "clear pixel counts");
+  if (P.n > 0) {
+    k_pix_count<<<point_grid(P.n), 256, 0, s>>>(P, pos, ws.pix_count);
+    INPC_TRY(check_launch("k_pix_count"));
+  }
+  INPC_TRY((scan::run<uint32_t, CountLoad, false>(CountLoad{ws.pix_count}, P.n_pix, ws.pix_start, ws.tops, s)));
+  const long long nb = ceil_div(P.n_pix, scan::kBlock);
+  k_heavy_list<<<(unsigned)ceil_div(P.n_pix, 256), 256, 0, s>>>(ws.pix_start, P.n_pix, ws.tops, nb, cap_group, ws.heavy,
+                                                                 ws.heavy_count, ws.pix_start);
+  INPC_TRY(check_launch("k_heavy_list"));
+  if (P.n > 0) {
+    k_pix_scatter<<<point_grid(P.n), 256, 0, s>>>(P, pos, ws.pix_start, ws.pix_count, ws.keys, ws.pslot);
+    INPC_TRY(check_launch("k_pix_scatter"));
+  }
+  return INPC_OK;
+}
+
+template <int V, int GA>
+inpc_status launch_fwd(const RP& P, const float* pos, const float* opacity, const float* feat, const RasterWs& ws,
+                       float* image, float* T_final, int32_t* n_contrib, cudaStream_t s) {
+  constexpr int CG = kGroupKeys / (kThreads / GA);
+  INPC_TRY(bin_fragments(P, pos, ws, CG, s));
+  static std::once_flag f1, f2;
+  set_smem(k_blend_fwd<V, GA>, kGroupSmemFwd, f1);
+  set_smem(k_blend_fwd_heavy<V, GA>, kHeavySmemFwd, f2);
+  k_blend_fwd<V, GA><<<P.n_tiles, kThreads, kGroupSmemFwd, s>>>(P, pos, opacity, feat, ws, image, T_final, n_contrib);
+  INPC_TRY(check_launch("k_blend_fwd"));
+  k_blend_fwd_heavy<V, GA><<<device_sm_count(), kThreads, kHeavySmemFwd, s>>>(P, pos, opacity, feat, ws, image,
+                                                                              T_final, n_contrib);
+  return check_launch("k_blend_fwd_heavy");
+}
+
+template <int V, int GA>
+inpc_status launch_bwd(const RP& P, const float* pos, const float* opacity, const float* feat,
+                       const int32_t* n_contrib, const float* d_image, const RasterWs& ws, float* d_opacity,
+                       float* d_feat, cudaStream_t s) {
+  static std::once_flag f1, f2;
+  const size_t gs = group_smem_bwd<V, GA>();
+  set_smem(k_blend_bwd<V, GA>, gs, f1);
+  set_smem(k_blend_bwd_heavy<V, GA>, kHeavySmemBwd, f2);
+  k_blend_bwd<V, GA><<<P.n_tiles, kThreads, gs, s>>>(P, pos, opacity, feat, n_contrib, d_image, ws);
+  INPC_TRY(check_launch("k_blend_bwd"));
+  k_blend_bwd_heavy<V, GA><<<device_sm_count(), kThreads, kHeavySmemBwd, s>>>(P, pos, opacity, feat, n_contrib,
+                                                                              d_image, ws);
+  INPC_TRY(check_launch("k_blend_bwd_heavy"));
+  constexpr int kGroups = kThreads / GA;
+  const long long grid = std::min<long long>(ceil_div(P.n, kGroups), (long long)device_sm_count() * 32);
+  k_point_grad<V, GA><<<(unsigned)std::max<long long>(grid, 1), kThreads, 0, s>>>(P, pos, opacity, feat, d_image, ws,
+                                                                                  d_opacity, d_feat);
+  return check_launch("k_point_grad");
+}
+
 }  // namespace
 }  // namespace inpc
 
@@ -842,7 +929,7 @@ extern "C" inpc_status inpc_rasterize_workspace_size(const inpc_camera* cam, con
   if (!bytes) return fail(INPC_ERR_INVALID_ARG, "bytes is null");
   RP P;
   INPC_TRY(make_rp(cam, opts, n, P));
-  *bytes = carve(nullptr, P.n_tiles, n).bytes;
+  *bytes = carve(nullptr, P.n_pix, n).bytes;
   return INPC_OK;
 }
 
@@ -852,7 +939,7 @@ extern "C" inpc_status inpc_rasterize_fwd(const inpc_camera* cam, const inpc_ras
                                           size_t workspace_bytes, inpc_stream_t stream) {
   RP P;
   INPC_TRY(make_rp(cam, opts, n, P));
-  const RasterWs need = carve(nullptr, P.n_tiles, n);
+  const RasterWs need = carve(nullptr, P.n_pix, n);
   if (!workspace || workspace_bytes < need.bytes || !aligned(workspace, 256))
     return fail(INPC_ERR_INVALID_ARG, "workspace null, unaligned or smaller than %zu bytes", need.bytes);
   if (!image || !T_final || !n_contrib) return fail(INPC_ERR_INVALID_ARG, "null output");
@@ -862,20 +949,9 @@ extern "C" inpc_status inpc_rasterize_fwd(const inpc_camera* cam, const inpc_ras
   if (!aligned(feat, va) || !aligned(image, va) || !aligned(pos, 4))
     return fail(INPC_ERR_INVALID_ARG, "feat/image must be %zu-byte aligned", va);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  RasterWs ws = carve(workspace, P.n_tiles, n);
+  RasterWs ws = carve(workspace, P.n_pix, n);
   INPC_CUDA(cudaMemsetAsync(workspace, 0, kHeaderBytes, s), "clear header");
-  INPC_CUDA(cudaMemsetAsync(ws.tile_count, 0, sizeof(uint32_t) * P.n_tiles, s), "clear tile counts");
   const float* f32 = static_cast<const float*>(feat);
-  if (n > 0) {
-    k_bin_count<<<point_grid(n), 256, 0, s>>>(P, pos, ws.tile_count);
-    INPC_TRY(check_launch("k_bin_count"));
-  }
-  k_scan_tiles<<<1, 1024, 0, s>>>(ws.tile_count, P.n_tiles, ws.tile_offset, ws.tile_cursor);
-  INPC_TRY(check_launch("k_scan_tiles"));
-  if (n > 0) {
-    k_bin_scatter<<<point_grid(n), 256, 0, s>>>(P, pos, ws.tile_offset, ws.tile_cursor, ws.keys);
-    INPC_TRY(check_launch("k_bin_scatter"));
-  }
   return dispatch(P.F, [&](auto Vc, auto Gc) {
     return launch_fwd<decltype(Vc)::value, decltype(Gc)::value>(P, pos, opacity, f32, ws, static_cast<float*>(image),
                                                                  T_final, n_contrib, s);
@@ -889,7 +965,7 @@ extern "C" inpc_status inpc_rasterize_bwd(const inpc_camera* cam, const inpc_ras
                                           inpc_stream_t stream) {
   RP P;
   INPC_TRY(make_rp(cam, opts, n, P));
-  const RasterWs need = carve(nullptr, P.n_tiles, n);
+  const RasterWs need = carve(nullptr, P.n_pix, n);
   if (!workspace || workspace_bytes < need.bytes || !aligned(workspace, 256))
     return fail(INPC_ERR_INVALID_ARG, "workspace null, unaligned or smaller than %zu bytes", need.bytes);
   if (n == 0) return INPC_OK;
@@ -900,13 +976,10 @@ extern "C" inpc_status inpc_rasterize_bwd(const inpc_camera* cam, const inpc_ras
   if (!aligned(feat, va) || !aligned(d_image, va) || !aligned(d_feat, va))
     return fail(INPC_ERR_INVALID_ARG, "feat/d_image/d_feat must be %zu-byte aligned", va);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  RasterWs ws = carve(workspace, P.n_tiles, n);
-  float* dop = P.head ? nullptr : d_opacity;
-  k_bwd_prep<<<point_grid(n), 256, 0, s>>>(P, pos, dop, d_feat);
-  INPC_TRY(check_launch("k_bwd_prep"));
+  RasterWs ws = carve(workspace, P.n_pix, n);
   const float* f32 = static_cast<const float*>(feat);
   return dispatch(P.F, [&](auto Vc, auto Gc) {
-    return launch_bwd<decltype(Vc)::value, decltype(Gc)::value>(P, pos, opacity, f32, T_final, n_contrib, d_image, ws,
-                                                                 dop, d_feat, s);
+    return launch_bwd<decltype(Vc)::value, decltype(Gc)::value>(P, pos, opacity, f32, n_contrib, d_image, ws,
+                                                                 P.head ? nullptr : d_opacity, d_feat, s);
   });
 }
