@@ -5,27 +5,29 @@
 // the pixel is the most significant radix digit and is handled by a
 // counting sort into per-pixel buckets (k_pix_count, prefix sum,
 // k_pix_scatter); each bucket is then ordered by the remaining key
-// (FP32 depth bits << 25 | point index) in shared memory by the lanes that
+// (FP32 depth bits << 25 | point index) in shared memory by the threads that
 // blend it: a group of GA lanes per pixel for buckets of at most CG
-// fragments, a whole CTA (bitonic network in shared memory) for larger ones,
-// and a stable LSD radix sort in global memory beyond the shared-memory
-// capacity.  Every path yields the exact (depth, point) order.
+// fragments, a whole CTA (bitonic network) for larger ones, and a stable LSD
+// radix sort in global memory beyond the shared-memory capacity.  Every path
+// yields the exact (depth, point) order.
 //
-// Blending.  alpha_k needs only the fragment's own point, so it is computed
-// for GA fragments at once; the transmittance T_k = prod_{j<k} (1 - alpha_j)
-// is a product scan across lanes, the stopping fragment (first with
-// T_{k+1} < t_min) comes from a ballot, and the color sum_k T_k alpha_k c_k is
-// an independent gather-reduce over the fragments' feature rows (V channels
-// per lane, float4 loads), so no dependent load chain limits a pixel.
+// Blending.  The scatter pass stores each fragment's alpha (Eq. 6 with the
+// clamp) beside its key, so blending gathers nothing but the feature rows of
+// the blended fragments.  T_k = prod_{j<k} (1 - alpha_j) is a product scan
+// across lanes (chunks of GA fragments on the group path, 256 on the CTA
+// path), the stopping fragment (first with T_{k+1} < t_min) comes from a
+// ballot, and sum_k T_k alpha_k c_k is an independent gather-reduce over the
+// feature rows (V channels per lane, float4 loads).
 //
 // Backward.  Per pixel, T_k is recomputed by the forward's own scan (same
-// rounding, no per-fragment storage between the passes) and the suffix
-// sums S_k = sum_{j>k} T_j alpha_j (c_j . g) run back to front, chunk by
-// chunk.  Each fragment's two scalars (T_k alpha_k, dL/dalpha_k) go to its
-// bucket slot; a per-point kernel then gathers its (at most four) slots and
-// the matching upstream-gradient rows and writes the point's gradient with
-// plain stores -- no atomics, no zero-fill pass.
+// rounding, nothing stored between the passes) and the suffix sums
+// S_k = sum_{j>k} T_j alpha_j (c_j . g) run back to front.  Each fragment's
+// two scalars (T_k alpha_k, dL/dalpha_k) go to its bucket slot; a per-point
+// kernel then gathers its (at most four) slots and the matching
+// upstream-gradient rows and writes the point's gradient with plain stores:
+// no atomics, no zero-fill pass.
 #include <algorithm>
+#include <climits>
 #include <mutex>
 
 #include "common.cuh"
@@ -38,8 +40,8 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kIdBits = 25;
 constexpr unsigned long long kIdMask = (1ull << kIdBits) - 1;
-constexpr int kGroupKeys = 8192;   // shared-memory keys per CTA on the group path (split among groups)
-constexpr int kHeavyKeys = 16384;  // shared-memory keys of the CTA path
+constexpr int kGroupKeys = 6144;  // shared-memory bucket entries per CTA on the group path (split among groups)
+constexpr int kHeavyKeys = 8192;  // shared-memory bucket entries on the CTA path
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 
 struct RP {
@@ -54,17 +56,18 @@ struct RP {
 
 struct RasterWs {
   uint32_t* status;
-  uint32_t* heavy_count;  // header word 1
-  uint32_t* pix_count;    // [n_pix]
-  uint32_t* pix_start;    // [n_pix + 1]
-  uint32_t* tops;         // prefix-sum block totals
-  uint32_t* heavy;        // [n_pix] pixels on the CTA path
+  uint32_t* heavy_count;     // header word 1
+  uint32_t* pix_count;       // [n_pix]
+  uint32_t* pix_start;       // [n_pix + 1]
+  uint32_t* tops;            // prefix-sum block totals
+  uint32_t* heavy;           // [n_pix] pixels on the CTA path
   unsigned long long* keys;  // [4n] bucketed fragment keys
-  uint32_t* pslot;        // [4n] bucket slot of each point corner (kNoSlot off-image)
-  float2* fscal;          // [4n] backward per-fragment scalars
+  float* alpha;              // [4n] fragment alphas
+  uint32_t* pslot;           // [4n] bucket slot of each point corner (kNoSlot off-image)
+  float2* fscal;             // [4n] backward per-fragment scalars
   unsigned long long* ka;    // [4n] global-sort result (largest buckets only)
   uint32_t* va;
-  unsigned long long* kb;    // [4n] global-sort scratch
+  unsigned long long* kb;    // [4n] global-sort scratch, then per-fragment (T_k, c_k . g)
   uint32_t* vb;
   size_t bytes;
 };
@@ -80,6 +83,7 @@ RasterWs carve(void* base, long long n_pix, long long n) {
   w.tops = c.take<uint32_t>(scan::n_tops(n_pix));
   w.heavy = c.take<uint32_t>(n_pix);
   w.keys = c.take<unsigned long long>(nf);
+  w.alpha = c.take<float>(nf);
   w.pslot = c.take<uint32_t>(nf);
   w.fscal = c.take<float2>(nf);
   w.ka = c.take<unsigned long long>(nf);
@@ -111,6 +115,7 @@ __device__ __forceinline__ long long corner_pixel(const RP& P, const Footprint& 
   return (long long)py * P.cam.W + px;
 }
 
+// Point opacity alpha_h: given, or 1 - exp(-exp(h0)) (Sec. 3.3) in head mode.
 __device__ __forceinline__ float point_alpha_h(const RP& P, const float* __restrict__ opacity,
                                                const float* __restrict__ feat, long long id, float* e_h0) {
   if (P.head) {
@@ -121,37 +126,17 @@ __device__ __forceinline__ float point_alpha_h(const RP& P, const float* __restr
   return __ldg(opacity + id);
 }
 
-// alpha of the fragment of point `id` at pixel (px, py) (Eq. 6 with the clamp).
-__device__ __forceinline__ float frag_alpha(const RP& P, const float* __restrict__ pos,
-                                            const float* __restrict__ opacity, const float* __restrict__ feat,
-                                            long long id, int px, int py) {
-  Splat s;
-  splat_point(P, pos, id, s);
-  const float w = corner_weight(s.f, px - s.f.i0, py - s.f.j0);
-  return fminf(__fmul_rn(point_alpha_h(P, opacity, feat, id, nullptr), w), P.alpha_max);
-}
-
 // ---------------------------------------------------------------- binning ---
-// Per-point corner pixels (or -1).
-__device__ __forceinline__ void point_pixels(const RP& P, const float* __restrict__ pos, long long id,
-                                             long long q[4], float& d) {
-  Splat s;
-  q[0] = q[1] = q[2] = q[3] = -1;
-  d = 0.f;
-  if (id < P.n && splat_point(P, pos, id, s)) {
-    d = s.d;
-    for (int k = 0; k < 4; ++k) q[k] = corner_pixel(P, s.f, k);
-  }
-}
-
 __global__ void __launch_bounds__(256) k_pix_count(RP P, const float* __restrict__ pos,
                                                    uint32_t* __restrict__ pix_count) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   for (long long base = blockIdx.x * (long long)blockDim.x; base < P.n; base += (long long)gridDim.x * blockDim.x) {
-    long long q[4];
-    float d;
-    point_pixels(P, pos, base + threadIdx.x, q, d);
+    const long long id = base + threadIdx.x;
+    long long q[4] = {-1, -1, -1, -1};
+    Splat s;
+    if (id < P.n && splat_point(P, pos, id, s))
+      for (int k = 0; k < 4; ++k) q[k] = corner_pixel(P, s.f, k);
     for (int k = 0; k < 4; ++k) {
       // leaf-grouped points are spatially coherent: aggregate equal pixels per warp
       const unsigned peers = __match_any_sync(full, q[k]);
@@ -161,18 +146,24 @@ __global__ void __launch_bounds__(256) k_pix_count(RP P, const float* __restrict
 }
 
 __global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restrict__ pos,
+                                                     const float* __restrict__ opacity,
+                                                     const float* __restrict__ feat,
                                                      const uint32_t* __restrict__ pix_start,
                                                      uint32_t* __restrict__ pix_count,
                                                      unsigned long long* __restrict__ keys,
-                                                     uint32_t* __restrict__ pslot) {
+                                                     float* __restrict__ alpha, uint32_t* __restrict__ pslot) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   for (long long base = blockIdx.x * (long long)blockDim.x; base < P.n; base += (long long)gridDim.x * blockDim.x) {
     const long long id = base + threadIdx.x;
-    long long q[4];
-    float d;
-    point_pixels(P, pos, id, q, d);
-    const unsigned long long key = ((unsigned long long)__float_as_uint(d) << kIdBits) | (unsigned long long)id;
+    long long q[4] = {-1, -1, -1, -1};
+    Splat s;
+    float ah = 0.f;
+    if (id < P.n && splat_point(P, pos, id, s)) {
+      for (int k = 0; k < 4; ++k) q[k] = corner_pixel(P, s.f, k);
+      ah = point_alpha_h(P, opacity, feat, id, nullptr);
+    }
+    const unsigned long long key = ((unsigned long long)__float_as_uint(s.d) << kIdBits) | (unsigned long long)id;
     uint32_t slots[4];
     for (int k = 0; k < 4; ++k) {
       const unsigned peers = __match_any_sync(full, q[k]);
@@ -186,6 +177,7 @@ __global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restri
         const uint32_t local = top - 1 - __popc(peers & ((1u << lane) - 1));
         slots[k] = pix_start[q[k]] + local;
         keys[slots[k]] = key;
+        alpha[slots[k]] = fminf(__fmul_rn(ah, corner_weight(s.f, k & 1, k >> 1)), P.alpha_max);
       }
     }
     if (id < P.n) reinterpret_cast<uint4*>(pslot)[id] = make_uint4(slots[0], slots[1], slots[2], slots[3]);
@@ -424,68 +416,81 @@ __device__ __forceinline__ void load_vec(const float* __restrict__ p, float* c) 
   }
 }
 
-// Transmittance bookkeeping of one chunk of GA fragments [b, b + GA) of a
-// pixel: lane j holds fragment b + j.  Returns the number of fragments of the
-// chunk that are blended (the stopping fragment included) and sets `stop`.
+// This lane's V channels of a point's blended color: its features, with
+// channel 0 replaced by 1 in head mode.
+template <int V>
+__device__ __forceinline__ void load_color(const RP& P, const float* __restrict__ feat, long long id, int ch, float* c) {
+  load_vec<V>(feat + (long long)P.F * id + ch, c);
+  if (P.head && ch == 0) c[0] = 1.0f;
+}
+
+template <int V>
+__device__ __forceinline__ void write_pixel(const RP& P, long long pix, int ch, const float* C, float* __restrict__ image) {
+  if (ch >= P.F) return;
+  float* o = image + pix * P.F + ch;
+  if (V == 4) __stcs(reinterpret_cast<float4*>(o), make_float4(C[0], C[1], C[2], C[3]));
+  else
+#pragma unroll
+    for (int v = 0; v < V; ++v) __stcs(o + v, C[v]);
+}
+
+// Transmittance of one chunk of GA fragments: lane j holds the alpha of
+// fragment b + j (0 beyond the list).  The inclusive product scan of
+// (1 - alpha) gives the transmittance behind each fragment, the shifted scan
+// the one in front of it; the first lane whose T drops below t_min stops the
+// pixel (that fragment is blended).
 template <int GA>
 struct ChunkT {
-  float a;      // alpha of this lane's fragment (0 beyond the list)
-  float Tk;     // transmittance in front of it
-  float Tn;     // transmittance behind it
-  int take;     // fragments of the chunk that are blended
+  float Tk;   // transmittance in front of this lane's fragment
+  float Tn;   // transmittance behind it
+  int take;   // fragments of the chunk that are blended
   bool stop;
 };
 
-template <int GA, class KeyAt>
-__device__ __forceinline__ ChunkT<GA> chunk_transmittance(const Group<GA>& G, const RP& P, KeyAt key_at, int b, int m,
-                                                          float T, int px, int py, const float* __restrict__ pos,
-                                                          const float* __restrict__ opacity,
-                                                          const float* __restrict__ feat, long long& id) {
+template <int GA>
+__device__ __forceinline__ ChunkT<GA> chunk_transmittance(const Group<GA>& G, const RP& P, float a, bool valid,
+                                                          int avail, float T) {
   ChunkT<GA> r;
-  const int k = b + G.lg;
-  r.a = 0.f;
-  id = 0;
-  if (k < m) {
-    id = (long long)(key_at(k) & kIdMask);
-    r.a = frag_alpha(P, pos, opacity, feat, id, px, py);
-  }
-  const float incl = G.prod_scan(__fsub_rn(1.0f, r.a));
+  const float incl = G.prod_scan(__fsub_rn(1.0f, a));
   float excl = G.bcast(incl, G.lg > 0 ? G.lg - 1 : 0);
   if (G.lg == 0) excl = 1.0f;
   r.Tk = __fmul_rn(T, excl);
   r.Tn = __fmul_rn(T, incl);
-  const unsigned st = G.ballot(k < m && r.Tn < P.t_min);
-  const int avail = min(GA, m - b);
+  const unsigned st = G.ballot(valid && r.Tn < P.t_min);
   r.stop = st != 0;
   r.take = r.stop ? __ffs(st) : avail;
   return r;
 }
 
-// ------------------------------------------------------------- forward ---
-template <int V, int GA, class KeyAt>
-__device__ void blend_fwd(const Group<GA>& G, const RP& P, KeyAt key_at, int m, int px, int py,
-                          const float* __restrict__ pos, const float* __restrict__ opacity,
-                          const float* __restrict__ feat, float* __restrict__ image, float* __restrict__ T_final,
-                          int32_t* __restrict__ n_contrib) {
+// ------------------------------------------------------ group path (fwd) ---
+// One pixel per group of GA lanes; its sorted bucket in shared memory (keys
+// K, alphas A, order idx).
+template <int V, int GA>
+__device__ void blend_fwd_group(const Group<GA>& G, const RP& P, const unsigned long long* K, const float* A,
+                                const uint16_t* idx, int m, long long pix, const float* __restrict__ feat,
+                                float* __restrict__ image, float* __restrict__ T_final,
+                                int32_t* __restrict__ n_contrib) {
   const int ch = G.lg * V;
-  const bool active = ch < P.F;
   float C[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) C[v] = 0.f;
   float T = 1.0f;
   int cnt = 0;
   for (int b = 0; b < m; b += GA) {
-    long long id;
-    const ChunkT<GA> r = chunk_transmittance<GA>(G, P, key_at, b, m, T, px, py, pos, opacity, feat, id);
-    const float wk = __fmul_rn(r.Tk, r.a);
-#pragma unroll 4
+    const int k = b + G.lg;
+    const bool valid = k < m;
+    const int q = valid ? idx[k] : 0;
+    const float a = valid ? A[q] : 0.f;
+    const long long id = valid ? (long long)(K[q] & kIdMask) : 0;
+    const ChunkT<GA> r = chunk_transmittance<GA>(G, P, a, valid, min(GA, m - b), T);
+    const float wk = __fmul_rn(r.Tk, a);
+#pragma unroll 8
     for (int j = 0; j < r.take; ++j) {
       const long long idj = G.bcast(id, j);
       const float wj = G.bcast(wk, j);
-      if (active) {
+      if (ch < P.F) {
         float c[V];
-        load_vec<V>(feat + (long long)P.F * idj + ch, c);
-        if (P.head && G.lg == 0) c[0] = 1.0f;
+        load_color<V>(P, feat, idj, ch, c);
 #pragma unroll
         for (int v = 0; v < V; ++v) C[v] = __fmaf_rn(wj, c[v], C[v]);
       }
@@ -494,139 +499,114 @@ __device__ void blend_fwd(const Group<GA>& G, const RP& P, KeyAt key_at, int m, 
     T = G.bcast(r.Tn, r.take - 1);
     if (r.stop) break;
   }
-  const long long pix = (long long)py * P.cam.W + px;
-  if (active) {
-    float* o = image + pix * P.F + ch;
-    if (V == 4) __stcs(reinterpret_cast<float4*>(o), make_float4(C[0], C[1], C[2], C[3]));
-    else
-#pragma unroll
-      for (int v = 0; v < V; ++v) __stcs(o + v, C[v]);
-  }
+  write_pixel<V>(P, pix, ch, C, image);
   if (G.lg == 0) {
     T_final[pix] = T;
     n_contrib[pix] = cnt;
   }
 }
 
+// Shared-memory carve of the group path: per group CG keys, alphas, order.
+template <int GA>
+struct GroupBuf {
+  static constexpr int kGroups = kThreads / GA;
+  static constexpr int CG = kGroupKeys / kGroups;
+  unsigned long long* K;
+  float* A;
+  uint16_t* idx;
+  float* chunkT;  // CG / GA + 1 per group (backward)
+  __device__ GroupBuf(unsigned char* dyn, int group) {
+    unsigned long long* k0 = reinterpret_cast<unsigned long long*>(dyn);
+    float* a0 = reinterpret_cast<float*>(k0 + kGroupKeys);
+    uint16_t* i0 = reinterpret_cast<uint16_t*>(a0 + kGroupKeys);
+    float* t0 = reinterpret_cast<float*>(i0 + kGroupKeys);
+    K = k0 + group * CG;
+    A = a0 + group * CG;
+    idx = i0 + group * CG;
+    chunkT = t0 + group * (CG / GA + 1);
+  }
+  static size_t bytes() { return (size_t)kGroupKeys * (8 + 4 + 2) + (size_t)kGroups * (CG / GA + 1) * 4; }
+};
+
+template <int GA>
+__device__ __forceinline__ void load_bucket(const Group<GA>& G, const RasterWs& ws, uint32_t s0, int m,
+                                            const GroupBuf<GA>& B) {
+  for (int j = G.lg; j < m; j += GA) {
+    B.K[j] = ws.keys[s0 + j];
+    B.A[j] = ws.alpha[s0 + j];
+    B.idx[j] = (uint16_t)j;
+  }
+  G.sync();
+  bitonic_sort_idx(B.K, B.idx, m, G.lg, GA, [&] { G.sync(); });
+}
+
 template <int V, int GA>
-__global__ void __launch_bounds__(kThreads) k_blend_fwd(RP P, const float* __restrict__ pos,
-                                                         const float* __restrict__ opacity,
-                                                         const float* __restrict__ feat, RasterWs ws,
+__global__ void __launch_bounds__(kThreads) k_blend_fwd(RP P, const float* __restrict__ feat, RasterWs ws,
                                                          float* __restrict__ image, float* __restrict__ T_final,
                                                          int32_t* __restrict__ n_contrib) {
-  constexpr int kGroups = kThreads / GA;
-  constexpr int CG = kGroupKeys / kGroups;
   extern __shared__ __align__(16) unsigned char dyn[];
   const Group<GA> G;
   const int group = threadIdx.x / GA;
-  unsigned long long* K = reinterpret_cast<unsigned long long*>(dyn) + group * CG;
-  uint16_t* idx = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned long long*>(dyn) + kGroupKeys) + group * CG;
+  const GroupBuf<GA> B(dyn, group);
   const int t = blockIdx.x;
   const int tx = t % P.tiles_x, ty = t / P.tiles_x;
-  for (int p = group; p < P.TW * P.TH; p += kGroups) {
+  for (int p = group; p < P.TW * P.TH; p += GroupBuf<GA>::kGroups) {
     const int px = tx * P.TW + p % P.TW, py = ty * P.TH + p / P.TW;
     if (px >= P.cam.W || py >= P.cam.H) continue;
     const long long q = (long long)py * P.cam.W + px;
     const uint32_t s0 = ws.pix_start[q];
     const int m = (int)(ws.pix_start[q + 1] - s0);
-    if (m > CG) continue;  // CTA path
-    for (int j = G.lg; j < m; j += GA) {
-      K[j] = ws.keys[s0 + j];
-      idx[j] = (uint16_t)j;
-    }
-    G.sync();
-    bitonic_sort_idx(K, idx, m, G.lg, GA, [&] { G.sync(); });
-    blend_fwd<V, GA>(G, P, [&](int k) { return K[idx[k]]; }, m, px, py, pos, opacity, feat, image, T_final,
-                     n_contrib);
+    if (m > GroupBuf<GA>::CG) continue;  // CTA path
+    load_bucket<GA>(G, ws, s0, m, B);
+    blend_fwd_group<V, GA>(G, P, B.K, B.A, B.idx, m, q, feat, image, T_final, n_contrib);
     G.sync();
   }
 }
 
+// ------------------------------------------------------ group path (bwd) ---
+// One pixel: recompute T_k with the forward's chunked scan (pass 1 keeps the
+// transmittance in front of every chunk), then walk the blended chunks back
+// to front accumulating S_k = sum_{j>k} T_j alpha_j (c_j . g) and write
+// fscal[slot_k] = (T_k alpha_k, dL/dalpha_k = T_k (c_k . g) - S_k / (1 - alpha_k)).
 template <int V, int GA>
-__global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const float* __restrict__ pos,
-                                                               const float* __restrict__ opacity,
-                                                               const float* __restrict__ feat, RasterWs ws,
-                                                               float* __restrict__ image, float* __restrict__ T_final,
-                                                               int32_t* __restrict__ n_contrib) {
-  extern __shared__ __align__(16) unsigned char dyn[];
-  __shared__ SortSmem S;
-  unsigned long long* K = reinterpret_cast<unsigned long long*>(dyn);
-  uint16_t* idx = reinterpret_cast<uint16_t*>(K + kHeavyKeys);
-  const Group<GA> G;
-  const uint32_t n_heavy = *ws.heavy_count;
-  for (uint32_t h = blockIdx.x; h < n_heavy; h += gridDim.x) {
-    const long long q = ws.heavy[h];
-    const int px = (int)(q % P.cam.W), py = (int)(q / P.cam.W);
-    const uint32_t s0 = ws.pix_start[q];
-    const int m = (int)(ws.pix_start[q + 1] - s0);
-    if (m <= kHeavyKeys) {
-      for (int j = threadIdx.x; j < m; j += kThreads) {
-        K[j] = ws.keys[s0 + j];
-        idx[j] = (uint16_t)j;
-      }
-      __syncthreads();
-      bitonic_sort_idx(K, idx, m, threadIdx.x, kThreads, [] { __syncthreads(); });
-      if (threadIdx.x < GA)
-        blend_fwd<V, GA>(G, P, [&](int k) { return K[idx[k]]; }, m, px, py, pos, opacity, feat, image, T_final,
-                         n_contrib);
-    } else {
-      unsigned long long* ka = ws.ka + s0;
-      cta_sort_global(ws.keys + s0, m, ka, ws.va + s0, ws.kb + s0, ws.vb + s0, S);
-      if (threadIdx.x < GA)
-        blend_fwd<V, GA>(G, P, [&](int k) { return ka[k]; }, m, px, py, pos, opacity, feat, image, T_final,
-                         n_contrib);
-    }
-    __syncthreads();
-  }
-}
-
-// ------------------------------------------------------------ backward ---
-// One pixel: recompute alpha_k and T_k with the forward's chunked scan, then
-// walk the blended chunks back to front accumulating
-// S_k = sum_{j>k} T_j alpha_j (c_j . g) and write
-//   fscal[slot_k] = (T_k alpha_k, dL/dalpha_k = T_k (c_k . g) - S_k / (1 - alpha_k)).
-// chunkT[c] keeps the transmittance in front of chunk c between the passes.
-template <int V, int GA, class KeyAt, class SlotAt>
-__device__ void blend_bwd(const Group<GA>& G, const RP& P, KeyAt key_at, SlotAt slot_at, int m, int nb, int px,
-                          int py, const float* __restrict__ pos, const float* __restrict__ opacity,
-                          const float* __restrict__ feat, const float* __restrict__ d_image,
-                          float2* __restrict__ fscal, float* chunkT) {
+__device__ void blend_bwd_group(const Group<GA>& G, const RP& P, const GroupBuf<GA>& B, uint32_t s0, int m, int nb,
+                                long long pix, const float* __restrict__ feat, const float* __restrict__ d_image,
+                                float2* __restrict__ fscal) {
   const int ch = G.lg * V;
-  const bool active = ch < P.F;
-  const long long pix = (long long)py * P.cam.W + px;
-  // fragments behind the stopping point get zero scalars
-  for (int k = nb + G.lg; k < m; k += GA) fscal[slot_at(k)] = make_float2(0.f, 0.f);
+  for (int k = nb + G.lg; k < m; k += GA) fscal[s0 + B.idx[k]] = make_float2(0.f, 0.f);
   if (nb == 0) return;
-  // pass 1: chunk-start transmittances
   float T = 1.0f;
   const int n_chunks = (nb + GA - 1) / GA;
   for (int c = 0; c < n_chunks; ++c) {
-    if (G.lg == 0) chunkT[c] = T;
-    long long id;
-    const ChunkT<GA> r = chunk_transmittance<GA>(G, P, key_at, c * GA, nb, T, px, py, pos, opacity, feat, id);
+    if (G.lg == 0) B.chunkT[c] = T;
+    const int k = c * GA + G.lg;
+    const bool valid = k < nb;
+    const float a = valid ? B.A[B.idx[k]] : 0.f;
+    const ChunkT<GA> r = chunk_transmittance<GA>(G, P, a, valid, min(GA, nb - c * GA), T);
     T = G.bcast(r.Tn, r.take - 1);
   }
   G.sync();
   float g[V];
-  if (active) load_vec<V>(d_image + pix * P.F + ch, g);
+  if (ch < P.F) load_vec<V>(d_image + pix * P.F + ch, g);
   else
 #pragma unroll
     for (int v = 0; v < V; ++v) g[v] = 0.f;
-  // pass 2: back to front
   float S = 0.f;
   for (int c = n_chunks - 1; c >= 0; --c) {
-    long long id;
-    const ChunkT<GA> r = chunk_transmittance<GA>(G, P, key_at, c * GA, nb, chunkT[c], px, py, pos, opacity, feat, id);
-    // c_k . g for each fragment of the chunk (rows spread over the lanes)
+    const int k = c * GA + G.lg;
+    const bool valid = k < nb;
+    const int q = valid ? B.idx[k] : 0;
+    const float a = valid ? B.A[q] : 0.f;
+    const long long id = valid ? (long long)(B.K[q] & kIdMask) : 0;
+    const ChunkT<GA> r = chunk_transmittance<GA>(G, P, a, valid, min(GA, nb - c * GA), B.chunkT[c]);
     float mydot = 0.f;
-#pragma unroll 4
+#pragma unroll 8
     for (int j = 0; j < r.take; ++j) {
       const long long idj = G.bcast(id, j);
       float part = 0.f;
-      if (active) {
+      if (ch < P.F) {
         float cc[V];
-        load_vec<V>(feat + (long long)P.F * idj + ch, cc);
-        if (P.head && G.lg == 0) cc[0] = 1.0f;
+        load_color<V>(P, feat, idj, ch, cc);
 #pragma unroll
         for (int v = 0; v < V; ++v) part = __fmaf_rn(cc[v], g[v], part);
       }
@@ -634,98 +614,318 @@ __device__ void blend_bwd(const Group<GA>& G, const RP& P, KeyAt key_at, SlotAt 
       if (G.lg == j) mydot = dj;
     }
     const bool mine = G.lg < r.take;
-    const float wk = mine ? __fmul_rn(r.Tk, r.a) : 0.f;
+    const float wk = mine ? __fmul_rn(r.Tk, a) : 0.f;
     const float term = __fmul_rn(wk, mydot);
-    const float suf = G.suffix_scan(term);  // sum over this chunk's fragments at or behind k
-    float behind = G.shift_down(suf);        // ... strictly behind k
-    const float Sk = __fadd_rn(S, behind);
-    const float om = __fsub_rn(1.0f, r.a);
-    const float da = __fsub_rn(__fmul_rn(r.Tk, mydot), __fdiv_rn(Sk, om));
-    if (mine) fscal[slot_at(c * GA + G.lg)] = make_float2(wk, da);
+    const float suf = G.suffix_scan(term);               // this chunk, at or behind k
+    const float Sk = __fadd_rn(S, G.shift_down(suf));    // strictly behind k
+    const float da = __fsub_rn(__fmul_rn(r.Tk, mydot), __fdiv_rn(Sk, __fsub_rn(1.0f, a)));
+    if (mine) fscal[s0 + q] = make_float2(wk, da);
     S = __fadd_rn(S, G.bcast(suf, 0));
   }
 }
 
 template <int V, int GA>
-__global__ void __launch_bounds__(kThreads) k_blend_bwd(RP P, const float* __restrict__ pos,
-                                                         const float* __restrict__ opacity,
-                                                         const float* __restrict__ feat,
+__global__ void __launch_bounds__(kThreads) k_blend_bwd(RP P, const float* __restrict__ feat,
                                                          const int32_t* __restrict__ n_contrib,
                                                          const float* __restrict__ d_image, RasterWs ws) {
-  constexpr int kGroups = kThreads / GA;
-  constexpr int CG = kGroupKeys / kGroups;
   extern __shared__ __align__(16) unsigned char dyn[];
   const Group<GA> G;
   const int group = threadIdx.x / GA;
-  unsigned long long* K = reinterpret_cast<unsigned long long*>(dyn) + group * CG;
-  uint16_t* idx = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned long long*>(dyn) + kGroupKeys) + group * CG;
-  float* chunkT = reinterpret_cast<float*>(reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned long long*>(dyn) +
-                                                                       kGroupKeys) + kGroupKeys) +
-                  group * (CG / GA + 1);
+  const GroupBuf<GA> B(dyn, group);
   const int t = blockIdx.x;
   const int tx = t % P.tiles_x, ty = t / P.tiles_x;
-  for (int p = group; p < P.TW * P.TH; p += kGroups) {
+  for (int p = group; p < P.TW * P.TH; p += GroupBuf<GA>::kGroups) {
     const int px = tx * P.TW + p % P.TW, py = ty * P.TH + p / P.TW;
     if (px >= P.cam.W || py >= P.cam.H) continue;
     const long long q = (long long)py * P.cam.W + px;
     const uint32_t s0 = ws.pix_start[q];
     const int m = (int)(ws.pix_start[q + 1] - s0);
-    if (m > CG || m == 0) continue;
-    for (int j = G.lg; j < m; j += GA) {
-      K[j] = ws.keys[s0 + j];
-      idx[j] = (uint16_t)j;
-    }
-    G.sync();
-    bitonic_sort_idx(K, idx, m, G.lg, GA, [&] { G.sync(); });
-    const int nb = min(m, (int)n_contrib[q]);
-    blend_bwd<V, GA>(G, P, [&](int k) { return K[idx[k]]; }, [&](int k) { return s0 + idx[k]; }, m, nb, px, py, pos,
-                     opacity, feat, d_image, ws.fscal, chunkT);
+    if (m > GroupBuf<GA>::CG || m == 0) continue;
+    load_bucket<GA>(G, ws, s0, m, B);
+    blend_bwd_group<V, GA>(G, P, B, s0, m, min(m, (int)n_contrib[q]), q, feat, d_image, ws.fscal);
     G.sync();
   }
 }
 
+// --------------------------------------------------------------- CTA path ---
+// Large buckets: the whole CTA sorts, scans and gathers for one pixel.
+struct HeavySmem {
+  float warp_tot[kWarps];
+  float prev[kThreads];
+  float red[kThreads];
+  float carry;
+  int stop;
+};
+
+// Inclusive product scan over the CTA's 256 threads (fixed order).
+__device__ __forceinline__ float cta_prod_scan(float x, float* warp_tot) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float t = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x = __fmul_rn(x, t);
+  }
+  __syncthreads();
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  float pre = 1.0f;
+  for (int w = 0; w < wid; ++w) pre = __fmul_rn(pre, warp_tot[w]);
+  return __fmul_rn(pre, x);
+}
+
+// Inclusive suffix-sum scan over the CTA's 256 threads (thread t gets the
+// sum over threads >= t).
+__device__ __forceinline__ float cta_suffix_scan(float x, float* warp_tot) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float t = __shfl_down_sync(0xffffffffu, x, o);
+    if (lane + o < 32) x += t;
+  }
+  __syncthreads();
+  if (lane == 0) warp_tot[wid] = x;
+  __syncthreads();
+  float post = 0.0f;
+  for (int w = kWarps - 1; w > wid; --w) post += warp_tot[w];
+  return x + post;
+}
+
+// Transmittance in front of every fragment of a sorted bucket (product scan
+// in chunks of 256), stored through t_store(k, T_k); returns the number of
+// blended fragments and the final transmittance.
+template <class AlphaAt, class TStore>
+__device__ int cta_transmittance(const RP& P, AlphaAt alpha_at, int m, TStore t_store, HeavySmem& H, float* T_out) {
+  float T = 1.0f;
+  int n = m;
+  for (int b = 0; b < m; b += kThreads) {
+    const int k = b + threadIdx.x;
+    const bool valid = k < m;
+    const float a = valid ? alpha_at(k) : 0.f;
+    const float incl = cta_prod_scan(__fsub_rn(1.0f, a), H.warp_tot);
+    H.prev[threadIdx.x] = incl;
+    if (threadIdx.x == 0) H.stop = INT_MAX;
+    __syncthreads();
+    const float ex = threadIdx.x > 0 ? H.prev[threadIdx.x - 1] : 1.0f;
+    const float Tn = __fmul_rn(T, incl);
+    if (valid) t_store(k, __fmul_rn(T, ex));
+    if (valid && Tn < P.t_min) atomicMin(&H.stop, k);
+    __syncthreads();
+    const int st = H.stop;
+    const int last = st != INT_MAX ? st : min(b + kThreads, m) - 1;
+    if (k == last) H.carry = Tn;
+    __syncthreads();
+    T = H.carry;
+    __syncthreads();
+    if (st != INT_MAX) {
+      n = st + 1;
+      break;
+    }
+  }
+  *T_out = T;
+  return n;
+}
+
+template <int V, int GA, class KeyAt, class AlphaAt, class TLoad>
+__device__ void blend_fwd_cta(const RP& P, KeyAt key_at, AlphaAt alpha_at, TLoad t_load, int n, float T, long long pix,
+                              const float* __restrict__ feat, float* __restrict__ image, float* __restrict__ T_final,
+                              int32_t* __restrict__ n_contrib, HeavySmem& H) {
+  constexpr int kGroups = kThreads / GA;
+  const Group<GA> G;
+  const int group = threadIdx.x / GA;
+  const int ch = G.lg * V;
+  float C[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) C[v] = 0.f;
+  if (ch < P.F) {
+    for (int k = group; k < n; k += kGroups) {
+      const float w = __fmul_rn(t_load(k), alpha_at(k));
+      float c[V];
+      load_color<V>(P, feat, (long long)(key_at(k) & kIdMask), ch, c);
+#pragma unroll
+      for (int v = 0; v < V; ++v) C[v] = __fmaf_rn(w, c[v], C[v]);
+    }
+  }
+  // sum the groups' partial colors, one channel of each lane at a time
+  for (int v = 0; v < V; ++v) {
+    __syncthreads();
+    H.red[threadIdx.x] = C[v];
+    __syncthreads();
+    if (threadIdx.x < GA) {
+      float s = 0.f;
+      for (int g2 = 0; g2 < kGroups; ++g2) s += H.red[g2 * GA + threadIdx.x];
+      C[v] = s;
+    }
+  }
+  if (threadIdx.x < GA) write_pixel<V>(P, pix, threadIdx.x * V, C, image);
+  if (threadIdx.x == 0) {
+    T_final[pix] = T;
+    n_contrib[pix] = n;
+  }
+  __syncthreads();
+}
+
+// Backward on the CTA path: T_k via the forward's scan, c_k . g split over
+// the groups, suffix sums by a CTA-wide reverse scan.
+template <int V, int GA, class KeyAt, class AlphaAt, class SlotAt, class TLoad, class DStore, class DLoad>
+__device__ void blend_bwd_cta(const RP& P, KeyAt key_at, AlphaAt alpha_at, SlotAt slot_at, TLoad t_load,
+                              DStore d_store, DLoad d_load, int nb, long long pix, const float* __restrict__ feat,
+                              const float* __restrict__ d_image, float2* __restrict__ fscal, HeavySmem& H) {
+  constexpr int kGroups = kThreads / GA;
+  const Group<GA> G;
+  const int group = threadIdx.x / GA;
+  const int ch = G.lg * V;
+  float g[V];
+  if (ch < P.F) load_vec<V>(d_image + pix * P.F + ch, g);
+  else
+#pragma unroll
+    for (int v = 0; v < V; ++v) g[v] = 0.f;
+  for (int k = group; k < nb; k += kGroups) {
+    float part = 0.f;
+    if (ch < P.F) {
+      float c[V];
+      load_color<V>(P, feat, (long long)(key_at(k) & kIdMask), ch, c);
+#pragma unroll
+      for (int v = 0; v < V; ++v) part = __fmaf_rn(c[v], g[v], part);
+    }
+    const float d = G.sum(part);
+    if (G.lg == 0) d_store(k, d);
+  }
+  __syncthreads();
+  float S = 0.f;  // sum over the fragments behind the current 256-block
+  const int n_blocks = (nb + kThreads - 1) / kThreads;
+  for (int blk = n_blocks - 1; blk >= 0; --blk) {
+    const int k = blk * kThreads + threadIdx.x;
+    const bool valid = k < nb;
+    const float a = valid ? alpha_at(k) : 0.f;
+    const float Tk = valid ? t_load(k) : 0.f;
+    const float dk = valid ? d_load(k) : 0.f;
+    const float wk = __fmul_rn(Tk, a);
+    const float term = __fmul_rn(wk, dk);
+    const float suf = cta_suffix_scan(term, H.warp_tot);
+    H.prev[threadIdx.x] = suf;
+    __syncthreads();
+    const float behind = threadIdx.x + 1 < kThreads ? H.prev[threadIdx.x + 1] : 0.f;
+    const float Sk = __fadd_rn(S, behind);
+    if (valid) fscal[slot_at(k)] = make_float2(wk, __fsub_rn(__fmul_rn(Tk, dk), __fdiv_rn(Sk, __fsub_rn(1.0f, a))));
+    S = __fadd_rn(S, H.prev[0]);
+    __syncthreads();
+  }
+}
+
+struct HeavyBuf {
+  unsigned long long* K;
+  float* A;
+  uint16_t* idx;
+  float* Tk;
+  float* D;
+  __device__ explicit HeavyBuf(unsigned char* dyn) {
+    K = reinterpret_cast<unsigned long long*>(dyn);
+    A = reinterpret_cast<float*>(K + kHeavyKeys);
+    Tk = A + kHeavyKeys;
+    D = Tk + kHeavyKeys;
+    idx = reinterpret_cast<uint16_t*>(D + kHeavyKeys);
+  }
+  static constexpr size_t bytes() { return (size_t)kHeavyKeys * (8 + 4 + 4 + 4 + 2); }
+};
+
+// Sort one large bucket: in shared memory (m <= kHeavyKeys) through the
+// index array, or in global memory (ka/va) beyond that.
+__device__ void cta_order_bucket(const RasterWs& ws, uint32_t s0, int m, const HeavyBuf& B, SortSmem& S) {
+  if (m <= kHeavyKeys) {
+    for (int j = threadIdx.x; j < m; j += kThreads) {
+      B.K[j] = ws.keys[s0 + j];
+      B.A[j] = ws.alpha[s0 + j];
+      B.idx[j] = (uint16_t)j;
+    }
+    __syncthreads();
+    bitonic_sort_idx(B.K, B.idx, m, threadIdx.x, kThreads, [] { __syncthreads(); });
+  } else {
+    cta_sort_global(ws.keys + s0, m, ws.ka + s0, ws.va + s0, ws.kb + s0, ws.vb + s0, S);
+  }
+}
+
 template <int V, int GA>
-__global__ void __launch_bounds__(kThreads) k_blend_bwd_heavy(RP P, const float* __restrict__ pos,
-                                                               const float* __restrict__ opacity,
-                                                               const float* __restrict__ feat,
-                                                               const int32_t* __restrict__ n_contrib,
-                                                               const float* __restrict__ d_image, RasterWs ws) {
+__global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const float* __restrict__ feat, RasterWs ws,
+                                                               float* __restrict__ image, float* __restrict__ T_final,
+                                                               int32_t* __restrict__ n_contrib) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ SortSmem S;
-  unsigned long long* K = reinterpret_cast<unsigned long long*>(dyn);
-  uint16_t* idx = reinterpret_cast<uint16_t*>(K + kHeavyKeys);
-  const Group<GA> G;
+  __shared__ HeavySmem H;
+  const HeavyBuf B(dyn);
   const uint32_t n_heavy = *ws.heavy_count;
   for (uint32_t h = blockIdx.x; h < n_heavy; h += gridDim.x) {
     const long long q = ws.heavy[h];
-    const int px = (int)(q % P.cam.W), py = (int)(q / P.cam.W);
     const uint32_t s0 = ws.pix_start[q];
     const int m = (int)(ws.pix_start[q + 1] - s0);
-    const int nb = min(m, (int)n_contrib[q]);
+    cta_order_bucket(ws, s0, m, B, S);
+    float T;
     if (m <= kHeavyKeys) {
-      for (int j = threadIdx.x; j < m; j += kThreads) {
-        K[j] = ws.keys[s0 + j];
-        idx[j] = (uint16_t)j;
-      }
+      auto key_at = [&](int k) { return B.K[B.idx[k]]; };
+      auto alpha_at = [&](int k) { return B.A[B.idx[k]]; };
+      const int n = cta_transmittance(P, alpha_at, m, [&](int k, float v) { B.Tk[k] = v; }, H, &T);
       __syncthreads();
-      bitonic_sort_idx(K, idx, m, threadIdx.x, kThreads, [] { __syncthreads(); });
-      // the bucket's global-sort scratch holds the chunk transmittances
-      if (threadIdx.x < GA)
-        blend_bwd<V, GA>(G, P, [&](int k) { return K[idx[k]]; }, [&](int k) { return s0 + idx[k]; }, m, nb, px, py,
-                         pos, opacity, feat, d_image, ws.fscal, reinterpret_cast<float*>(ws.kb + s0));
+      blend_fwd_cta<V, GA>(P, key_at, alpha_at, [&](int k) { return B.Tk[k]; }, n, T, q, feat, image, T_final,
+                           n_contrib, H);
     } else {
-      unsigned long long* ka = ws.ka + s0;
-      uint32_t* va = ws.va + s0;
-      cta_sort_global(ws.keys + s0, m, ka, va, ws.kb + s0, ws.vb + s0, S);
-      // the sort's scratch keys hold the chunk transmittances of this pixel
-      if (threadIdx.x < GA)
-        blend_bwd<V, GA>(G, P, [&](int k) { return ka[k]; }, [&](int k) { return s0 + va[k]; }, m, nb, px, py, pos,
-                         opacity, feat, d_image, ws.fscal, reinterpret_cast<float*>(ws.kb + s0));
+      const unsigned long long* ka = ws.ka + s0;
+      const uint32_t* va = ws.va + s0;
+      float2* tmp = reinterpret_cast<float2*>(ws.kb + s0);
+      auto key_at = [&](int k) { return ka[k]; };
+      auto alpha_at = [&](int k) { return ws.alpha[s0 + va[k]]; };
+      const int n = cta_transmittance(P, alpha_at, m, [&](int k, float v) { tmp[k].x = v; }, H, &T);
+      __syncthreads();
+      blend_fwd_cta<V, GA>(P, key_at, alpha_at, [&](int k) { return tmp[k].x; }, n, T, q, feat, image, T_final,
+                           n_contrib, H);
     }
     __syncthreads();
   }
 }
 
+template <int V, int GA>
+__global__ void __launch_bounds__(kThreads) k_blend_bwd_heavy(RP P, const float* __restrict__ feat,
+                                                               const int32_t* __restrict__ n_contrib,
+                                                               const float* __restrict__ d_image, RasterWs ws) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ SortSmem S;
+  __shared__ HeavySmem H;
+  const HeavyBuf B(dyn);
+  const uint32_t n_heavy = *ws.heavy_count;
+  for (uint32_t h = blockIdx.x; h < n_heavy; h += gridDim.x) {
+    const long long q = ws.heavy[h];
+    const uint32_t s0 = ws.pix_start[q];
+    const int m = (int)(ws.pix_start[q + 1] - s0);
+    const int nb = min(m, (int)n_contrib[q]);
+    cta_order_bucket(ws, s0, m, B, S);
+    float T;
+    if (m <= kHeavyKeys) {
+      auto key_at = [&](int k) { return B.K[B.idx[k]]; };
+      auto alpha_at = [&](int k) { return B.A[B.idx[k]]; };
+      auto slot_at = [&](int k) { return s0 + B.idx[k]; };
+      for (int k = nb + (int)threadIdx.x; k < m; k += kThreads) ws.fscal[slot_at(k)] = make_float2(0.f, 0.f);
+      cta_transmittance(P, alpha_at, nb, [&](int k, float v) { B.Tk[k] = v; }, H, &T);
+      __syncthreads();
+      blend_bwd_cta<V, GA>(P, key_at, alpha_at, slot_at, [&](int k) { return B.Tk[k]; },
+                           [&](int k, float v) { B.D[k] = v; }, [&](int k) { return B.D[k]; }, nb, q, feat, d_image,
+                           ws.fscal, H);
+    } else {
+      const unsigned long long* ka = ws.ka + s0;
+      const uint32_t* va = ws.va + s0;
+      float2* tmp = reinterpret_cast<float2*>(ws.kb + s0);
+      auto key_at = [&](int k) { return ka[k]; };
+      auto alpha_at = [&](int k) { return ws.alpha[s0 + va[k]]; };
+      auto slot_at = [&](int k) { return s0 + va[k]; };
+      for (int k = nb + (int)threadIdx.x; k < m; k += kThreads) ws.fscal[slot_at(k)] = make_float2(0.f, 0.f);
+      cta_transmittance(P, alpha_at, nb, [&](int k, float v) { tmp[k].x = v; }, H, &T);
+      __syncthreads();
+      blend_bwd_cta<V, GA>(P, key_at, alpha_at, slot_at, [&](int k) { return tmp[k].x; },
+                           [&](int k, float v) { tmp[k].y = v; }, [&](int k) { return tmp[k].y; }, nb, q, feat,
+                           d_image, ws.fscal, H);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------ per-point gradient ---
 // Per point: gather the scalars of its (at most four) splats and the
 // upstream-gradient rows of their pixels.  d_feat row = sum_k (T_k alpha_k) g_k;
 // d alpha_h = sum_k w_k [unclamped] dL/dalpha_k.
@@ -751,18 +951,20 @@ __global__ void __launch_bounds__(kThreads) k_point_grad(RP P, const float* __re
     if ((sl.x & sl.y & sl.z & sl.w) != kNoSlot) {
       splat_point(P, pos, id, s);
       const float ah = point_alpha_h(P, opacity, feat, id, &e_h0);
+      float2 sc[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) sc[k] = slots[k] == kNoSlot ? make_float2(0.f, 0.f) : __ldg(ws.fscal + slots[k]);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (slots[k] == kNoSlot) continue;
-        const float2 sc = __ldg(ws.fscal + slots[k]);
         const float w = corner_weight(s.f, k & 1, k >> 1);
-        if (__fmul_rn(ah, w) <= P.alpha_max) dah = __fmaf_rn(w, sc.y, dah);
+        if (__fmul_rn(ah, w) <= P.alpha_max) dah = __fmaf_rn(w, sc[k].y, dah);
         if (active) {
           const long long pix = (long long)(s.f.j0 + (k >> 1)) * P.cam.W + (s.f.i0 + (k & 1));
           float g[V];
           load_vec<V>(d_image + pix * P.F + ch, g);
 #pragma unroll
-          for (int v = 0; v < V; ++v) dc[v] = __fmaf_rn(sc.x, g[v], dc[v]);
+          for (int v = 0; v < V; ++v) dc[v] = __fmaf_rn(sc[k].x, g[v], dc[v]);
         }
       }
     }
@@ -810,7 +1012,6 @@ inpc_status make_rp(const inpc_camera* cam, const inpc_raster_opts* o, int64_t n
   P.alpha_max = o->alpha_max;
   P.n = n;
   P.n_pix = (long long)cam->width * cam->height;
-  if (4 * n > (int64_t)UINT32_MAX - 1) return fail(INPC_ERR_CAPACITY, "too many fragments");
   return INPC_OK;
 }
 
@@ -820,6 +1021,7 @@ int next_pow2(int x) {
   return p;
 }
 
+// (V, GA): V channels per lane, GA lanes per pixel.
 template <class Fn>
 inpc_status dispatch(int F, Fn&& fn) {
   if (F % 4 == 0) {
@@ -854,19 +1056,11 @@ void set_smem(K kernel, size_t bytes, std::once_flag& once) {
   std::call_once(once, [&] { cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); });
 }
 
-constexpr size_t kGroupSmemFwd = (size_t)kGroupKeys * (8 + 2);
-constexpr size_t kHeavySmemFwd = (size_t)kHeavyKeys * (8 + 2);
-
-template <int V, int GA>
-size_t group_smem_bwd() {
-  constexpr int kGroups = kThreads / GA;
-  return (size_t)kGroupKeys * (8 + 2) + (size_t)kGroups * (kGroupKeys / kGroups / GA + 1) * 4;
-}
-constexpr size_t kHeavySmemBwd = (size_t)kHeavyKeys * (8 + 2);
-
-// Forward binning: per-pixel counts, offsets, buckets, per-point slots and
-// the list of pixels for the CTA path (kept in the workspace for the backward).
-inpc_status bin_fragments(const RP& P, const float* pos, const RasterWs& ws, uint32_t cap_group, cudaStream_t s) {
+// Forward binning: per-pixel counts, offsets, buckets (keys and alphas),
+// per-point slots and the list of pixels for the CTA path (all kept in the
+// workspace for the backward).
+inpc_status bin_fragments(const RP& P, const float* pos, const float* opacity, const float* feat, const RasterWs& ws,
+                          uint32_t cap_group, cudaStream_t s) {
   INPC_CUDA(cudaMemsetAsync(ws.pix_count, 0, sizeof(uint32_t) * P.n_pix, s), "clear pixel counts");
   if (P.n > 0) {
     k_pix_count<<<point_grid(P.n), 256, 0, s>>>(P, pos, ws.pix_count);
@@ -878,7 +1072,8 @@ inpc_status bin_fragments(const RP& P, const float* pos, const RasterWs& ws, uin
                                                                  ws.heavy_count, ws.pix_start);
   INPC_TRY(check_launch("k_heavy_list"));
   if (P.n > 0) {
-    k_pix_scatter<<<point_grid(P.n), 256, 0, s>>>(P, pos, ws.pix_start, ws.pix_count, ws.keys, ws.pslot);
+    k_pix_scatter<<<point_grid(P.n), 256, 0, s>>>(P, pos, opacity, feat, ws.pix_start, ws.pix_count, ws.keys, ws.alpha,
+                                                  ws.pslot);
     INPC_TRY(check_launch("k_pix_scatter"));
   }
   return INPC_OK;
@@ -887,15 +1082,15 @@ inpc_status bin_fragments(const RP& P, const float* pos, const RasterWs& ws, uin
 template <int V, int GA>
 inpc_status launch_fwd(const RP& P, const float* pos, const float* opacity, const float* feat, const RasterWs& ws,
                        float* image, float* T_final, int32_t* n_contrib, cudaStream_t s) {
-  constexpr int CG = kGroupKeys / (kThreads / GA);
-  INPC_TRY(bin_fragments(P, pos, ws, CG, s));
+  INPC_TRY(bin_fragments(P, pos, opacity, feat, ws, GroupBuf<GA>::CG, s));
   static std::once_flag f1, f2;
-  set_smem(k_blend_fwd<V, GA>, kGroupSmemFwd, f1);
-  set_smem(k_blend_fwd_heavy<V, GA>, kHeavySmemFwd, f2);
-  k_blend_fwd<V, GA><<<P.n_tiles, kThreads, kGroupSmemFwd, s>>>(P, pos, opacity, feat, ws, image, T_final, n_contrib);
+  const size_t gs = GroupBuf<GA>::bytes();
+  set_smem(k_blend_fwd<V, GA>, gs, f1);
+  set_smem(k_blend_fwd_heavy<V, GA>, HeavyBuf::bytes(), f2);
+  k_blend_fwd<V, GA><<<P.n_tiles, kThreads, gs, s>>>(P, feat, ws, image, T_final, n_contrib);
   INPC_TRY(check_launch("k_blend_fwd"));
-  k_blend_fwd_heavy<V, GA><<<device_sm_count(), kThreads, kHeavySmemFwd, s>>>(P, pos, opacity, feat, ws, image,
-                                                                              T_final, n_contrib);
+  k_blend_fwd_heavy<V, GA><<<device_sm_count(), kThreads, HeavyBuf::bytes(), s>>>(P, feat, ws, image, T_final,
+                                                                                   n_contrib);
   return check_launch("k_blend_fwd_heavy");
 }
 
@@ -904,13 +1099,12 @@ inpc_status launch_bwd(const RP& P, const float* pos, const float* opacity, cons
                        const int32_t* n_contrib, const float* d_image, const RasterWs& ws, float* d_opacity,
                        float* d_feat, cudaStream_t s) {
   static std::once_flag f1, f2;
-  const size_t gs = group_smem_bwd<V, GA>();
+  const size_t gs = GroupBuf<GA>::bytes();
   set_smem(k_blend_bwd<V, GA>, gs, f1);
-  set_smem(k_blend_bwd_heavy<V, GA>, kHeavySmemBwd, f2);
-  k_blend_bwd<V, GA><<<P.n_tiles, kThreads, gs, s>>>(P, pos, opacity, feat, n_contrib, d_image, ws);
+  set_smem(k_blend_bwd_heavy<V, GA>, HeavyBuf::bytes(), f2);
+  k_blend_bwd<V, GA><<<P.n_tiles, kThreads, gs, s>>>(P, feat, n_contrib, d_image, ws);
   INPC_TRY(check_launch("k_blend_bwd"));
-  k_blend_bwd_heavy<V, GA><<<device_sm_count(), kThreads, kHeavySmemBwd, s>>>(P, pos, opacity, feat, n_contrib,
-                                                                              d_image, ws);
+  k_blend_bwd_heavy<V, GA><<<device_sm_count(), kThreads, HeavyBuf::bytes(), s>>>(P, feat, n_contrib, d_image, ws);
   INPC_TRY(check_launch("k_blend_bwd_heavy"));
   constexpr int kGroups = kThreads / GA;
   const long long grid = std::min<long long>(ceil_div(P.n, kGroups), (long long)device_sm_count() * 32);
