@@ -104,6 +104,31 @@ inpc_status inpc_sample_octree(const inpc_octree* tree, uint64_t seed, uint32_t 
                                int32_t* leaf_idx_out, float* pos_out, int32_t* leaf_counts_out,
                                void* workspace, size_t workspace_bytes, inpc_stream_t stream);
 
+/* Allocation-free variant of inpc_sample_octree (the paper has no
+ * counterpart; this is a deployment aid).  Some callers cannot allocate
+ * device memory at all: a host application or engine that owns every byte of
+ * the device behind its own allocator, a frame loop that must not stall on a
+ * cudaMalloc, or a plugin that is handed buffers but no allocation rights.
+ * They still pass the octree and the output arrays; the sampler's scratch
+ * lives in a file-scope device array of INPC_SAMPLE_STATIC_SCRATCH_BYTES
+ * (4 MiB + 64 KiB: about 262,000 leaves), which every GPU that loads this
+ * library holds until the process exits.
+ *   - Same definition, outputs and device status bits as inpc_sample_octree
+ *     (the status word sits at the start of the static array).
+ *   - Returns INPC_ERR_CAPACITY, before touching the device, when the tree
+ *     needs more scratch than the array holds.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture.
+ *   - Allocates nothing (no cudaMalloc, no library allocation); every call on
+ *     a device shares the one array, each call clears what must start at
+ *     zero, and calls whose GPU work overlaps (other streams, other host
+ *     threads) race on it. */
+#define INPC_SAMPLE_STATIC_SCRATCH_BYTES ((4u << 20) + (64u << 10))
+inpc_status inpc_sample_octree_noalloc(const inpc_octree* tree, uint64_t seed, uint32_t view_id, int64_t n_samples,
+                                       int32_t* leaf_idx_out, float* pos_out, int32_t* leaf_counts_out,
+                                       inpc_stream_t stream);
+
 /* ======================================================================== */
 /* (b) Multi-resolution hash-grid query                                     */
 /* ======================================================================== */

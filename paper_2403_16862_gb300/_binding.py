@@ -33,7 +33,7 @@ INPC_OPACITY_FROM_CH0 = 1
 # Every symbol the header declares; tests check the library exports them.
 DECLARED = [
     "inpc_last_error", "inpc_version", "inpc_kernel_launches", "inpc_read_device_status",
-    "inpc_sample_workspace_size", "inpc_sample_octree",
+    "inpc_sample_workspace_size", "inpc_sample_octree", "inpc_sample_octree_noalloc",
     "inpc_hashgrid_n_entries", "inpc_query_hashgrid", "inpc_query_hashgrid_bwd",
     "inpc_rasterize_workspace_size", "inpc_rasterize_fwd", "inpc_rasterize_bwd",
 ]
@@ -89,6 +89,8 @@ def load(path: str = LIB_PATH):
         L.inpc_sample_workspace_size.argtypes = [C.c_int64, C.c_int64, C.POINTER(C.c_size_t)]
         L.inpc_sample_octree.argtypes = [C.POINTER(InpcOctree), C.c_uint64, C.c_uint32, C.c_int64, _P, _P, _P, _P,
                                          C.c_size_t, _P]
+        L.inpc_sample_octree_noalloc.argtypes = [C.POINTER(InpcOctree), C.c_uint64, C.c_uint32, C.c_int64, _P, _P,
+                                                 _P, _P]
         L.inpc_hashgrid_n_entries.argtypes = [C.POINTER(InpcHashgridDesc), C.POINTER(C.c_int64)]
         L.inpc_query_hashgrid.argtypes = [C.POINTER(InpcHashgridDesc), _P, _P, C.c_int64, _P, _P]
         L.inpc_query_hashgrid_bwd.argtypes = [C.POINTER(InpcHashgridDesc), _P, _P, C.c_int64, _P, _P]
@@ -136,6 +138,15 @@ def inpc_sample_octree(tree: InpcOctree, seed: int, view_id: int, n_samples: int
                        pos_out: int, leaf_counts_out, workspace: int, workspace_bytes: int, stream: int):
     check(load().inpc_sample_octree(C.byref(tree), C.c_uint64(seed), C.c_uint32(view_id), n_samples, leaf_idx_out,
                                     pos_out, leaf_counts_out, workspace, workspace_bytes, stream))
+
+
+INPC_SAMPLE_STATIC_SCRATCH_BYTES = (4 << 20) + (64 << 10)
+
+
+def inpc_sample_octree_noalloc(tree: InpcOctree, seed: int, view_id: int, n_samples: int, leaf_idx_out: int,
+                               pos_out: int, leaf_counts_out, stream: int):
+    check(load().inpc_sample_octree_noalloc(C.byref(tree), C.c_uint64(seed), C.c_uint32(view_id), n_samples,
+                                            leaf_idx_out, pos_out, leaf_counts_out, stream))
 
 
 def inpc_hashgrid_n_entries(desc: InpcHashgridDesc) -> int:
