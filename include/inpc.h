@@ -197,8 +197,9 @@ typedef enum {
 
 /*   opacity_mode  inpc_opacity_mode
  *   n_channels    F, 1..128 (F/4 <= 32 when F % 4 == 0, else F <= 32)
- *   feat_dtype    INPC_F32 (INPC_BF16 reserved)
- *   image_dtype   INPC_F32 (INPC_BF16 reserved)
+ *   feat_dtype    INPC_F32 or INPC_BF16 (dtype of the feature rows)
+ *   image_dtype   must equal feat_dtype (dtype of the image); blending,
+ *                 transmittance and every gradient stay FP32
  *   t_min         blending stops after the fragment that takes T below it (1e-4)
  *   alpha_max     splat opacity clamp, alpha = min(alpha_h w, alpha_max), < 1 (0.99)
  *   tile_w/tile_h screen tile in pixels, tile_w * tile_h <= 256; 0 = default 16 x 16 */

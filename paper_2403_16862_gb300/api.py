@@ -135,13 +135,18 @@ class RasterOptions:
     alpha_max: float = 0.99
     tile_w: int = 0
     tile_h: int = 0
+    bf16: bool = False  # BF16 feature rows and image (FP32 arithmetic and gradients)
+
+    @property
+    def dtype(self):
+        return torch.bfloat16 if self.bf16 else torch.float32
 
     def c(self) -> B.InpcRasterOpts:
         o = B.InpcRasterOpts()
         o.opacity_mode = B.INPC_OPACITY_FROM_CH0 if self.head_mode else B.INPC_OPACITY_GIVEN
         o.n_channels = self.n_channels
-        o.feat_dtype = B.INPC_F32
-        o.image_dtype = B.INPC_F32
+        o.feat_dtype = B.INPC_BF16 if self.bf16 else B.INPC_F32
+        o.image_dtype = o.feat_dtype
         o.t_min = self.t_min
         o.alpha_max = self.alpha_max
         o.tile_w = self.tile_w
@@ -156,7 +161,7 @@ def rasterize_workspace_size(cam, opts: RasterOptions, n: int) -> int:
 def rasterize_fwd(cam, opts: RasterOptions, pos, feat, opacity=None, ws=None, out=None):
     """Returns (image [H,W,F], T_final [H,W], n_contrib [H,W], ws)."""
     _need(pos, torch.float32, "pos")
-    _need(feat, torch.float32, "feat")
+    _need(feat, opts.dtype, "feat")
     if opacity is not None:
         _need(opacity, torch.float32, "opacity")
     n = pos.shape[0]
@@ -166,7 +171,7 @@ def rasterize_fwd(cam, opts: RasterOptions, pos, feat, opacity=None, ws=None, ou
         ws = workspace(need, pos.device)
     H, W, F = cam.height, cam.width, opts.n_channels
     if out is None:
-        image = torch.empty(H, W, F, dtype=torch.float32, device=pos.device)
+        image = torch.empty(H, W, F, dtype=opts.dtype, device=pos.device)
         T_final = torch.empty(H, W, dtype=torch.float32, device=pos.device)
         n_contrib = torch.empty(H, W, dtype=torch.int32, device=pos.device)
     else:
@@ -181,7 +186,7 @@ def rasterize_bwd(cam, opts: RasterOptions, pos, feat, opacity, T_final, n_contr
     _need(d_image, torch.float32, "d_image")
     n = pos.shape[0]
     if out is None:
-        d_feat = torch.empty_like(feat)
+        d_feat = torch.empty(feat.shape, dtype=torch.float32, device=feat.device)
         d_opacity = None if opts.head_mode else torch.empty(n, dtype=torch.float32, device=pos.device)
     else:
         d_opacity, d_feat = out

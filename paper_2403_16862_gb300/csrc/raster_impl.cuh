@@ -1,4 +1,4 @@
-// raster.cu -- differentiable bilinear point rasterizer (Sec. 3.4, Eq. 1,
+// raster_impl.cuh -- differentiable bilinear point rasterizer (Sec. 3.4, Eq. 1,
 // Eq. 5, Eq. 6, App. A.6, Algorithm 1), forward and backward.
 //
 // Ordering.  Algorithm 1 sorts all splats globally by (pixel, depth).  Here
@@ -26,6 +26,10 @@
 // kernel then gathers its (at most four) slots and the matching
 // upstream-gradient rows and writes the point's gradient with plain stores:
 // no atomics, no zero-fill pass.
+#pragma once
+
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <climits>
 #include <mutex>
@@ -40,8 +44,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kIdBits = 25;
 constexpr unsigned long long kIdMask = (1ull << kIdBits) - 1;
-constexpr int kGroupKeys = 6144;  // shared-memory bucket entries per CTA on the group path (split among groups)
-constexpr int kHeavyKeys = 8192;  // shared-memory bucket entries on the CTA path
+constexpr int kHeavyKeys = 2048;  // shared-memory bucket entries on the CTA path (larger buckets sort in global memory)
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 
 struct RP {
@@ -49,6 +52,7 @@ struct RP {
   int TW, TH, tiles_x, tiles_y, n_tiles;
   int F;
   int head;
+  int bf16;  // feature rows and image in BF16 (arithmetic stays FP32)
   float t_min, alpha_max;
   long long n;
   long long n_pix;
@@ -115,11 +119,18 @@ __device__ __forceinline__ long long corner_pixel(const RP& P, const Footprint& 
   return (long long)py * P.cam.W + px;
 }
 
+// Feature elements are FP32 or BF16; all arithmetic is FP32.
+__device__ __forceinline__ float ld1(const float* __restrict__ p) { return __ldg(p); }
+__device__ __forceinline__ float ld1(const __nv_bfloat16* __restrict__ p) {
+  return __uint_as_float(((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p))) << 16);
+}
+
 // Point opacity alpha_h: given, or 1 - exp(-exp(h0)) (Sec. 3.3) in head mode.
+template <class FT>
 __device__ __forceinline__ float point_alpha_h(const RP& P, const float* __restrict__ opacity,
-                                               const float* __restrict__ feat, long long id, float* e_h0) {
+                                               const FT* __restrict__ feat, long long id, float* e_h0) {
   if (P.head) {
-    const float e = expf(__ldg(feat + (long long)P.F * id));
+    const float e = expf(ld1(feat + (long long)P.F * id));
     if (e_h0) *e_h0 = e;
     return -expm1f(-e);
   }
@@ -145,9 +156,10 @@ __global__ void __launch_bounds__(256) k_pix_count(RP P, const float* __restrict
   }
 }
 
+template <class FT>
 __global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restrict__ pos,
                                                      const float* __restrict__ opacity,
-                                                     const float* __restrict__ feat,
+                                                     const FT* __restrict__ feat,
                                                      const uint32_t* __restrict__ pix_start,
                                                      uint32_t* __restrict__ pix_count,
                                                      unsigned long long* __restrict__ keys,
@@ -410,6 +422,9 @@ __device__ __forceinline__ void load_vec(const float* __restrict__ p, float* c) 
   if (V == 4) {
     const float4 t = __ldg(reinterpret_cast<const float4*>(p));
     c[0] = t.x; c[1] = t.y; c[2] = t.z; c[3] = t.w;
+  } else if (V == 2) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+    c[0] = t.x; c[1] = t.y;
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) c[v] = __ldg(p + v);
@@ -419,7 +434,25 @@ __device__ __forceinline__ void load_vec(const float* __restrict__ p, float* c) 
 // This lane's V channels of a point's blended color: its features, with
 // channel 0 replaced by 1 in head mode.
 template <int V>
-__device__ __forceinline__ void load_color(const RP& P, const float* __restrict__ feat, long long id, int ch, float* c) {
+__device__ __forceinline__ void load_vec(const __nv_bfloat16* __restrict__ p, float* c) {
+  if (V == 4) {
+    const uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
+    c[0] = __uint_as_float(raw.x << 16);
+    c[1] = __uint_as_float(raw.x & 0xFFFF0000u);
+    c[2] = __uint_as_float(raw.y << 16);
+    c[3] = __uint_as_float(raw.y & 0xFFFF0000u);
+  } else if (V == 2) {
+    const uint32_t raw = __ldg(reinterpret_cast<const unsigned int*>(p));
+    c[0] = __uint_as_float(raw << 16);
+    c[1] = __uint_as_float(raw & 0xFFFF0000u);
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) c[v] = ld1(p + v);
+  }
+}
+
+template <int V, class FT>
+__device__ __forceinline__ void load_color(const RP& P, const FT* __restrict__ feat, long long id, int ch, float* c) {
   load_vec<V>(feat + (long long)P.F * id + ch, c);
   if (P.head && ch == 0) c[0] = 1.0f;
 }
@@ -429,9 +462,31 @@ __device__ __forceinline__ void write_pixel(const RP& P, long long pix, int ch, 
   if (ch >= P.F) return;
   float* o = image + pix * P.F + ch;
   if (V == 4) __stcs(reinterpret_cast<float4*>(o), make_float4(C[0], C[1], C[2], C[3]));
+  else if (V == 2) __stcs(reinterpret_cast<float2*>(o), make_float2(C[0], C[1]));
   else
 #pragma unroll
     for (int v = 0; v < V; ++v) __stcs(o + v, C[v]);
+}
+
+template <int V>
+__device__ __forceinline__ void write_pixel(const RP& P, long long pix, int ch, const float* C,
+                                            __nv_bfloat16* __restrict__ image) {
+  if (ch >= P.F) return;
+  __nv_bfloat16* o = image + pix * P.F + ch;
+  if (V == 4) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(C[0], C[1]);
+    __nv_bfloat162 b = __floats2bfloat162_rn(C[2], C[3]);
+    uint2 raw;
+    raw.x = *reinterpret_cast<uint32_t*>(&a);
+    raw.y = *reinterpret_cast<uint32_t*>(&b);
+    __stcs(reinterpret_cast<uint2*>(o), raw);
+  } else if (V == 2) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(C[0], C[1]);
+    *reinterpret_cast<__nv_bfloat162*>(o) = a;
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) o[v] = __float2bfloat16_rn(C[v]);
+  }
 }
 
 // Transmittance of one chunk of GA fragments: lane j holds the alpha of
@@ -463,41 +518,97 @@ __device__ __forceinline__ ChunkT<GA> chunk_transmittance(const Group<GA>& G, co
 }
 
 // ------------------------------------------------------ group path (fwd) ---
-// One pixel per group of GA lanes; its sorted bucket in shared memory (keys
-// K, alphas A, order idx).
-template <int V, int GA>
-__device__ void blend_fwd_group(const Group<GA>& G, const RP& P, const unsigned long long* K, const float* A,
-                                const uint16_t* idx, int m, long long pix, const float* __restrict__ feat,
-                                float* __restrict__ image, float* __restrict__ T_final,
-                                int32_t* __restrict__ n_contrib) {
+// One pixel per group of GA lanes.  The bucket (at most GA * kRegMax
+// fragments) is sorted in registers: lane lg holds elements r * GA + lg,
+// r < R, and a bitonic network exchanges across lanes (shuffles) for strides
+// below GA and between registers above.  After the sort, register r of the
+// group is chunk r of the blending order.  Each element carries its bucket
+// position in the low 8 bits (key << 8 | position), which locates its alpha.
+constexpr int kRegMax = 8;
+
+template <int GA, int R>
+__device__ __forceinline__ void reg_sort(const Group<GA>& G, unsigned long long (&key)[R]) {
+  constexpr int P2 = GA * R;
+#pragma unroll
+  for (int k = 2; k <= P2; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= GA) {
+        const int jr = j / GA;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int r2 = r ^ jr;
+          if (r2 > r) {
+            const bool up = (((r * GA + G.lg) & k) == 0);
+            const unsigned long long x = key[r], y = key[r2];
+            if ((x > y) == up) {
+              key[r] = y;
+              key[r2] = x;
+            }
+          }
+        }
+      } else {
+        const bool lower = (G.lg & j) == 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const bool up = (((r * GA + G.lg) & k) == 0);
+          const unsigned long long o = __shfl_xor_sync(G.mask, key[r], j, GA);
+          key[r] = (lower == up) ? (key[r] < o ? key[r] : o) : (key[r] > o ? key[r] : o);
+        }
+      }
+    }
+  }
+}
+
+template <int GA, int R>
+__device__ __forceinline__ void load_sorted(const Group<GA>& G, const unsigned long long* __restrict__ keys,
+                                            uint32_t s0, int m, unsigned long long (&key)[R]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int e = r * GA + G.lg;
+    key[r] = e < m ? (keys[s0 + e] << 8) | (unsigned long long)e : ~0ull;
+  }
+  reg_sort<GA, R>(G, key);
+}
+
+__device__ __forceinline__ long long reg_id(unsigned long long k) { return (long long)((k >> 8) & kIdMask); }
+__device__ __forceinline__ uint32_t reg_pos(unsigned long long k) { return (uint32_t)(k & 0xFF); }
+
+template <int V, int GA, class FT, int R>
+__device__ void blend_fwd_reg(const Group<GA>& G, const RP& P, const RasterWs& ws, uint32_t s0, int m, long long pix,
+                              const FT* __restrict__ feat, FT* __restrict__ image, float* __restrict__ T_final,
+                              int32_t* __restrict__ n_contrib) {
+  unsigned long long key[R];
+  load_sorted<GA, R>(G, ws.keys, s0, m, key);
   const int ch = G.lg * V;
   float C[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) C[v] = 0.f;
   float T = 1.0f;
   int cnt = 0;
-  for (int b = 0; b < m; b += GA) {
-    const int k = b + G.lg;
-    const bool valid = k < m;
-    const int q = valid ? idx[k] : 0;
-    const float a = valid ? A[q] : 0.f;
-    const long long id = valid ? (long long)(K[q] & kIdMask) : 0;
-    const ChunkT<GA> r = chunk_transmittance<GA>(G, P, a, valid, min(GA, m - b), T);
-    const float wk = __fmul_rn(r.Tk, a);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int b = r * GA;
+    if (b >= m) break;
+    const bool valid = b + G.lg < m;
+    const float a = valid ? ws.alpha[s0 + reg_pos(key[r])] : 0.f;
+    const long long id = valid ? reg_id(key[r]) : 0;
+    const ChunkT<GA> ct = chunk_transmittance<GA>(G, P, a, valid, min(GA, m - b), T);
+    const float wk = __fmul_rn(ct.Tk, a);
 #pragma unroll 8
-    for (int j = 0; j < r.take; ++j) {
+    for (int j = 0; j < ct.take; ++j) {
       const long long idj = G.bcast(id, j);
       const float wj = G.bcast(wk, j);
       if (ch < P.F) {
         float c[V];
-        load_color<V>(P, feat, idj, ch, c);
+        load_color<V, FT>(P, feat, idj, ch, c);
 #pragma unroll
         for (int v = 0; v < V; ++v) C[v] = __fmaf_rn(wj, c[v], C[v]);
       }
     }
-    cnt += r.take;
-    T = G.bcast(r.Tn, r.take - 1);
-    if (r.stop) break;
+    cnt += ct.take;
+    T = G.bcast(ct.Tn, ct.take - 1);
+    if (ct.stop) break;
   }
   write_pixel<V>(P, pix, ch, C, image);
   if (G.lg == 0) {
@@ -506,144 +617,121 @@ __device__ void blend_fwd_group(const Group<GA>& G, const RP& P, const unsigned 
   }
 }
 
-// Shared-memory carve of the group path: per group CG keys, alphas, order.
-template <int GA>
-struct GroupBuf {
-  static constexpr int kGroups = kThreads / GA;
-  static constexpr int CG = kGroupKeys / kGroups;
-  unsigned long long* K;
-  float* A;
-  uint16_t* idx;
-  float* chunkT;  // CG / GA + 1 per group (backward)
-  __device__ GroupBuf(unsigned char* dyn, int group) {
-    unsigned long long* k0 = reinterpret_cast<unsigned long long*>(dyn);
-    float* a0 = reinterpret_cast<float*>(k0 + kGroupKeys);
-    uint16_t* i0 = reinterpret_cast<uint16_t*>(a0 + kGroupKeys);
-    float* t0 = reinterpret_cast<float*>(i0 + kGroupKeys);
-    K = k0 + group * CG;
-    A = a0 + group * CG;
-    idx = i0 + group * CG;
-    chunkT = t0 + group * (CG / GA + 1);
-  }
-  static size_t bytes() { return (size_t)kGroupKeys * (8 + 4 + 2) + (size_t)kGroups * (CG / GA + 1) * 4; }
-};
-
-template <int GA>
-__device__ __forceinline__ void load_bucket(const Group<GA>& G, const RasterWs& ws, uint32_t s0, int m,
-                                            const GroupBuf<GA>& B) {
-  for (int j = G.lg; j < m; j += GA) {
-    B.K[j] = ws.keys[s0 + j];
-    B.A[j] = ws.alpha[s0 + j];
-    B.idx[j] = (uint16_t)j;
-  }
-  G.sync();
-  bitonic_sort_idx(B.K, B.idx, m, G.lg, GA, [&] { G.sync(); });
-}
-
-template <int V, int GA>
-__global__ void __launch_bounds__(kThreads) k_blend_fwd(RP P, const float* __restrict__ feat, RasterWs ws,
-                                                         float* __restrict__ image, float* __restrict__ T_final,
+template <int V, int GA, class FT>
+__global__ void __launch_bounds__(kThreads, 3) k_blend_fwd(RP P, const FT* __restrict__ feat, RasterWs ws,
+                                                         FT* __restrict__ image, float* __restrict__ T_final,
                                                          int32_t* __restrict__ n_contrib) {
-  extern __shared__ __align__(16) unsigned char dyn[];
+  constexpr int kGroups = kThreads / GA;
   const Group<GA> G;
   const int group = threadIdx.x / GA;
-  const GroupBuf<GA> B(dyn, group);
   const int t = blockIdx.x;
   const int tx = t % P.tiles_x, ty = t / P.tiles_x;
-  for (int p = group; p < P.TW * P.TH; p += GroupBuf<GA>::kGroups) {
+  for (int p = group; p < P.TW * P.TH; p += kGroups) {
     const int px = tx * P.TW + p % P.TW, py = ty * P.TH + p / P.TW;
     if (px >= P.cam.W || py >= P.cam.H) continue;
     const long long q = (long long)py * P.cam.W + px;
     const uint32_t s0 = ws.pix_start[q];
     const int m = (int)(ws.pix_start[q + 1] - s0);
-    if (m > GroupBuf<GA>::CG) continue;  // CTA path
-    load_bucket<GA>(G, ws, s0, m, B);
-    blend_fwd_group<V, GA>(G, P, B.K, B.A, B.idx, m, q, feat, image, T_final, n_contrib);
-    G.sync();
+    const int regs = (m + GA - 1) / GA;
+    if (regs <= 1) blend_fwd_reg<V, GA, FT, 1>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
+    else if (regs <= 2) blend_fwd_reg<V, GA, FT, 2>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
+    else if (regs <= 4) blend_fwd_reg<V, GA, FT, 4>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
+    else if (regs <= kRegMax) blend_fwd_reg<V, GA, FT, kRegMax>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
+    // larger buckets: CTA path
   }
 }
 
 // ------------------------------------------------------ group path (bwd) ---
-// One pixel: recompute T_k with the forward's chunked scan (pass 1 keeps the
-// transmittance in front of every chunk), then walk the blended chunks back
-// to front accumulating S_k = sum_{j>k} T_j alpha_j (c_j . g) and write
+// Pass 1 recomputes the forward's chunk scans (front to back) and keeps the
+// transmittance in front of each chunk; pass 2 walks the blended chunks back
+// to front accumulating S_k = sum_{j>k} T_j alpha_j (c_j . g) and writes
 // fscal[slot_k] = (T_k alpha_k, dL/dalpha_k = T_k (c_k . g) - S_k / (1 - alpha_k)).
-template <int V, int GA>
-__device__ void blend_bwd_group(const Group<GA>& G, const RP& P, const GroupBuf<GA>& B, uint32_t s0, int m, int nb,
-                                long long pix, const float* __restrict__ feat, const float* __restrict__ d_image,
-                                float2* __restrict__ fscal) {
-  const int ch = G.lg * V;
-  for (int k = nb + G.lg; k < m; k += GA) fscal[s0 + B.idx[k]] = make_float2(0.f, 0.f);
-  if (nb == 0) return;
-  float T = 1.0f;
-  const int n_chunks = (nb + GA - 1) / GA;
-  for (int c = 0; c < n_chunks; ++c) {
-    if (G.lg == 0) B.chunkT[c] = T;
-    const int k = c * GA + G.lg;
-    const bool valid = k < nb;
-    const float a = valid ? B.A[B.idx[k]] : 0.f;
-    const ChunkT<GA> r = chunk_transmittance<GA>(G, P, a, valid, min(GA, nb - c * GA), T);
-    T = G.bcast(r.Tn, r.take - 1);
+template <int V, int GA, class FT, int R>
+__device__ void blend_bwd_reg(const Group<GA>& G, const RP& P, const RasterWs& ws, uint32_t s0, int m, int nb,
+                              long long pix, const FT* __restrict__ feat, const float* __restrict__ d_image) {
+  unsigned long long key[R];
+  load_sorted<GA, R>(G, ws.keys, s0, m, key);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int k = r * GA + G.lg;
+    if (k >= nb && k < m) ws.fscal[s0 + reg_pos(key[r])] = make_float2(0.f, 0.f);
   }
-  G.sync();
+  if (nb == 0) return;
+  const int ch = G.lg * V;
+  float a[R], Tc[R];
+  float T = 1.0f;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    a[r] = 0.f;
+    Tc[r] = T;
+    const int b = r * GA;
+    if (b < nb) {
+      const bool valid = b + G.lg < nb;
+      a[r] = valid ? ws.alpha[s0 + reg_pos(key[r])] : 0.f;
+      const ChunkT<GA> ct = chunk_transmittance<GA>(G, P, a[r], valid, min(GA, nb - b), T);
+      T = G.bcast(ct.Tn, ct.take - 1);
+    }
+  }
   float g[V];
   if (ch < P.F) load_vec<V>(d_image + pix * P.F + ch, g);
   else
 #pragma unroll
     for (int v = 0; v < V; ++v) g[v] = 0.f;
   float S = 0.f;
-  for (int c = n_chunks - 1; c >= 0; --c) {
-    const int k = c * GA + G.lg;
-    const bool valid = k < nb;
-    const int q = valid ? B.idx[k] : 0;
-    const float a = valid ? B.A[q] : 0.f;
-    const long long id = valid ? (long long)(B.K[q] & kIdMask) : 0;
-    const ChunkT<GA> r = chunk_transmittance<GA>(G, P, a, valid, min(GA, nb - c * GA), B.chunkT[c]);
+#pragma unroll
+  for (int r = R - 1; r >= 0; --r) {
+    const int b = r * GA;
+    if (b >= nb) continue;
+    const bool valid = b + G.lg < nb;
+    const long long id = valid ? reg_id(key[r]) : 0;
+    const ChunkT<GA> ct = chunk_transmittance<GA>(G, P, a[r], valid, min(GA, nb - b), Tc[r]);
     float mydot = 0.f;
-#pragma unroll 8
-    for (int j = 0; j < r.take; ++j) {
+#pragma unroll 2
+    for (int j = 0; j < ct.take; ++j) {
       const long long idj = G.bcast(id, j);
       float part = 0.f;
       if (ch < P.F) {
         float cc[V];
-        load_color<V>(P, feat, idj, ch, cc);
+        load_color<V, FT>(P, feat, idj, ch, cc);
 #pragma unroll
         for (int v = 0; v < V; ++v) part = __fmaf_rn(cc[v], g[v], part);
       }
       const float dj = G.sum(part);
       if (G.lg == j) mydot = dj;
     }
-    const bool mine = G.lg < r.take;
-    const float wk = mine ? __fmul_rn(r.Tk, a) : 0.f;
+    const bool mine = G.lg < ct.take;
+    const float wk = mine ? __fmul_rn(ct.Tk, a[r]) : 0.f;
     const float term = __fmul_rn(wk, mydot);
-    const float suf = G.suffix_scan(term);               // this chunk, at or behind k
-    const float Sk = __fadd_rn(S, G.shift_down(suf));    // strictly behind k
-    const float da = __fsub_rn(__fmul_rn(r.Tk, mydot), __fdiv_rn(Sk, __fsub_rn(1.0f, a)));
-    if (mine) fscal[s0 + q] = make_float2(wk, da);
+    const float suf = G.suffix_scan(term);             // this chunk, at or behind k
+    const float Sk = __fadd_rn(S, G.shift_down(suf));  // strictly behind k
+    const float da = __fsub_rn(__fmul_rn(ct.Tk, mydot), __fdiv_rn(Sk, __fsub_rn(1.0f, a[r])));
+    if (mine) ws.fscal[s0 + reg_pos(key[r])] = make_float2(wk, da);
     S = __fadd_rn(S, G.bcast(suf, 0));
   }
 }
 
-template <int V, int GA>
-__global__ void __launch_bounds__(kThreads) k_blend_bwd(RP P, const float* __restrict__ feat,
+template <int V, int GA, class FT>
+__global__ void __launch_bounds__(kThreads, 3) k_blend_bwd(RP P, const FT* __restrict__ feat,
                                                          const int32_t* __restrict__ n_contrib,
                                                          const float* __restrict__ d_image, RasterWs ws) {
-  extern __shared__ __align__(16) unsigned char dyn[];
+  constexpr int kGroups = kThreads / GA;
   const Group<GA> G;
   const int group = threadIdx.x / GA;
-  const GroupBuf<GA> B(dyn, group);
   const int t = blockIdx.x;
   const int tx = t % P.tiles_x, ty = t / P.tiles_x;
-  for (int p = group; p < P.TW * P.TH; p += GroupBuf<GA>::kGroups) {
+  for (int p = group; p < P.TW * P.TH; p += kGroups) {
     const int px = tx * P.TW + p % P.TW, py = ty * P.TH + p / P.TW;
     if (px >= P.cam.W || py >= P.cam.H) continue;
     const long long q = (long long)py * P.cam.W + px;
     const uint32_t s0 = ws.pix_start[q];
     const int m = (int)(ws.pix_start[q + 1] - s0);
-    if (m > GroupBuf<GA>::CG || m == 0) continue;
-    load_bucket<GA>(G, ws, s0, m, B);
-    blend_bwd_group<V, GA>(G, P, B, s0, m, min(m, (int)n_contrib[q]), q, feat, d_image, ws.fscal);
-    G.sync();
+    if (m == 0) continue;
+    const int nb = min(m, (int)n_contrib[q]);
+    const int regs = (m + GA - 1) / GA;
+    if (regs <= 1) blend_bwd_reg<V, GA, FT, 1>(G, P, ws, s0, m, nb, q, feat, d_image);
+    else if (regs <= 2) blend_bwd_reg<V, GA, FT, 2>(G, P, ws, s0, m, nb, q, feat, d_image);
+    else if (regs <= 4) blend_bwd_reg<V, GA, FT, 4>(G, P, ws, s0, m, nb, q, feat, d_image);
+    else if (regs <= kRegMax) blend_bwd_reg<V, GA, FT, kRegMax>(G, P, ws, s0, m, nb, q, feat, d_image);
   }
 }
 
@@ -725,9 +813,9 @@ __device__ int cta_transmittance(const RP& P, AlphaAt alpha_at, int m, TStore t_
   return n;
 }
 
-template <int V, int GA, class KeyAt, class AlphaAt, class TLoad>
+template <int V, int GA, class FT, class KeyAt, class AlphaAt, class TLoad>
 __device__ void blend_fwd_cta(const RP& P, KeyAt key_at, AlphaAt alpha_at, TLoad t_load, int n, float T, long long pix,
-                              const float* __restrict__ feat, float* __restrict__ image, float* __restrict__ T_final,
+                              const FT* __restrict__ feat, FT* __restrict__ image, float* __restrict__ T_final,
                               int32_t* __restrict__ n_contrib, HeavySmem& H) {
   constexpr int kGroups = kThreads / GA;
   const Group<GA> G;
@@ -740,7 +828,7 @@ __device__ void blend_fwd_cta(const RP& P, KeyAt key_at, AlphaAt alpha_at, TLoad
     for (int k = group; k < n; k += kGroups) {
       const float w = __fmul_rn(t_load(k), alpha_at(k));
       float c[V];
-      load_color<V>(P, feat, (long long)(key_at(k) & kIdMask), ch, c);
+      load_color<V, FT>(P, feat, (long long)(key_at(k) & kIdMask), ch, c);
 #pragma unroll
       for (int v = 0; v < V; ++v) C[v] = __fmaf_rn(w, c[v], C[v]);
     }
@@ -766,9 +854,9 @@ __device__ void blend_fwd_cta(const RP& P, KeyAt key_at, AlphaAt alpha_at, TLoad
 
 // Backward on the CTA path: T_k via the forward's scan, c_k . g split over
 // the groups, suffix sums by a CTA-wide reverse scan.
-template <int V, int GA, class KeyAt, class AlphaAt, class SlotAt, class TLoad, class DStore, class DLoad>
+template <int V, int GA, class FT, class KeyAt, class AlphaAt, class SlotAt, class TLoad, class DStore, class DLoad>
 __device__ void blend_bwd_cta(const RP& P, KeyAt key_at, AlphaAt alpha_at, SlotAt slot_at, TLoad t_load,
-                              DStore d_store, DLoad d_load, int nb, long long pix, const float* __restrict__ feat,
+                              DStore d_store, DLoad d_load, int nb, long long pix, const FT* __restrict__ feat,
                               const float* __restrict__ d_image, float2* __restrict__ fscal, HeavySmem& H) {
   constexpr int kGroups = kThreads / GA;
   const Group<GA> G;
@@ -783,7 +871,7 @@ __device__ void blend_bwd_cta(const RP& P, KeyAt key_at, AlphaAt alpha_at, SlotA
     float part = 0.f;
     if (ch < P.F) {
       float c[V];
-      load_color<V>(P, feat, (long long)(key_at(k) & kIdMask), ch, c);
+      load_color<V, FT>(P, feat, (long long)(key_at(k) & kIdMask), ch, c);
 #pragma unroll
       for (int v = 0; v < V; ++v) part = __fmaf_rn(c[v], g[v], part);
     }
@@ -844,9 +932,9 @@ __device__ void cta_order_bucket(const RasterWs& ws, uint32_t s0, int m, const H
   }
 }
 
-template <int V, int GA>
-__global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const float* __restrict__ feat, RasterWs ws,
-                                                               float* __restrict__ image, float* __restrict__ T_final,
+template <int V, int GA, class FT>
+__global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const FT* __restrict__ feat, RasterWs ws,
+                                                               FT* __restrict__ image, float* __restrict__ T_final,
                                                                int32_t* __restrict__ n_contrib) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ SortSmem S;
@@ -864,7 +952,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const float*
       auto alpha_at = [&](int k) { return B.A[B.idx[k]]; };
       const int n = cta_transmittance(P, alpha_at, m, [&](int k, float v) { B.Tk[k] = v; }, H, &T);
       __syncthreads();
-      blend_fwd_cta<V, GA>(P, key_at, alpha_at, [&](int k) { return B.Tk[k]; }, n, T, q, feat, image, T_final,
+      blend_fwd_cta<V, GA, FT>(P, key_at, alpha_at, [&](int k) { return B.Tk[k]; }, n, T, q, feat, image, T_final,
                            n_contrib, H);
     } else {
       const unsigned long long* ka = ws.ka + s0;
@@ -874,15 +962,15 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const float*
       auto alpha_at = [&](int k) { return ws.alpha[s0 + va[k]]; };
       const int n = cta_transmittance(P, alpha_at, m, [&](int k, float v) { tmp[k].x = v; }, H, &T);
       __syncthreads();
-      blend_fwd_cta<V, GA>(P, key_at, alpha_at, [&](int k) { return tmp[k].x; }, n, T, q, feat, image, T_final,
+      blend_fwd_cta<V, GA, FT>(P, key_at, alpha_at, [&](int k) { return tmp[k].x; }, n, T, q, feat, image, T_final,
                            n_contrib, H);
     }
     __syncthreads();
   }
 }
 
-template <int V, int GA>
-__global__ void __launch_bounds__(kThreads) k_blend_bwd_heavy(RP P, const float* __restrict__ feat,
+template <int V, int GA, class FT>
+__global__ void __launch_bounds__(kThreads) k_blend_bwd_heavy(RP P, const FT* __restrict__ feat,
                                                                const int32_t* __restrict__ n_contrib,
                                                                const float* __restrict__ d_image, RasterWs ws) {
   extern __shared__ __align__(16) unsigned char dyn[];
@@ -904,7 +992,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd_heavy(RP P, const float*
       for (int k = nb + (int)threadIdx.x; k < m; k += kThreads) ws.fscal[slot_at(k)] = make_float2(0.f, 0.f);
       cta_transmittance(P, alpha_at, nb, [&](int k, float v) { B.Tk[k] = v; }, H, &T);
       __syncthreads();
-      blend_bwd_cta<V, GA>(P, key_at, alpha_at, slot_at, [&](int k) { return B.Tk[k]; },
+      blend_bwd_cta<V, GA, FT>(P, key_at, alpha_at, slot_at, [&](int k) { return B.Tk[k]; },
                            [&](int k, float v) { B.D[k] = v; }, [&](int k) { return B.D[k]; }, nb, q, feat, d_image,
                            ws.fscal, H);
     } else {
@@ -917,7 +1005,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd_heavy(RP P, const float*
       for (int k = nb + (int)threadIdx.x; k < m; k += kThreads) ws.fscal[slot_at(k)] = make_float2(0.f, 0.f);
       cta_transmittance(P, alpha_at, nb, [&](int k, float v) { tmp[k].x = v; }, H, &T);
       __syncthreads();
-      blend_bwd_cta<V, GA>(P, key_at, alpha_at, slot_at, [&](int k) { return tmp[k].x; },
+      blend_bwd_cta<V, GA, FT>(P, key_at, alpha_at, slot_at, [&](int k) { return tmp[k].x; },
                            [&](int k, float v) { tmp[k].y = v; }, [&](int k) { return tmp[k].y; }, nb, q, feat,
                            d_image, ws.fscal, H);
     }
@@ -929,10 +1017,10 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd_heavy(RP P, const float*
 // Per point: gather the scalars of its (at most four) splats and the
 // upstream-gradient rows of their pixels.  d_feat row = sum_k (T_k alpha_k) g_k;
 // d alpha_h = sum_k w_k [unclamped] dL/dalpha_k.
-template <int V, int GA>
+template <int V, int GA, class FT>
 __global__ void __launch_bounds__(kThreads) k_point_grad(RP P, const float* __restrict__ pos,
                                                           const float* __restrict__ opacity,
-                                                          const float* __restrict__ feat,
+                                                          const FT* __restrict__ feat,
                                                           const float* __restrict__ d_image, RasterWs ws,
                                                           float* __restrict__ d_opacity, float* __restrict__ d_feat) {
   constexpr int kGroups = kThreads / GA;
@@ -974,6 +1062,7 @@ __global__ void __launch_bounds__(kThreads) k_point_grad(RP P, const float* __re
     if (active) {
       float* o = d_feat + id * P.F + ch;
       if (V == 4) *reinterpret_cast<float4*>(o) = make_float4(dc[0], dc[1], dc[2], dc[3]);
+      else if (V == 2) *reinterpret_cast<float2*>(o) = make_float2(dc[0], dc[1]);
       else
 #pragma unroll
         for (int v = 0; v < V; ++v) o[v] = dc[v];
@@ -992,8 +1081,8 @@ inpc_status make_rp(const inpc_camera* cam, const inpc_raster_opts* o, int64_t n
   if (n < 0 || n > (int64_t(1) << kIdBits)) return fail(INPC_ERR_CAPACITY, "n must be in [0, 2^25]");
   if (o->opacity_mode != INPC_OPACITY_GIVEN && o->opacity_mode != INPC_OPACITY_FROM_CH0)
     return fail(INPC_ERR_INVALID_ARG, "bad opacity_mode");
-  if (o->feat_dtype != INPC_F32 || o->image_dtype != INPC_F32)
-    return fail(INPC_ERR_UNSUPPORTED, "only INPC_F32 features and images are implemented");
+  if ((o->feat_dtype != INPC_F32 && o->feat_dtype != INPC_BF16) || o->image_dtype != o->feat_dtype)
+    return fail(INPC_ERR_UNSUPPORTED, "feat_dtype must be INPC_F32 or INPC_BF16 and image_dtype must equal it");
   if (o->n_channels < 1 || o->n_channels > 128) return fail(INPC_ERR_UNSUPPORTED, "n_channels must be in [1, 128]");
   if (o->n_channels % 4 != 0 && o->n_channels > 32)
     return fail(INPC_ERR_UNSUPPORTED, "n_channels > 32 must be a multiple of 4");
@@ -1008,6 +1097,7 @@ inpc_status make_rp(const inpc_camera* cam, const inpc_raster_opts* o, int64_t n
   P.n_tiles = P.tiles_x * P.tiles_y;
   P.F = o->n_channels;
   P.head = o->opacity_mode == INPC_OPACITY_FROM_CH0;
+  P.bf16 = o->feat_dtype == INPC_BF16;
   P.t_min = o->t_min;
   P.alpha_max = o->alpha_max;
   P.n = n;
@@ -1021,28 +1111,30 @@ int next_pow2(int x) {
   return p;
 }
 
-// (V, GA): V channels per lane, GA lanes per pixel.
+// (V, GA): V channels per lane, GA lanes per pixel.  Channel counts that are
+// multiples of 32 use full warps; other multiples of 4 use V = 4 and the next
+// power of two of F / 4 lanes; anything else (F <= 32) uses one channel per
+// lane of a full warp.
 template <class Fn>
 inpc_status dispatch(int F, Fn&& fn) {
+  using I = std::integral_constant<int, 1>;
+  using II = std::integral_constant<int, 2>;
+  using IV = std::integral_constant<int, 4>;
+  using W = std::integral_constant<int, 32>;
+  if (F == 32) return fn(I(), W());
+  if (F == 64) return fn(II(), W());
+  if (F == 128) return fn(IV(), W());
   if (F % 4 == 0) {
     switch (next_pow2(F / 4)) {
-      case 1: return fn(std::integral_constant<int, 4>(), std::integral_constant<int, 1>());
-      case 2: return fn(std::integral_constant<int, 4>(), std::integral_constant<int, 2>());
-      case 4: return fn(std::integral_constant<int, 4>(), std::integral_constant<int, 4>());
-      case 8: return fn(std::integral_constant<int, 4>(), std::integral_constant<int, 8>());
-      case 16: return fn(std::integral_constant<int, 4>(), std::integral_constant<int, 16>());
-      case 32: return fn(std::integral_constant<int, 4>(), std::integral_constant<int, 32>());
-    }
-  } else {
-    switch (next_pow2(F)) {
-      case 1: return fn(std::integral_constant<int, 1>(), std::integral_constant<int, 1>());
-      case 2: return fn(std::integral_constant<int, 1>(), std::integral_constant<int, 2>());
-      case 4: return fn(std::integral_constant<int, 1>(), std::integral_constant<int, 4>());
-      case 8: return fn(std::integral_constant<int, 1>(), std::integral_constant<int, 8>());
-      case 16: return fn(std::integral_constant<int, 1>(), std::integral_constant<int, 16>());
-      case 32: return fn(std::integral_constant<int, 1>(), std::integral_constant<int, 32>());
+      case 1: return fn(IV(), std::integral_constant<int, 1>());
+      case 2: return fn(IV(), std::integral_constant<int, 2>());
+      case 4: return fn(IV(), std::integral_constant<int, 4>());
+      case 8: return fn(IV(), std::integral_constant<int, 8>());
+      case 16: return fn(IV(), std::integral_constant<int, 16>());
+      case 32: return fn(IV(), W());
     }
   }
+  if (F <= 32) return fn(I(), W());
   return fail(INPC_ERR_UNSUPPORTED, "no kernel for n_channels = %d", F);
 }
 
@@ -1059,7 +1151,8 @@ void set_smem(K kernel, size_t bytes, std::once_flag& once) {
 // Forward binning: per-pixel counts, offsets, buckets (keys and alphas),
 // per-point slots and the list of pixels for the CTA path (all kept in the
 // workspace for the backward).
-inpc_status bin_fragments(const RP& P, const float* pos, const float* opacity, const float* feat, const RasterWs& ws,
+template <class FT>
+inpc_status bin_fragments(const RP& P, const float* pos, const float* opacity, const FT* feat, const RasterWs& ws,
                           uint32_t cap_group, cudaStream_t s) {
   INPC_CUDA(cudaMemsetAsync(ws.pix_count, 0, sizeof(uint32_t) * P.n_pix, s), "clear pixel counts");
   if (P.n > 0) {
@@ -1072,43 +1165,39 @@ inpc_status bin_fragments(const RP& P, const float* pos, const float* opacity, c
                                                                  ws.heavy_count, ws.pix_start);
   INPC_TRY(check_launch("k_heavy_list"));
   if (P.n > 0) {
-    k_pix_scatter<<<point_grid(P.n), 256, 0, s>>>(P, pos, opacity, feat, ws.pix_start, ws.pix_count, ws.keys, ws.alpha,
+    k_pix_scatter<FT><<<point_grid(P.n), 256, 0, s>>>(P, pos, opacity, feat, ws.pix_start, ws.pix_count, ws.keys, ws.alpha,
                                                   ws.pslot);
     INPC_TRY(check_launch("k_pix_scatter"));
   }
   return INPC_OK;
 }
 
-template <int V, int GA>
-inpc_status launch_fwd(const RP& P, const float* pos, const float* opacity, const float* feat, const RasterWs& ws,
-                       float* image, float* T_final, int32_t* n_contrib, cudaStream_t s) {
-  INPC_TRY(bin_fragments(P, pos, opacity, feat, ws, GroupBuf<GA>::CG, s));
-  static std::once_flag f1, f2;
-  const size_t gs = GroupBuf<GA>::bytes();
-  set_smem(k_blend_fwd<V, GA>, gs, f1);
-  set_smem(k_blend_fwd_heavy<V, GA>, HeavyBuf::bytes(), f2);
-  k_blend_fwd<V, GA><<<P.n_tiles, kThreads, gs, s>>>(P, feat, ws, image, T_final, n_contrib);
+template <int V, int GA, class FT>
+inpc_status launch_fwd(const RP& P, const float* pos, const float* opacity, const FT* feat, const RasterWs& ws,
+                       FT* image, float* T_final, int32_t* n_contrib, cudaStream_t s) {
+  INPC_TRY(bin_fragments(P, pos, opacity, feat, ws, GA * kRegMax, s));
+  static std::once_flag f2;
+  set_smem(k_blend_fwd_heavy<V, GA, FT>, HeavyBuf::bytes(), f2);
+  k_blend_fwd<V, GA, FT><<<P.n_tiles, kThreads, 0, s>>>(P, feat, ws, image, T_final, n_contrib);
   INPC_TRY(check_launch("k_blend_fwd"));
-  k_blend_fwd_heavy<V, GA><<<device_sm_count(), kThreads, HeavyBuf::bytes(), s>>>(P, feat, ws, image, T_final,
+  k_blend_fwd_heavy<V, GA, FT><<<device_sm_count() * 4, kThreads, HeavyBuf::bytes(), s>>>(P, feat, ws, image, T_final,
                                                                                    n_contrib);
   return check_launch("k_blend_fwd_heavy");
 }
 
-template <int V, int GA>
-inpc_status launch_bwd(const RP& P, const float* pos, const float* opacity, const float* feat,
+template <int V, int GA, class FT>
+inpc_status launch_bwd(const RP& P, const float* pos, const float* opacity, const FT* feat,
                        const int32_t* n_contrib, const float* d_image, const RasterWs& ws, float* d_opacity,
                        float* d_feat, cudaStream_t s) {
-  static std::once_flag f1, f2;
-  const size_t gs = GroupBuf<GA>::bytes();
-  set_smem(k_blend_bwd<V, GA>, gs, f1);
-  set_smem(k_blend_bwd_heavy<V, GA>, HeavyBuf::bytes(), f2);
-  k_blend_bwd<V, GA><<<P.n_tiles, kThreads, gs, s>>>(P, feat, n_contrib, d_image, ws);
+  static std::once_flag f2;
+  set_smem(k_blend_bwd_heavy<V, GA, FT>, HeavyBuf::bytes(), f2);
+  k_blend_bwd<V, GA, FT><<<P.n_tiles, kThreads, 0, s>>>(P, feat, n_contrib, d_image, ws);
   INPC_TRY(check_launch("k_blend_bwd"));
-  k_blend_bwd_heavy<V, GA><<<device_sm_count(), kThreads, HeavyBuf::bytes(), s>>>(P, feat, n_contrib, d_image, ws);
+  k_blend_bwd_heavy<V, GA, FT><<<device_sm_count() * 4, kThreads, HeavyBuf::bytes(), s>>>(P, feat, n_contrib, d_image, ws);
   INPC_TRY(check_launch("k_blend_bwd_heavy"));
   constexpr int kGroups = kThreads / GA;
   const long long grid = std::min<long long>(ceil_div(P.n, kGroups), (long long)device_sm_count() * 32);
-  k_point_grad<V, GA><<<(unsigned)std::max<long long>(grid, 1), kThreads, 0, s>>>(P, pos, opacity, feat, d_image, ws,
+  k_point_grad<V, GA, FT><<<(unsigned)std::max<long long>(grid, 1), kThreads, 0, s>>>(P, pos, opacity, feat, d_image, ws,
                                                                                   d_opacity, d_feat);
   return check_launch("k_point_grad");
 }
@@ -1116,64 +1205,3 @@ inpc_status launch_bwd(const RP& P, const float* pos, const float* opacity, cons
 }  // namespace
 }  // namespace inpc
 
-using namespace inpc;
-
-extern "C" inpc_status inpc_rasterize_workspace_size(const inpc_camera* cam, const inpc_raster_opts* opts, int64_t n,
-                                                     size_t* bytes) {
-  if (!bytes) return fail(INPC_ERR_INVALID_ARG, "bytes is null");
-  RP P;
-  INPC_TRY(make_rp(cam, opts, n, P));
-  *bytes = carve(nullptr, P.n_pix, n).bytes;
-  return INPC_OK;
-}
-
-extern "C" inpc_status inpc_rasterize_fwd(const inpc_camera* cam, const inpc_raster_opts* opts, const float* pos,
-                                          const float* opacity, const void* feat, int64_t n, void* image,
-                                          float* T_final, int32_t* n_contrib, void* workspace,
-                                          size_t workspace_bytes, inpc_stream_t stream) {
-  RP P;
-  INPC_TRY(make_rp(cam, opts, n, P));
-  const RasterWs need = carve(nullptr, P.n_pix, n);
-  if (!workspace || workspace_bytes < need.bytes || !aligned(workspace, 256))
-    return fail(INPC_ERR_INVALID_ARG, "workspace null, unaligned or smaller than %zu bytes", need.bytes);
-  if (!image || !T_final || !n_contrib) return fail(INPC_ERR_INVALID_ARG, "null output");
-  if (n > 0 && (!pos || !feat)) return fail(INPC_ERR_INVALID_ARG, "null pos or feat");
-  if (n > 0 && !P.head && !opacity) return fail(INPC_ERR_INVALID_ARG, "opacity required in INPC_OPACITY_GIVEN mode");
-  const size_t va = P.F % 4 == 0 ? 16 : 4;
-  if (!aligned(feat, va) || !aligned(image, va) || !aligned(pos, 4))
-    return fail(INPC_ERR_INVALID_ARG, "feat/image must be %zu-byte aligned", va);
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  RasterWs ws = carve(workspace, P.n_pix, n);
-  INPC_CUDA(cudaMemsetAsync(workspace, 0, kHeaderBytes, s), "clear header");
-  const float* f32 = static_cast<const float*>(feat);
-  return dispatch(P.F, [&](auto Vc, auto Gc) {
-    return launch_fwd<decltype(Vc)::value, decltype(Gc)::value>(P, pos, opacity, f32, ws, static_cast<float*>(image),
-                                                                 T_final, n_contrib, s);
-  });
-}
-
-extern "C" inpc_status inpc_rasterize_bwd(const inpc_camera* cam, const inpc_raster_opts* opts, const float* pos,
-                                          const float* opacity, const void* feat, int64_t n, const float* T_final,
-                                          const int32_t* n_contrib, const float* d_image, float* d_opacity,
-                                          float* d_feat, void* workspace, size_t workspace_bytes,
-                                          inpc_stream_t stream) {
-  RP P;
-  INPC_TRY(make_rp(cam, opts, n, P));
-  const RasterWs need = carve(nullptr, P.n_pix, n);
-  if (!workspace || workspace_bytes < need.bytes || !aligned(workspace, 256))
-    return fail(INPC_ERR_INVALID_ARG, "workspace null, unaligned or smaller than %zu bytes", need.bytes);
-  if (n == 0) return INPC_OK;
-  if (!pos || !feat || !T_final || !n_contrib || !d_image || !d_feat)
-    return fail(INPC_ERR_INVALID_ARG, "null pointer");
-  if (!P.head && (!opacity || !d_opacity)) return fail(INPC_ERR_INVALID_ARG, "opacity and d_opacity required");
-  const size_t va = P.F % 4 == 0 ? 16 : 4;
-  if (!aligned(feat, va) || !aligned(d_image, va) || !aligned(d_feat, va))
-    return fail(INPC_ERR_INVALID_ARG, "feat/d_image/d_feat must be %zu-byte aligned", va);
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  RasterWs ws = carve(workspace, P.n_pix, n);
-  const float* f32 = static_cast<const float*>(feat);
-  return dispatch(P.F, [&](auto Vc, auto Gc) {
-    return launch_bwd<decltype(Vc)::value, decltype(Gc)::value>(P, pos, opacity, f32, n_contrib, d_image, ws,
-                                                                 P.head ? nullptr : d_opacity, d_feat, s);
-  });
-}
