@@ -185,6 +185,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--unfused", action="store_true",
+                    help="separate rasterizer backward and grid adjoint (materialises dh)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -226,7 +228,7 @@ def main():
     img = torch.empty(H, W, C, dtype=torch.float32, device=dev)
     T = torch.empty(H, W, dtype=torch.float32, device=dev)
     ncon = torch.empty(H, W, dtype=torch.int32, device=dev)
-    dh = torch.empty(N, C, dtype=torch.float32, device=dev)
+    dh = torch.empty(N, C, dtype=torch.float32, device=dev) if args.unfused else None
     gtab = torch.zeros(n_entries, 4, dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
@@ -242,13 +244,18 @@ def main():
         mark(2)
         api.rasterize_fwd(cam, opts, pos, h, None, ws=ws_r, out=(img, T, ncon))
         mark(3)
-        api.rasterize_bwd(cam, opts, pos, h, None, T, ncon, g_img, ws_r, out=(None, dh))
-        mark(4)
         gtab.zero_()
-        api.query_hashgrid_bwd(desc, pos, dh, gtab)
+        if args.unfused:
+            api.rasterize_bwd(cam, opts, pos, h, None, T, ncon, g_img, ws_r, out=(None, dh))
+            mark(4)
+            api.query_hashgrid_bwd(desc, pos, dh, gtab)
+        else:
+            mark(4)
+            api.rasterize_bwd_hashgrid(cam, opts, desc, pos, h, T, ncon, g_img, ws_r, gtab)
         mark(5)
 
-    stages = ["sample", "query_fwd", "raster_fwd", "raster_bwd", "query_bwd"]
+    stages = ["sample", "query_fwd", "raster_fwd", "table_zero", "raster_bwd+query_bwd"] if not args.unfused else \
+        ["sample", "query_fwd", "raster_fwd", "raster_bwd", "query_bwd"]
     for i in range(args.warmup):
         view(1000 + i + rank * 97)
     torch.cuda.synchronize()
@@ -283,6 +290,9 @@ def main():
     # every sample of this workload lies inside the view, so each splats to
     # exactly four on-image pixels: the fragment count is 4N
     bytes_model = algorithmic_bytes(N, N_LEAVES, n_entries, 4 * N, H * W)
+    if not args.unfused:
+        bytes_model["table_zero"] = 0
+        bytes_model["raster_bwd+query_bwd"] = bytes_model.pop("raster_bwd") + bytes_model.pop("query_bwd")
     peak, peak_kind = measured_peak_hbm()
     stage_mean = {s: statistics.mean(v) for s, v in per_stage.items()}
     dom = max(stage_mean, key=stage_mean.get)
@@ -344,9 +354,8 @@ def run_e2e(args, api, B, tree, grid, cam, g_np, res, desc, opts, dev, world, ra
         _, pos = api.sample_octree(c, l, w, tree.root_size, 0, view_id, N)
         hq = api.query_hashgrid(desc, table, pos)
         img, T, n, ws = api.rasterize_fwd(cam, opts, pos, hq)
-        _, dh = api.rasterize_bwd(cam, opts, pos, hq, None, T, n, g, ws)
         gt = torch.zeros_like(table)
-        api.query_hashgrid_bwd(desc, pos, dh, gt)
+        api.rasterize_bwd_hashgrid(cam, opts, desc, pos, hq, T, n, g, ws, gt)
         out_img.copy_(img, non_blocking=True)
         out_gt.copy_(gt, non_blocking=True)
 

@@ -250,6 +250,23 @@ inpc_status inpc_rasterize_bwd(const inpc_camera* cam, const inpc_raster_opts* o
                                const int32_t* n_contrib, const float* d_image, float* d_opacity, float* d_feat,
                                void* workspace, size_t workspace_bytes, inpc_stream_t stream);
 
+/* Rasterizer backward fused with the grid query's adjoint, for head mode
+ * (INPC_OPACITY_FROM_CH0) when the features are the grid query's output
+ * (n_channels = n_levels * n_feats): the same result as inpc_rasterize_bwd
+ * followed by inpc_query_hashgrid_bwd on its d_feat, but each point's
+ * gradient row goes from registers straight into the table gradient, so it
+ * is never written to and read back from memory (App. A.6 backward, then the
+ * adjoint of the Sec. 3.3 query).
+ *   grid        descriptor of the query that produced `feat`
+ *   grad_table  float32 [n_entries, n_feats], accumulated (+=)
+ *   d_feat      optional float32 [n, F]: also written when non-NULL
+ * Other arguments as for inpc_rasterize_bwd. */
+inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const inpc_raster_opts* opts,
+                                        const inpc_hashgrid_desc* grid, const float* pos, const void* feat, int64_t n,
+                                        const float* T_final, const int32_t* n_contrib, const float* d_image,
+                                        float* grad_table, float* d_feat, void* workspace, size_t workspace_bytes,
+                                        inpc_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

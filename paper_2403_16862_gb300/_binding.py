@@ -35,7 +35,7 @@ DECLARED = [
     "inpc_last_error", "inpc_version", "inpc_kernel_launches", "inpc_read_device_status",
     "inpc_sample_workspace_size", "inpc_sample_octree", "inpc_sample_octree_noalloc",
     "inpc_hashgrid_n_entries", "inpc_query_hashgrid", "inpc_query_hashgrid_bwd",
-    "inpc_rasterize_workspace_size", "inpc_rasterize_fwd", "inpc_rasterize_bwd",
+    "inpc_rasterize_workspace_size", "inpc_rasterize_fwd", "inpc_rasterize_bwd", "inpc_rasterize_bwd_hashgrid",
 ]
 
 
@@ -100,6 +100,9 @@ def load(path: str = LIB_PATH):
                                          _P, _P, _P, _P, C.c_size_t, _P]
         L.inpc_rasterize_bwd.argtypes = [C.POINTER(InpcCamera), C.POINTER(InpcRasterOpts), _P, _P, _P, C.c_int64,
                                          _P, _P, _P, _P, _P, _P, C.c_size_t, _P]
+        L.inpc_rasterize_bwd_hashgrid.argtypes = [C.POINTER(InpcCamera), C.POINTER(InpcRasterOpts),
+                                                  C.POINTER(InpcHashgridDesc), _P, _P, C.c_int64, _P, _P, _P, _P, _P,
+                                                  _P, C.c_size_t, _P]
         for name in DECLARED:
             if name not in ("inpc_last_error", "inpc_version", "inpc_kernel_launches"):
                 getattr(L, name).restype = C.c_int
@@ -180,3 +183,11 @@ def inpc_rasterize_bwd(cam: InpcCamera, opts: InpcRasterOpts, pos: int, opacity,
                        stream: int):
     check(load().inpc_rasterize_bwd(C.byref(cam), C.byref(opts), pos, opacity, feat, n, T_final, n_contrib, d_image,
                                     d_opacity, d_feat, workspace, workspace_bytes, stream))
+
+
+def inpc_rasterize_bwd_hashgrid(cam: InpcCamera, opts: InpcRasterOpts, desc: InpcHashgridDesc, pos: int, feat: int,
+                                n: int, T_final: int, n_contrib: int, d_image: int, grad_table: int, d_feat,
+                                workspace: int, workspace_bytes: int, stream: int):
+    check(load().inpc_rasterize_bwd_hashgrid(C.byref(cam), C.byref(opts), C.byref(desc), pos, feat, n, T_final,
+                                             n_contrib, d_image, grad_table, d_feat, workspace, workspace_bytes,
+                                             stream))

@@ -196,6 +196,19 @@ def rasterize_bwd(cam, opts: RasterOptions, pos, feat, opacity, T_final, n_contr
     return d_opacity, d_feat
 
 
+def rasterize_bwd_hashgrid(cam, opts: RasterOptions, desc, pos, feat, T_final, n_contrib, d_image, ws, grad_table,
+                           d_feat=None):
+    """Head-mode rasterizer backward fused with the grid query's adjoint:
+    accumulates the table gradient (FP32) directly; d_feat is written only
+    when given."""
+    _need(d_image, torch.float32, "d_image")
+    _need(grad_table, torch.float32, "grad_table")
+    B.inpc_rasterize_bwd_hashgrid(camera(cam), opts.c(), desc, pos.data_ptr(), feat.data_ptr(), pos.shape[0],
+                                  T_final.data_ptr(), n_contrib.data_ptr(), d_image.data_ptr(), grad_table.data_ptr(),
+                                  _ptr(d_feat), ws.data_ptr(), ws.numel(), _stream())
+    return grad_table
+
+
 # ---------------------------------------------------------------- autograd ---
 class HashGridQuery(torch.autograd.Function):
     """h = query(table, pos); gradient flows to the table (FP32)."""

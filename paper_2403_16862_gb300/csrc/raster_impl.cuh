@@ -1186,19 +1186,26 @@ inpc_status launch_fwd(const RP& P, const float* pos, const float* opacity, cons
 }
 
 template <int V, int GA, class FT>
-inpc_status launch_bwd(const RP& P, const float* pos, const float* opacity, const FT* feat,
-                       const int32_t* n_contrib, const float* d_image, const RasterWs& ws, float* d_opacity,
-                       float* d_feat, cudaStream_t s) {
+inpc_status launch_blend_bwd(const RP& P, const FT* feat, const int32_t* n_contrib, const float* d_image,
+                             const RasterWs& ws, cudaStream_t s) {
   static std::once_flag f2;
   set_smem(k_blend_bwd_heavy<V, GA, FT>, HeavyBuf::bytes(), f2);
   k_blend_bwd<V, GA, FT><<<P.n_tiles, kThreads, 0, s>>>(P, feat, n_contrib, d_image, ws);
   INPC_TRY(check_launch("k_blend_bwd"));
-  k_blend_bwd_heavy<V, GA, FT><<<device_sm_count() * 4, kThreads, HeavyBuf::bytes(), s>>>(P, feat, n_contrib, d_image, ws);
-  INPC_TRY(check_launch("k_blend_bwd_heavy"));
+  k_blend_bwd_heavy<V, GA, FT><<<device_sm_count() * 4, kThreads, HeavyBuf::bytes(), s>>>(P, feat, n_contrib, d_image,
+                                                                                           ws);
+  return check_launch("k_blend_bwd_heavy");
+}
+
+template <int V, int GA, class FT>
+inpc_status launch_bwd(const RP& P, const float* pos, const float* opacity, const FT* feat,
+                       const int32_t* n_contrib, const float* d_image, const RasterWs& ws, float* d_opacity,
+                       float* d_feat, cudaStream_t s) {
+  INPC_TRY((launch_blend_bwd<V, GA, FT>(P, feat, n_contrib, d_image, ws, s)));
   constexpr int kGroups = kThreads / GA;
   const long long grid = std::min<long long>(ceil_div(P.n, kGroups), (long long)device_sm_count() * 32);
-  k_point_grad<V, GA, FT><<<(unsigned)std::max<long long>(grid, 1), kThreads, 0, s>>>(P, pos, opacity, feat, d_image, ws,
-                                                                                  d_opacity, d_feat);
+  k_point_grad<V, GA, FT><<<(unsigned)std::max<long long>(grid, 1), kThreads, 0, s>>>(P, pos, opacity, feat, d_image,
+                                                                                      ws, d_opacity, d_feat);
   return check_launch("k_point_grad");
 }
 

@@ -36,6 +36,11 @@ def _pipeline(gpu, oracle, n_leaves, n_samples, log2_T, cam, seed=0, graph_check
     _, dh = api.rasterize_bwd(cam, opts, pos, h, None, T, n, torch.from_numpy(g_img).to(gpu), ws)
     gt = torch.zeros_like(table)
     api.query_hashgrid_bwd(desc, pos, dh, gt)
+    # the fused backward (rasterizer backward + query adjoint in one pass)
+    gt_fused = torch.zeros_like(table)
+    dh_fused = torch.empty_like(dh)
+    api.rasterize_bwd_hashgrid(cam, opts, desc, pos, h, T, n, torch.from_numpy(g_img).to(gpu), ws, gt_fused,
+                               d_feat=dh_fused)
     torch.cuda.synchronize()
 
     # ---- oracle
@@ -61,6 +66,8 @@ def _pipeline(gpu, oracle, n_leaves, n_samples, log2_T, cam, seed=0, graph_check
     # table rows reached by an excluded point (threshold-ambiguous pixel) are excluded too
     reach = oracle.hash_bwd(RES16, log2_T, 4, o_pos, np.repeat((~keep)[:, None], 64, 1).astype(np.float64))
     assert_cond_close(gt.cpu().numpy(), o_gt, o_gab, mask=reach == 0, what="grad_table")
+    assert torch.equal(dh_fused, dh), "fused backward writes the same point gradients"
+    assert_cond_close(gt_fused.cpu().numpy(), o_gt, o_gab, mask=reach == 0, what="grad_table (fused)")
     print("pipeline: %d samples, %d fragments, max blended per pixel %d, flagged pixels %d"
           % (n_samples, int(ref["n_frags"].sum()), int(ref["n_contrib"].max()), int((~ok).sum())))
 
