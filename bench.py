@@ -221,7 +221,7 @@ def main():
 
     # preallocated buffers: the timed loop allocates nothing
     ws_s = api.workspace(B.inpc_sample_workspace_size(N_LEAVES, N), dev)
-    ws_r = api.workspace(api.rasterize_workspace_size(cam, opts, N), dev)
+    ws_r = api.workspace(api.rasterize_bwd_hashgrid_workspace_size(cam, opts, desc, N), dev)
     leaf = torch.empty(N, dtype=torch.int32, device=dev)
     pos = torch.empty(N, 3, dtype=torch.float32, device=dev)
     h = torch.empty(N, C, dtype=torch.float32, device=dev)
@@ -353,7 +353,8 @@ def run_e2e(args, api, B, tree, grid, cam, g_np, res, desc, opts, dev, world, ra
         g = hg.to(dev, non_blocking=True)
         _, pos = api.sample_octree(c, l, w, tree.root_size, 0, view_id, N)
         hq = api.query_hashgrid(desc, table, pos)
-        img, T, n, ws = api.rasterize_fwd(cam, opts, pos, hq)
+        ws = api.workspace(api.rasterize_bwd_hashgrid_workspace_size(cam, opts, desc, N), dev)
+        img, T, n, ws = api.rasterize_fwd(cam, opts, pos, hq, ws=ws)
         gt = torch.zeros_like(table)
         api.rasterize_bwd_hashgrid(cam, opts, desc, pos, hq, T, n, g, ws, gt)
         out_img.copy_(img, non_blocking=True)

@@ -140,7 +140,9 @@ inpc_status inpc_sample_octree_noalloc(const inpc_octree* tree, uint64_t seed, u
  *   table_dtype INPC_F32 or INPC_BF16 (dtype of the parameter table)
  *   out_dtype   INPC_F32 or INPC_BF16 (dtype of the query output h)
  * Table layout: level-major; level l has E_l = min(T, (N_l+1)^3) rows of
- * n_feats values; level l is stored densely iff (N_l+1)^3 <= T (row =
+ * n_feats values and starts on a multiple of 16 rows (the total is rounded
+ * up to 16; padding rows are never read and receive no gradient); level l
+ * is stored densely iff (N_l+1)^3 <= T (row =
  * x + y (N_l+1) + z (N_l+1)^2), otherwise through the spatial hash
  * row = (x * 1 ^ y * 2654435761 ^ z * 805459861) mod T (uint32 arithmetic). */
 typedef struct {
@@ -152,7 +154,7 @@ typedef struct {
   int32_t out_dtype;
 } inpc_hashgrid_desc;
 
-/* Total table rows (sum of E_l). */
+/* Total table rows (sum of E_l with the 16-row alignment of every level). */
 inpc_status inpc_hashgrid_n_entries(const inpc_hashgrid_desc* g, int64_t* n_entries);
 
 /* h[p, l * n_feats + f] = sum over the 8 corners of the level-l cell holding
@@ -260,7 +262,13 @@ inpc_status inpc_rasterize_bwd(const inpc_camera* cam, const inpc_raster_opts* o
  *   grid        descriptor of the query that produced `feat`
  *   grad_table  float32 [n_entries, n_feats], accumulated (+=)
  *   d_feat      optional float32 [n, F]: also written when non-NULL
- * Other arguments as for inpc_rasterize_bwd. */
+ * The workspace is the forward's, sized by
+ * inpc_rasterize_bwd_hashgrid_workspace_size (the rasterizer's workspace
+ * plus replicas of the coarse levels' gradient, which spread the atomic
+ * additions those few rows receive; they are summed into grad_table at the
+ * end of the call).  Other arguments as for inpc_rasterize_bwd. */
+inpc_status inpc_rasterize_bwd_hashgrid_workspace_size(const inpc_camera* cam, const inpc_raster_opts* opts,
+                                                       const inpc_hashgrid_desc* grid, int64_t n, size_t* bytes);
 inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const inpc_raster_opts* opts,
                                         const inpc_hashgrid_desc* grid, const float* pos, const void* feat, int64_t n,
                                         const float* T_final, const int32_t* n_contrib, const float* d_image,

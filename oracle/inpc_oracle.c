@@ -32,7 +32,8 @@
  *   - a level-l leaf spans center +- root_size * 2^-l / 2, half-open;
  *   - grid level l has resolution N_l; vertex coordinates 0..N_l; the level is
  *     stored densely iff (N_l+1)^3 <= T, else through the spatial hash
- *     x*1 ^ y*2654435761 ^ z*805459861 (mod T);
+ *     x*1 ^ y*2654435761 ^ z*805459861 (mod T); levels start on multiples of
+ *     16 table rows;
  *   - the projection (Eq. 5) is evaluated in the kernel's FP32 arithmetic with
  *     a fixed operation order, because it decides integer pixel indices and
  *     the depth order; everything downstream of it is FP64 here;
@@ -232,15 +233,18 @@ static int64_t level_entries(int64_t res, int64_t T) {
   return dense <= T ? dense : T;
 }
 
-/* Table rows per level and their level-major offsets; returns the total. */
+/* Table rows per level and their level-major offsets; returns the total.
+ * Storage layout (not fixed by the paper): each level starts on a multiple
+ * of 16 rows and the total is rounded up to 16; padding rows are unused. */
 int64_t oracle_hash_layout(int32_t n_levels, const int32_t* res, int32_t log2_T, int64_t* offsets) {
   int64_t T = 1ll << log2_T;
   int64_t off = 0;
   for (int l = 0; l < n_levels; ++l) {
+    off = (off + 15) / 16 * 16;
     if (offsets) offsets[l] = off;
     off += level_entries(res[l], T);
   }
-  return off;
+  return (off + 15) / 16 * 16;
 }
 
 /* Row of the table (within its level) that holds grid vertex (vx, vy, vz). */

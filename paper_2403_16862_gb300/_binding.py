@@ -35,7 +35,8 @@ DECLARED = [
     "inpc_last_error", "inpc_version", "inpc_kernel_launches", "inpc_read_device_status",
     "inpc_sample_workspace_size", "inpc_sample_octree", "inpc_sample_octree_noalloc",
     "inpc_hashgrid_n_entries", "inpc_query_hashgrid", "inpc_query_hashgrid_bwd",
-    "inpc_rasterize_workspace_size", "inpc_rasterize_fwd", "inpc_rasterize_bwd", "inpc_rasterize_bwd_hashgrid",
+    "inpc_rasterize_workspace_size", "inpc_rasterize_fwd", "inpc_rasterize_bwd",
+    "inpc_rasterize_bwd_hashgrid_workspace_size", "inpc_rasterize_bwd_hashgrid",
 ]
 
 
@@ -100,6 +101,9 @@ def load(path: str = LIB_PATH):
                                          _P, _P, _P, _P, C.c_size_t, _P]
         L.inpc_rasterize_bwd.argtypes = [C.POINTER(InpcCamera), C.POINTER(InpcRasterOpts), _P, _P, _P, C.c_int64,
                                          _P, _P, _P, _P, _P, _P, C.c_size_t, _P]
+        L.inpc_rasterize_bwd_hashgrid_workspace_size.argtypes = [C.POINTER(InpcCamera), C.POINTER(InpcRasterOpts),
+                                                                 C.POINTER(InpcHashgridDesc), C.c_int64,
+                                                                 C.POINTER(C.c_size_t)]
         L.inpc_rasterize_bwd_hashgrid.argtypes = [C.POINTER(InpcCamera), C.POINTER(InpcRasterOpts),
                                                   C.POINTER(InpcHashgridDesc), _P, _P, C.c_int64, _P, _P, _P, _P, _P,
                                                   _P, C.c_size_t, _P]
@@ -183,6 +187,14 @@ def inpc_rasterize_bwd(cam: InpcCamera, opts: InpcRasterOpts, pos: int, opacity,
                        stream: int):
     check(load().inpc_rasterize_bwd(C.byref(cam), C.byref(opts), pos, opacity, feat, n, T_final, n_contrib, d_image,
                                     d_opacity, d_feat, workspace, workspace_bytes, stream))
+
+
+def inpc_rasterize_bwd_hashgrid_workspace_size(cam: InpcCamera, opts: InpcRasterOpts, desc: InpcHashgridDesc,
+                                               n: int) -> int:
+    out = C.c_size_t(0)
+    check(load().inpc_rasterize_bwd_hashgrid_workspace_size(C.byref(cam), C.byref(opts), C.byref(desc), n,
+                                                            C.byref(out)))
+    return int(out.value)
 
 
 def inpc_rasterize_bwd_hashgrid(cam: InpcCamera, opts: InpcRasterOpts, desc: InpcHashgridDesc, pos: int, feat: int,

@@ -196,6 +196,11 @@ def rasterize_bwd(cam, opts: RasterOptions, pos, feat, opacity, T_final, n_contr
     return d_opacity, d_feat
 
 
+def rasterize_bwd_hashgrid_workspace_size(cam, opts: RasterOptions, desc, n: int) -> int:
+    """Workspace for rasterize_fwd followed by rasterize_bwd_hashgrid."""
+    return B.inpc_rasterize_bwd_hashgrid_workspace_size(camera(cam), opts.c(), desc, n)
+
+
 def rasterize_bwd_hashgrid(cam, opts: RasterOptions, desc, pos, feat, T_final, n_contrib, d_image, ws, grad_table,
                            d_feat=None):
     """Head-mode rasterizer backward fused with the grid query's adjoint:

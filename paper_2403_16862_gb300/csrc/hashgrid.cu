@@ -24,7 +24,7 @@ namespace {
 // stay resident in L2 instead of the whole table.
 constexpr int kLevelGroup = 2;
 
-template <class TT, class OT>
+template <class TT, class OT, bool kPairs>
 __global__ void __launch_bounds__(256) k_hash_fwd(GridParams P, const TT* __restrict__ table,
                                                   const float* __restrict__ pos, long long n, OT* __restrict__ h) {
   const int l0 = blockIdx.y * kLevelGroup;
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_hash_fwd(GridParams P, const TT* __rest
       const uint32_t r0 = vertex_row(P, l, cx, cy + by, cz + bz);
       const uint32_t r1 = vertex_row(P, l, cx + 1, cy + by, cz + bz);
       float4 t0, t1;
-      if ((r0 ^ r1) == 1u) {
+      if (kPairs && (r0 ^ r1) == 1u) {
         load_row_pair<TT>(tab, r0 & ~1u, t0, t1);
         if (r0 & 1u) {
           const float4 tmp = t0;
@@ -141,15 +141,25 @@ extern "C" inpc_status inpc_query_hashgrid(const inpc_hashgrid_desc* g, const vo
     return fail(INPC_ERR_INVALID_ARG, "inpc_query_hashgrid: misaligned table/output/pos");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const dim3 grid = grid_for(n, P.n_levels, 256);
-  if (g->table_dtype == INPC_F32 && g->out_dtype == INPC_F32)
-    k_hash_fwd<float, float><<<grid, 256, 0, s>>>(P, (const float*)table, pos, n, (float*)h_out);
-  else if (g->table_dtype == INPC_F32)
-    k_hash_fwd<float, __nv_bfloat16><<<grid, 256, 0, s>>>(P, (const float*)table, pos, n, (__nv_bfloat16*)h_out);
-  else if (g->out_dtype == INPC_F32)
-    k_hash_fwd<__nv_bfloat16, float><<<grid, 256, 0, s>>>(P, (const __nv_bfloat16*)table, pos, n, (float*)h_out);
-  else
-    k_hash_fwd<__nv_bfloat16, __nv_bfloat16>
-        <<<grid, 256, 0, s>>>(P, (const __nv_bfloat16*)table, pos, n, (__nv_bfloat16*)h_out);
+  // aligned row pairs need the table to start on a pair boundary
+  const bool pairs = aligned(table, 2 * ta);
+  if (g->table_dtype == INPC_F32 && g->out_dtype == INPC_F32) {
+    if (pairs) k_hash_fwd<float, float, true><<<grid, 256, 0, s>>>(P, (const float*)table, pos, n, (float*)h_out);
+    else k_hash_fwd<float, float, false><<<grid, 256, 0, s>>>(P, (const float*)table, pos, n, (float*)h_out);
+  } else if (g->table_dtype == INPC_F32) {
+    k_hash_fwd<float, __nv_bfloat16, false>
+        <<<grid, 256, 0, s>>>(P, (const float*)table, pos, n, (__nv_bfloat16*)h_out);
+  } else if (g->out_dtype == INPC_F32) {
+    k_hash_fwd<__nv_bfloat16, float, false>
+        <<<grid, 256, 0, s>>>(P, (const __nv_bfloat16*)table, pos, n, (float*)h_out);
+  } else {
+    if (pairs)
+      k_hash_fwd<__nv_bfloat16, __nv_bfloat16, true>
+          <<<grid, 256, 0, s>>>(P, (const __nv_bfloat16*)table, pos, n, (__nv_bfloat16*)h_out);
+    else
+      k_hash_fwd<__nv_bfloat16, __nv_bfloat16, false>
+          <<<grid, 256, 0, s>>>(P, (const __nv_bfloat16*)table, pos, n, (__nv_bfloat16*)h_out);
+  }
   return check_launch("k_hash_fwd");
 }
 

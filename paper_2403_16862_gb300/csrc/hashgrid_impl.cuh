@@ -11,6 +11,10 @@ namespace inpc {
 namespace {
 
 constexpr int kMaxLevels = 32;
+// Every level starts on a multiple of 16 rows (256 bytes of FP32 rows), so
+// row parity is the same within a level and in the whole table and aligned
+// row pairs can be fetched with one vector load.
+constexpr int64_t kLevelAlignRows = 16;
 
 struct GridParams {
   int n_levels;
@@ -42,9 +46,11 @@ inpc_status make_params(const inpc_hashgrid_desc* g, GridParams& p, int64_t* tot
     p.res[l] = (int)r;
     p.side[l] = (uint32_t)side;
     p.dense[l] = dense ? 1u : 0u;
+    off = (off + kLevelAlignRows - 1) / kLevelAlignRows * kLevelAlignRows;
     p.offset[l] = off;
     off += dense ? side * side * side : T;
   }
+  off = (off + kLevelAlignRows - 1) / kLevelAlignRows * kLevelAlignRows;
   for (int l = g->n_levels; l < kMaxLevels; ++l) {
     p.res[l] = 1; p.side[l] = 2; p.dense[l] = 1; p.offset[l] = off;
   }

@@ -9,12 +9,53 @@ namespace {
 // row, gathered as in k_point_grad, then that level's eight corner
 // contributions to the table gradient straight from registers (the adjoint
 // of the query, as in k_hash_bwd), so the row never goes through memory.
+// Coarse levels have few rows and receive millions of additions each, which
+// serialise on the same L2 addresses.  Their contributions go to one of
+// kReplicas copies (chosen by CTA) and k_fold_replicas sums the copies into
+// the table gradient afterwards.
+constexpr int kReplicas = 16;
+constexpr int64_t kReplicaMaxRows = 1 << 17;  // levels up to this many rows are replicated
+
+struct Replicas {
+  int n_levels;      // leading levels that are replicated
+  long long rows;    // table rows they span (level-aligned)
+  float* base;       // [kReplicas][rows][4]
+};
+
+inline Replicas replica_plan(const GridParams& Gp, void* base) {
+  Replicas r;
+  r.n_levels = 0;
+  while (r.n_levels < Gp.n_levels && r.n_levels + 1 < kMaxLevels &&
+         (Gp.offset[r.n_levels + 1] - Gp.offset[r.n_levels]) <= kReplicaMaxRows)
+    ++r.n_levels;
+  r.rows = r.n_levels > 0 ? Gp.offset[r.n_levels] : 0;
+  r.base = static_cast<float*>(base);
+  return r;
+}
+
+inline size_t replica_bytes(const Replicas& r) { return (size_t)kReplicas * r.rows * 4 * sizeof(float); }
+
+__global__ void k_fold_replicas(const float4* __restrict__ rep, long long rows, float4* __restrict__ grad) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < rows; i += (long long)gridDim.x * blockDim.x) {
+    float4 s = grad[i];
+#pragma unroll
+    for (int k = 0; k < kReplicas; ++k) {
+      const float4 v = rep[k * rows + i];
+      s.x += v.x;
+      s.y += v.y;
+      s.z += v.z;
+      s.w += v.w;
+    }
+    grad[i] = s;
+  }
+}
+
 template <int GA, class FT>
 __global__ void __launch_bounds__(kThreads) k_point_grad_hash(RP P, GridParams Gp, const float* __restrict__ pos,
                                                                const FT* __restrict__ feat,
                                                                const float* __restrict__ d_image, RasterWs ws,
                                                                float* __restrict__ grad_table,
-                                                               float* __restrict__ d_feat) {
+                                                               float* __restrict__ d_feat, Replicas rep) {
   constexpr int kGroups = kThreads / GA;
   const Group<GA> G;
   const int l = G.lg;
@@ -61,7 +102,9 @@ __global__ void __launch_bounds__(kThreads) k_point_grad_hash(RP P, GridParams G
     cell_frac(__ldg(pos + 3 * id + 0), N, cx, gx[0], gx[1]);
     cell_frac(__ldg(pos + 3 * id + 1), N, cy, gy[0], gy[1]);
     cell_frac(__ldg(pos + 3 * id + 2), N, cz, gz[0], gz[1]);
-    float* gl = grad_table + 4 * Gp.offset[l];
+    float* gl = l < rep.n_levels
+                    ? rep.base + 4 * ((long long)(blockIdx.x % kReplicas) * rep.rows + Gp.offset[l])
+                    : grad_table + 4 * Gp.offset[l];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
@@ -75,12 +118,19 @@ __global__ void __launch_bounds__(kThreads) k_point_grad_hash(RP P, GridParams G
 template <int GA, class FT>
 inpc_status launch_point_grad_hash(const RP& P, const GridParams& Gp, const float* pos, const FT* feat,
                                    const float* d_image, const RasterWs& ws, float* grad_table, float* d_feat,
-                                   cudaStream_t s) {
+                                   const Replicas& rep, cudaStream_t s) {
   constexpr int kGroups = kThreads / GA;
+  if (rep.rows > 0) INPC_CUDA(cudaMemsetAsync(rep.base, 0, replica_bytes(rep), s), "clear replicas");
   const long long grid = std::min<long long>(ceil_div(P.n, kGroups), (long long)device_sm_count() * 32);
   k_point_grad_hash<GA, FT><<<(unsigned)std::max<long long>(grid, 1), kThreads, 0, s>>>(P, Gp, pos, feat, d_image, ws,
-                                                                                         grad_table, d_feat);
-  return check_launch("k_point_grad_hash");
+                                                                                         grad_table, d_feat, rep);
+  INPC_TRY(check_launch("k_point_grad_hash"));
+  if (rep.rows > 0) {
+    k_fold_replicas<<<(unsigned)std::min<long long>(ceil_div(rep.rows, 256), device_sm_count() * 8), 256, 0, s>>>(
+        reinterpret_cast<const float4*>(rep.base), rep.rows, reinterpret_cast<float4*>(grad_table));
+    INPC_TRY(check_launch("k_fold_replicas"));
+  }
+  return INPC_OK;
 }
 
 }  // namespace
@@ -134,8 +184,12 @@ extern "C" inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const
   if (P.F != 4 * Gp.n_levels)
     return fail(INPC_ERR_INVALID_ARG, "n_channels (%d) must equal n_levels * n_feats (%d)", P.F, 4 * Gp.n_levels);
   const RasterWs need = carve(nullptr, P.n_pix, n);
-  if (!workspace || workspace_bytes < need.bytes || !aligned(workspace, 256))
-    return fail(INPC_ERR_INVALID_ARG, "workspace null, unaligned or smaller than %zu bytes", need.bytes);
+  const Replicas rep_need = replica_plan(Gp, nullptr);
+  const size_t total = need.bytes + replica_bytes(rep_need);
+  if (!workspace || workspace_bytes < total || !aligned(workspace, 256))
+    return fail(INPC_ERR_INVALID_ARG,
+                "workspace null, unaligned or smaller than %zu bytes (inpc_rasterize_bwd_hashgrid_workspace_size)",
+                total);
   if (n == 0) return INPC_OK;
   if (!pos || !feat || !T_final || !n_contrib || !d_image || !grad_table)
     return fail(INPC_ERR_INVALID_ARG, "null pointer");
@@ -144,15 +198,18 @@ extern "C" inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const
     return fail(INPC_ERR_INVALID_ARG, "feat/d_image/grad_table/d_feat misaligned");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   RasterWs ws = carve(workspace, P.n_pix, n);
+  const Replicas rep = replica_plan(Gp, static_cast<char*>(workspace) + need.bytes);
   return dispatch(P.F, [&](auto Vc, auto Gc) -> inpc_status {
     constexpr int V = decltype(Vc)::value, GA = decltype(Gc)::value;
     auto run = [&](auto ftag) -> inpc_status {
       using FT = decltype(ftag);
       const FT* f = static_cast<const FT*>(feat);
       INPC_TRY((launch_blend_bwd<V, GA, FT>(P, f, n_contrib, d_image, ws, s)));
-      if (Gp.n_levels <= 8) return launch_point_grad_hash<8, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, s);
-      if (Gp.n_levels <= 16) return launch_point_grad_hash<16, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, s);
-      return launch_point_grad_hash<32, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, s);
+      if (Gp.n_levels <= 8)
+        return launch_point_grad_hash<8, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, rep, s);
+      if (Gp.n_levels <= 16)
+        return launch_point_grad_hash<16, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, rep, s);
+      return launch_point_grad_hash<32, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, rep, s);
     };
     if constexpr (GA != 32) {
       if (P.bf16) return fail(INPC_ERR_UNSUPPORTED, "BF16 features need n_channels = 32, 64 or 128");
@@ -162,4 +219,17 @@ extern "C" inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const
       return run(float());
     }
   });
+}
+
+extern "C" inpc_status inpc_rasterize_bwd_hashgrid_workspace_size(const inpc_camera* cam, const inpc_raster_opts* opts,
+                                                                  const inpc_hashgrid_desc* grid, int64_t n,
+                                                                  size_t* bytes) {
+  if (!bytes) return fail(INPC_ERR_INVALID_ARG, "bytes is null");
+  RP P;
+  INPC_TRY(make_rp(cam, opts, n, P));
+  GridParams Gp;
+  int64_t n_entries = 0;
+  INPC_TRY(make_params(grid, Gp, &n_entries));
+  *bytes = carve(nullptr, P.n_pix, n).bytes + replica_bytes(replica_plan(Gp, nullptr));
+  return INPC_OK;
 }

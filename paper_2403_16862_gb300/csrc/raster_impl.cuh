@@ -61,10 +61,12 @@ struct RP {
 struct RasterWs {
   uint32_t* status;
   uint32_t* heavy_count;     // header word 1
+  uint32_t* large_count;     // header word 2
   uint32_t* pix_count;       // [n_pix]
   uint32_t* pix_start;       // [n_pix + 1]
   uint32_t* tops;            // prefix-sum block totals
   uint32_t* heavy;           // [n_pix] pixels on the CTA path
+  uint32_t* large;           // [n_pix] pixels with 4 or 8 registers per lane
   unsigned long long* keys;  // [4n] bucketed fragment keys
   float* alpha;              // [4n] fragment alphas
   uint32_t* pslot;           // [4n] bucket slot of each point corner (kNoSlot off-image)
@@ -81,11 +83,13 @@ RasterWs carve(void* base, long long n_pix, long long n) {
   RasterWs w;
   w.status = reinterpret_cast<uint32_t*>(base);
   w.heavy_count = base ? reinterpret_cast<uint32_t*>(base) + 1 : nullptr;
+  w.large_count = base ? reinterpret_cast<uint32_t*>(base) + 2 : nullptr;
   const long long nf = std::max<long long>(4 * n, 1);
   w.pix_count = c.take<uint32_t>(n_pix);
   w.pix_start = c.take<uint32_t>(n_pix + 1);
   w.tops = c.take<uint32_t>(scan::n_tops(n_pix));
   w.heavy = c.take<uint32_t>(n_pix);
+  w.large = c.take<uint32_t>(n_pix);
   w.keys = c.take<unsigned long long>(nf);
   w.alpha = c.take<float>(nf);
   w.pslot = c.take<uint32_t>(nf);
@@ -201,15 +205,21 @@ struct CountLoad {
   __device__ uint32_t operator()(int64_t i) const { return c[i]; }
 };
 
-// Pixels whose bucket exceeds the group capacity go to the CTA path.
-__global__ void k_heavy_list(const uint32_t* __restrict__ pix_start, long long n_pix, const uint32_t* __restrict__ tops,
-                             long long nb, uint32_t cap, uint32_t* __restrict__ heavy, uint32_t* heavy_count,
-                             uint32_t* __restrict__ pix_start_w) {
+// Bucket-size classes: up to cap_small fragments (at most 2 registers per
+// lane) stay with the tile-order kernel; up to cap_large go to the list of
+// the register kernel with 4 or 8 registers per lane; larger ones go to the
+// CTA path.
+__global__ void k_classify(const uint32_t* __restrict__ pix_start, long long n_pix, const uint32_t* __restrict__ tops,
+                           long long nb, uint32_t cap_small, uint32_t cap_large, uint32_t* __restrict__ heavy,
+                           uint32_t* heavy_count, uint32_t* __restrict__ large, uint32_t* large_count,
+                           uint32_t* __restrict__ pix_start_w) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q == 0) pix_start_w[n_pix] = tops[nb];
   if (q >= n_pix) return;
   const uint32_t end = q + 1 < n_pix ? pix_start[q + 1] : tops[nb];
-  if (end - pix_start[q] > cap) heavy[atomicAdd(heavy_count, 1u)] = (uint32_t)q;
+  const uint32_t m = end - pix_start[q];
+  if (m > cap_large) heavy[atomicAdd(heavy_count, 1u)] = (uint32_t)q;
+  else if (m > cap_small) large[atomicAdd(large_count, 1u)] = (uint32_t)q;
 }
 
 // ------------------------------------------------------------- ordering ---
@@ -617,8 +627,28 @@ __device__ void blend_fwd_reg(const Group<GA>& G, const RP& P, const RasterWs& w
   }
 }
 
+// Bucket offsets of a group's pixels, GA at a time: lane j holds pixel
+// `first + j * stride` of the tile (or m = -1 outside the image).
+template <int GA>
+__device__ __forceinline__ void pixel_batch(const Group<GA>& G, const RP& P, const RasterWs& ws, int tx, int ty,
+                                            int p, uint32_t& s0, int& m, long long& q) {
+  m = -1;
+  s0 = 0;
+  q = 0;
+  if (p < P.TW * P.TH) {
+    const int px = tx * P.TW + p % P.TW, py = ty * P.TH + p / P.TW;
+    if (px < P.cam.W && py < P.cam.H) {
+      q = (long long)py * P.cam.W + px;
+      s0 = ws.pix_start[q];
+      m = (int)(ws.pix_start[q + 1] - s0);
+    }
+  }
+}
+
+// Tile-order kernel for small buckets (at most 2 registers per lane): high
+// occupancy, the offsets of GA pixels fetched with one load per lane.
 template <int V, int GA, class FT>
-__global__ void __launch_bounds__(kThreads, 3) k_blend_fwd(RP P, const FT* __restrict__ feat, RasterWs ws,
+__global__ void __launch_bounds__(kThreads, 6) k_blend_fwd(RP P, const FT* __restrict__ feat, RasterWs ws,
                                                          FT* __restrict__ image, float* __restrict__ T_final,
                                                          int32_t* __restrict__ n_contrib) {
   constexpr int kGroups = kThreads / GA;
@@ -626,18 +656,37 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_fwd(RP P, const FT* __res
   const int group = threadIdx.x / GA;
   const int t = blockIdx.x;
   const int tx = t % P.tiles_x, ty = t / P.tiles_x;
-  for (int p = group; p < P.TW * P.TH; p += kGroups) {
-    const int px = tx * P.TW + p % P.TW, py = ty * P.TH + p / P.TW;
-    if (px >= P.cam.W || py >= P.cam.H) continue;
-    const long long q = (long long)py * P.cam.W + px;
+  const int npix = P.TW * P.TH;
+  for (int b = group; b < npix; b += kGroups * GA) {
+    uint32_t s0l;
+    int ml;
+    long long ql;
+    pixel_batch<GA>(G, P, ws, tx, ty, b + G.lg * kGroups, s0l, ml, ql);
+    for (int j = 0; j < GA && b + j * kGroups < npix; ++j) {
+      const int m = G.bcast(ml, j);
+      if (m < 0 || m > 2 * GA) continue;  // outside the image, or another class
+      const uint32_t s0 = G.bcast(s0l, j);
+      const long long q = G.bcast(ql, j);
+      if (m <= GA) blend_fwd_reg<V, GA, FT, 1>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
+      else blend_fwd_reg<V, GA, FT, 2>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
+    }
+  }
+}
+
+// List kernel for buckets of 2 * GA < m <= kRegMax * GA.
+template <int V, int GA, class FT>
+__global__ void __launch_bounds__(kThreads, 3) k_blend_fwd_large(RP P, const FT* __restrict__ feat, RasterWs ws,
+                                                               FT* __restrict__ image, float* __restrict__ T_final,
+                                                               int32_t* __restrict__ n_contrib) {
+  constexpr int kGroups = kThreads / GA;
+  const Group<GA> G;
+  const uint32_t n_large = *ws.large_count;
+  for (uint32_t h = blockIdx.x * kGroups + threadIdx.x / GA; h < n_large; h += gridDim.x * kGroups) {
+    const long long q = ws.large[h];
     const uint32_t s0 = ws.pix_start[q];
     const int m = (int)(ws.pix_start[q + 1] - s0);
-    const int regs = (m + GA - 1) / GA;
-    if (regs <= 1) blend_fwd_reg<V, GA, FT, 1>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
-    else if (regs <= 2) blend_fwd_reg<V, GA, FT, 2>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
-    else if (regs <= 4) blend_fwd_reg<V, GA, FT, 4>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
-    else if (regs <= kRegMax) blend_fwd_reg<V, GA, FT, kRegMax>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
-    // larger buckets: CTA path
+    if (m <= 4 * GA) blend_fwd_reg<V, GA, FT, 4>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
+    else blend_fwd_reg<V, GA, FT, kRegMax>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
   }
 }
 
@@ -711,7 +760,7 @@ __device__ void blend_bwd_reg(const Group<GA>& G, const RP& P, const RasterWs& w
 }
 
 template <int V, int GA, class FT>
-__global__ void __launch_bounds__(kThreads, 3) k_blend_bwd(RP P, const FT* __restrict__ feat,
+__global__ void __launch_bounds__(kThreads, 6) k_blend_bwd(RP P, const FT* __restrict__ feat,
                                                          const int32_t* __restrict__ n_contrib,
                                                          const float* __restrict__ d_image, RasterWs ws) {
   constexpr int kGroups = kThreads / GA;
@@ -719,19 +768,39 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_bwd(RP P, const FT* __res
   const int group = threadIdx.x / GA;
   const int t = blockIdx.x;
   const int tx = t % P.tiles_x, ty = t / P.tiles_x;
-  for (int p = group; p < P.TW * P.TH; p += kGroups) {
-    const int px = tx * P.TW + p % P.TW, py = ty * P.TH + p / P.TW;
-    if (px >= P.cam.W || py >= P.cam.H) continue;
-    const long long q = (long long)py * P.cam.W + px;
+  const int npix = P.TW * P.TH;
+  for (int b = group; b < npix; b += kGroups * GA) {
+    uint32_t s0l;
+    int ml;
+    long long ql;
+    pixel_batch<GA>(G, P, ws, tx, ty, b + G.lg * kGroups, s0l, ml, ql);
+    const int nbl = ml > 0 ? min(ml, (int)n_contrib[ql]) : 0;
+    for (int j = 0; j < GA && b + j * kGroups < npix; ++j) {
+      const int m = G.bcast(ml, j);
+      if (m <= 0 || m > 2 * GA) continue;
+      const uint32_t s0 = G.bcast(s0l, j);
+      const long long q = G.bcast(ql, j);
+      const int nb = G.bcast(nbl, j);
+      if (m <= GA) blend_bwd_reg<V, GA, FT, 1>(G, P, ws, s0, m, nb, q, feat, d_image);
+      else blend_bwd_reg<V, GA, FT, 2>(G, P, ws, s0, m, nb, q, feat, d_image);
+    }
+  }
+}
+
+template <int V, int GA, class FT>
+__global__ void __launch_bounds__(kThreads, 3) k_blend_bwd_large(RP P, const FT* __restrict__ feat,
+                                                               const int32_t* __restrict__ n_contrib,
+                                                               const float* __restrict__ d_image, RasterWs ws) {
+  constexpr int kGroups = kThreads / GA;
+  const Group<GA> G;
+  const uint32_t n_large = *ws.large_count;
+  for (uint32_t h = blockIdx.x * kGroups + threadIdx.x / GA; h < n_large; h += gridDim.x * kGroups) {
+    const long long q = ws.large[h];
     const uint32_t s0 = ws.pix_start[q];
     const int m = (int)(ws.pix_start[q + 1] - s0);
-    if (m == 0) continue;
     const int nb = min(m, (int)n_contrib[q]);
-    const int regs = (m + GA - 1) / GA;
-    if (regs <= 1) blend_bwd_reg<V, GA, FT, 1>(G, P, ws, s0, m, nb, q, feat, d_image);
-    else if (regs <= 2) blend_bwd_reg<V, GA, FT, 2>(G, P, ws, s0, m, nb, q, feat, d_image);
-    else if (regs <= 4) blend_bwd_reg<V, GA, FT, 4>(G, P, ws, s0, m, nb, q, feat, d_image);
-    else if (regs <= kRegMax) blend_bwd_reg<V, GA, FT, kRegMax>(G, P, ws, s0, m, nb, q, feat, d_image);
+    if (m <= 4 * GA) blend_bwd_reg<V, GA, FT, 4>(G, P, ws, s0, m, nb, q, feat, d_image);
+    else blend_bwd_reg<V, GA, FT, kRegMax>(G, P, ws, s0, m, nb, q, feat, d_image);
   }
 }
 
@@ -1153,7 +1222,7 @@ void set_smem(K kernel, size_t bytes, std::once_flag& once) {
 // workspace for the backward).
 template <class FT>
 inpc_status bin_fragments(const RP& P, const float* pos, const float* opacity, const FT* feat, const RasterWs& ws,
-                          uint32_t cap_group, cudaStream_t s) {
+                          uint32_t cap_small, uint32_t cap_group, cudaStream_t s) {
   INPC_CUDA(cudaMemsetAsync(ws.pix_count, 0, sizeof(uint32_t) * P.n_pix, s), "clear pixel counts");
   if (P.n > 0) {
     k_pix_count<<<point_grid(P.n), 256, 0, s>>>(P, pos, ws.pix_count);
@@ -1161,9 +1230,10 @@ inpc_status bin_fragments(const RP& P, const float* pos, const float* opacity, c
   }
   INPC_TRY((scan::run<uint32_t, CountLoad, false>(CountLoad{ws.pix_count}, P.n_pix, ws.pix_start, ws.tops, s)));
   const long long nb = ceil_div(P.n_pix, scan::kBlock);
-  k_heavy_list<<<(unsigned)ceil_div(P.n_pix, 256), 256, 0, s>>>(ws.pix_start, P.n_pix, ws.tops, nb, cap_group, ws.heavy,
-                                                                 ws.heavy_count, ws.pix_start);
-  INPC_TRY(check_launch("k_heavy_list"));
+  k_classify<<<(unsigned)ceil_div(P.n_pix, 256), 256, 0, s>>>(ws.pix_start, P.n_pix, ws.tops, nb, cap_small, cap_group,
+                                                               ws.heavy, ws.heavy_count, ws.large, ws.large_count,
+                                                               ws.pix_start);
+  INPC_TRY(check_launch("k_classify"));
   if (P.n > 0) {
     k_pix_scatter<FT><<<point_grid(P.n), 256, 0, s>>>(P, pos, opacity, feat, ws.pix_start, ws.pix_count, ws.keys, ws.alpha,
                                                   ws.pslot);
@@ -1175,11 +1245,13 @@ inpc_status bin_fragments(const RP& P, const float* pos, const float* opacity, c
 template <int V, int GA, class FT>
 inpc_status launch_fwd(const RP& P, const float* pos, const float* opacity, const FT* feat, const RasterWs& ws,
                        FT* image, float* T_final, int32_t* n_contrib, cudaStream_t s) {
-  INPC_TRY(bin_fragments(P, pos, opacity, feat, ws, GA * kRegMax, s));
+  INPC_TRY(bin_fragments(P, pos, opacity, feat, ws, 2 * GA, GA * kRegMax, s));
   static std::once_flag f2;
   set_smem(k_blend_fwd_heavy<V, GA, FT>, HeavyBuf::bytes(), f2);
   k_blend_fwd<V, GA, FT><<<P.n_tiles, kThreads, 0, s>>>(P, feat, ws, image, T_final, n_contrib);
   INPC_TRY(check_launch("k_blend_fwd"));
+  k_blend_fwd_large<V, GA, FT><<<device_sm_count() * 3, kThreads, 0, s>>>(P, feat, ws, image, T_final, n_contrib);
+  INPC_TRY(check_launch("k_blend_fwd_large"));
   k_blend_fwd_heavy<V, GA, FT><<<device_sm_count() * 4, kThreads, HeavyBuf::bytes(), s>>>(P, feat, ws, image, T_final,
                                                                                    n_contrib);
   return check_launch("k_blend_fwd_heavy");
@@ -1192,6 +1264,8 @@ inpc_status launch_blend_bwd(const RP& P, const FT* feat, const int32_t* n_contr
   set_smem(k_blend_bwd_heavy<V, GA, FT>, HeavyBuf::bytes(), f2);
   k_blend_bwd<V, GA, FT><<<P.n_tiles, kThreads, 0, s>>>(P, feat, n_contrib, d_image, ws);
   INPC_TRY(check_launch("k_blend_bwd"));
+  k_blend_bwd_large<V, GA, FT><<<device_sm_count() * 3, kThreads, 0, s>>>(P, feat, n_contrib, d_image, ws);
+  INPC_TRY(check_launch("k_blend_bwd_large"));
   k_blend_bwd_heavy<V, GA, FT><<<device_sm_count() * 4, kThreads, HeavyBuf::bytes(), s>>>(P, feat, n_contrib, d_image,
                                                                                            ws);
   return check_launch("k_blend_bwd_heavy");

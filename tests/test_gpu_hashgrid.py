@@ -88,3 +88,18 @@ def test_bf16_table_error_statement(gpu, oracle):
     rel = np.abs(h - ref) / (ab + 1e-30)
     print("BF16 table+output: max err/sum|terms| = %.3e, mean = %.3e" % (rel.max(), rel.mean()))
     assert rel.max() < 2 * 2.0 ** -8
+
+
+def test_query_table_alignments(gpu, oracle):
+    """A 16-byte-aligned (not 32) FP32 table takes the per-row kernel; both
+    variants give the oracle's values."""
+    grid = _grid(oracle, 14, res=RES16[:8])
+    pos = _pos(9, 20_000)
+    desc = api.hashgrid_desc(grid.res, grid.log2_T)
+    ref, ab = oracle.hash_fwd(grid.res, grid.log2_T, grid.table, pos, with_abs=True)
+    buf = torch.zeros(grid.table.size + 8, dtype=torch.float32, device=gpu)
+    for shift in (0, 4):  # floats: 0 -> 32-byte aligned, 4 -> 16-byte aligned
+        t = buf[shift:shift + grid.table.size].view(grid.table.shape)
+        t.copy_(torch.from_numpy(grid.table).to(gpu))
+        h = api.query_hashgrid(desc, t, torch.from_numpy(pos).to(gpu))
+        assert_cond_close(h.cpu().numpy(), ref, ab, what="h (shift %d)" % shift)

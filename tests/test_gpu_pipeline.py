@@ -32,7 +32,8 @@ def _pipeline(gpu, oracle, n_leaves, n_samples, log2_T, cam, seed=0, graph_check
     opts = api.RasterOptions(n_channels=64, head_mode=True)
     leaf, pos = api.sample_octree(c, l, w, tree.root_size, seed, 0, n_samples)
     h = api.query_hashgrid(desc, table, pos)
-    img, T, n, ws = api.rasterize_fwd(cam, opts, pos, h)
+    ws = api.workspace(api.rasterize_bwd_hashgrid_workspace_size(cam, opts, desc, n_samples), gpu)
+    img, T, n, ws = api.rasterize_fwd(cam, opts, pos, h, ws=ws)
     _, dh = api.rasterize_bwd(cam, opts, pos, h, None, T, n, torch.from_numpy(g_img).to(gpu), ws)
     gt = torch.zeros_like(table)
     api.query_hashgrid_bwd(desc, pos, dh, gt)

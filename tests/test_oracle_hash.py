@@ -13,15 +13,29 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 RES16 = scenes.geometric_resolutions(16, 16, 4096)
 
 
+def _up16(x):
+    return (x + 15) // 16 * 16
+
+
 def test_resolutions_and_layout(oracle):
     assert RES16 == [16, 23, 33, 48, 70, 101, 147, 212, 307, 445, 645, 933, 1351, 1955, 2830, 4096]
     total, offs = oracle.hash_layout(RES16, 19)
     dense = [(r + 1) ** 3 for r in RES16[:5]]
+    assert dense == [4913, 13824, 39304, 117649, 357911]
     assert all(d <= 2 ** 19 for d in dense) and (RES16[5] + 1) ** 3 > 2 ** 19
-    assert total == sum(dense) + 11 * 2 ** 19 == 6300769
-    assert offs[0] == 0 and offs[5] == sum(dense)
+    # every level starts on a multiple of 16 rows
+    want, off = [], 0
+    for e in dense + [2 ** 19] * 11:
+        off = _up16(off)
+        want.append(off)
+        off += e
+    assert list(offs) == want and total == _up16(off)
+    assert offs[1] == 4928 and offs[5] == 533648 and total == 533648 + 11 * 2 ** 19 == 6300816
     total21, _ = oracle.hash_layout(RES16, 21)
-    assert total21 == sum((r + 1) ** 3 for r in RES16[:6]) + 10 * 2 ** 21
+    off = 0
+    for e in [(r + 1) ** 3 for r in RES16[:6]] + [2 ** 21] * 10:
+        off = _up16(off) + e
+    assert total21 == _up16(off)
 
 
 def test_dense_index_is_bijective(oracle):
