@@ -72,6 +72,40 @@ def algorithmic_bytes(n, n_leaves, n_entries, n_frag, n_pix):
     }
 
 
+KERNELS = ["k_draw_count", "k_place", "k_hash_fwd", "k_pix_count", "k_pix_scatter", "k_blend_fwd",
+           "k_blend_fwd_large", "k_blend_fwd_heavy", "k_blend_bwd", "k_blend_bwd_large", "k_blend_bwd_heavy",
+           "k_point_grad_hash", "k_fold_replicas", "k_point_grad", "k_hash_bwd"]
+
+# DRAM bytes per launch of the dominant kernel on the full workload, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); see profiles/.
+TRAFFIC = {"k_point_grad_hash": 2.358428e9 + 1.331076e9}
+
+
+def kernel_bytes(kernel, n, n_entries, n_frag, n_pix):
+    """Algorithmic bytes of one launch (FP32, head mode, C channels).
+
+    k_point_grad_hash (fused rasterizer backward tail + grid adjoint): per
+    point its four fragment slots (16 B), position (12 B), channel 0 of its
+    feature row (4 B); per fragment the blend backward's two scalars (8 B);
+    the upstream image gradient once (4 C per pixel); the table gradient
+    read and written once (2 x 16 B per row).
+    k_hash_fwd: positions, the table once, the feature rows written once."""
+    if kernel == "k_point_grad_hash":
+        return 32 * n + 8 * n_frag + 4 * C * n_pix + 32 * n_entries
+    if kernel == "k_hash_fwd":
+        return 12 * n + 16 * n_entries + 4 * C * n
+    return None
+
+
+def atomic_ceiling(kernel, n, ms):
+    """The grid adjoint issues 8 vector reductions (16 B) per point and level;
+    L2 atomic throughput bounds it, not DRAM."""
+    if kernel != "k_point_grad_hash":
+        return {}
+    ops = 8 * 16 * n
+    return {"l2_vector_atomics": ops, "l2_atomic_gops": ops / (ms * 1e-3) / 1e9}
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -185,6 +219,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the BF16 (16M points, 1920x1080) and batched BF16 (8 views) forms")
     ap.add_argument("--unfused", action="store_true",
                     help="separate rasterizer backward and grid adjoint (materialises dh)")
     args = ap.parse_args()
@@ -201,7 +237,7 @@ def main():
     from paper_2403_16862_gb300 import build
     build.build()
     from paper_2403_16862_gb300 import _binding as B
-    from paper_2403_16862_gb300 import api
+    from paper_2403_16862_gb300 import api, shard
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -268,11 +304,19 @@ def main():
     sampler.start()
     time.sleep(0.3)
     launches0 = B.inpc_kernel_launches()
+    B.inpc_kernel_timer_read()  # drop records of earlier launches
+    B.inpc_kernel_timer_enable(True)
     for k in range(args.steps):
         flush.fill_(k & 0xFF)  # evict the previous step from L2 (outside the events)
-        view(rank * args.steps + k, evs[k])
+        view(shard.view_ids(rank, world, k)[0], evs[k])
     torch.cuda.synchronize()
+    B.inpc_kernel_timer_enable(False)
     launches = B.inpc_kernel_launches() - launches0
+    kernel_ms = {}
+    for kname in KERNELS:
+        ms, cnt = B.inpc_kernel_timer_read(kname)
+        if cnt:
+            kernel_ms[kname] = (ms / args.steps, cnt // args.steps)
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
@@ -280,10 +324,7 @@ def main():
     per_stage = {s: [evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)] for i, s in enumerate(stages)}
     step_ms = [evs[k][0].elapsed_time(evs[k][5]) for k in range(args.steps)]
     total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = shard.max_over_ranks(total_ms, dev)
     value = N * args.steps * world / (total_ms * 1e-3) / 1e9
     ms_per_step = total_ms / args.steps
 
@@ -295,13 +336,22 @@ def main():
         bytes_model["raster_bwd+query_bwd"] = bytes_model.pop("raster_bwd") + bytes_model.pop("query_bwd")
     peak, peak_kind = measured_peak_hbm()
     stage_mean = {s: statistics.mean(v) for s, v in per_stage.items()}
-    dom = max(stage_mean, key=stage_mean.get)
-    achieved = bytes_model[dom] / (stage_mean[dom] * 1e-3) / 1e9
     total_bytes = sum(bytes_model.values())
+    # the dominant kernel: most device time per step (one launch per step)
+    if not kernel_ms:
+        raise RuntimeError("the library's kernel timer recorded no launch")
+    dom = max(kernel_ms, key=lambda k: kernel_ms[k][0])
+    dom_ms = kernel_ms[dom][0] / max(kernel_ms[dom][1], 1)
+    dom_bytes = kernel_bytes(dom, N, n_entries, 4 * N, H * W)
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_bytes else None
 
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, api, B, tree, grid, cam, g_np, res, desc, opts, dev, world, rank)
+
+    forms = None
+    if not args.no_forms and not args.unfused:
+        forms = run_forms(args, api, B, dev, world, rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -314,15 +364,19 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config({"views_per_step_per_gpu": 1, "parallelism": "views sharded over %d GPU(s)" % world}),
             "stages_ms": {s: round(stage_mean[s], 4) for s in stages},
+            "kernels_ms": {k: round(v[0], 4) for k, v in sorted(kernel_ms.items(), key=lambda kv: -kv[1][0])},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "algorithmic_bytes": bytes_model[dom]},
+                         "frac": achieved / peak if achieved else None,
+                         "traffic": TRAFFIC.get(dom) if not args.unfused else None,
+                         "peak_kind": peak_kind + " (copy bandwidth)", "launch_ms": dom_ms,
+                         "algorithmic_bytes": dom_bytes, **atomic_ceiling(dom, N, dom_ms)},
             "step_roofline": {"algorithmic_bytes": total_bytes,
                               "achieved_gbs": total_bytes / (ms_per_step * 1e-3) / 1e9,
                               "frac": total_bytes / (ms_per_step * 1e-3) / 1e9 / peak},
             "gpu_launches": int(launches),
             "clocks": clocks,
             "e2e": e2e,
+            "forms": forms,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -331,12 +385,145 @@ def main():
     return 0
 
 
+def run_forms(args, api, B, dev, world, rank):
+    """The precision and batching forms on the same GPU.
+
+    BF16 form: a 1,048,576-leaf octree, 16,777,216 samples, a 16-level 2^21
+    BF16 grid, BF16 feature rows and image (FP32 blending, transmittance and
+    gradients), 1920x1080, forward + fused backward; against the same view in
+    FP32.  Batched BF16 form: 8 views of uneven size (640x480 .. 1920x1080,
+    9.33 Mpixels in all) on an orbit around the scene, 8,388,608 samples per
+    view from the shared octree and BF16 grid, all views in one CUDA graph
+    over 4 streams with autotuned tiles; against the plain FP32 form (the
+    same views one after another on one stream).  Accuracy is stated as the
+    norm-wise difference to the FP32 form (the FP32 form itself matches the
+    FP64 oracle to 1e-5 in the tests).  Upstream image gradients ~ N(0, 1)
+    are drawn on the device from a seeded generator."""
+    import torch
+    from paper_2403_16862_gb300 import scenes
+    from paper_2403_16862_gb300.batch import ViewBatch
+
+    steps = max(2, min(args.steps, 5))
+    res = scenes.geometric_resolutions(16, 16, 4096)
+    tree = scenes.make_octree(0, 1 << 20, start_level=6)
+    log2_T = 21
+    n_ent = api.hashgrid_n_entries(res, log2_T)
+    grid = scenes.make_hashgrid(1, n_ent, res, log2_T)
+    c, l, w = (torch.from_numpy(x).to(dev) for x in (tree.centers, tree.levels, tree.weights))
+    t32 = torch.from_numpy(grid.table).to(dev)
+    t16 = t32.to(torch.bfloat16)
+    d32 = api.hashgrid_desc(res, log2_T)
+    d16 = api.hashgrid_desc(res, log2_T, table_dtype=torch.bfloat16, out_dtype=torch.bfloat16)
+    gen = torch.Generator(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def dgrad(cam, seed):
+        gen.manual_seed(seed)
+        return torch.randn(cam.height, cam.width, C, generator=gen, device=dev)
+
+    def nerr(a, b):
+        a, b = a.double(), b.double()
+        return float(torch.linalg.norm(a - b) / torch.linalg.norm(a))
+
+    def timed(fn, n_steps):
+        for i in range(3):
+            fn(i)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2 * n_steps)]
+        for k in range(n_steps):
+            flush.fill_(k & 0xFF)
+            e[2 * k].record()
+            fn(k)
+            e[2 * k + 1].record()
+        torch.cuda.synchronize()
+        return statistics.median(e[2 * k].elapsed_time(e[2 * k + 1]) for k in range(n_steps))
+
+    class Plain:
+        """One view at a time on the current stream, preallocated buffers."""
+        def __init__(self, cams, n, bf16):
+            self.n, self.bf16 = n, bf16
+            self.desc, self.table = (d16, t16) if bf16 else (d32, t32)
+            hdt = torch.bfloat16 if bf16 else torch.float32
+            self.opts = api.RasterOptions(n_channels=C, head_mode=True, bf16=bf16)
+            big = max(cams, key=lambda q: q.width * q.height)
+            self.ws_s = api.workspace(B.inpc_sample_workspace_size(tree.n_leaves, n), dev)
+            self.ws_r = api.workspace(api.rasterize_bwd_hashgrid_workspace_size(big, self.opts, self.desc, n), dev)
+            self.leaf = torch.empty(n, dtype=torch.int32, device=dev)
+            self.pos = torch.empty(n, 3, dtype=torch.float32, device=dev)
+            self.h = torch.empty(n, C, dtype=hdt, device=dev)
+            self.imgs = [torch.empty(q.height, q.width, C, dtype=hdt, device=dev) for q in cams]
+            self.Ts = [torch.empty(q.height, q.width, dtype=torch.float32, device=dev) for q in cams]
+            self.ncs = [torch.empty(q.height, q.width, dtype=torch.int32, device=dev) for q in cams]
+            self.gt = torch.zeros(n_ent, 4, dtype=torch.float32, device=dev)
+            self.cams = cams
+
+        def run(self, grads, view0=0):
+            self.gt.zero_()
+            for v, cam in enumerate(self.cams):
+                api.sample_octree(c, l, w, tree.root_size, 0, view0 + v, self.n, ws=self.ws_s,
+                                  out=(self.leaf, self.pos))
+                api.query_hashgrid(self.desc, self.table, self.pos, out=self.h)
+                api.rasterize_fwd(cam, self.opts, self.pos, self.h, None, ws=self.ws_r,
+                                  out=(self.imgs[v], self.Ts[v], self.ncs[v]))
+                api.rasterize_bwd_hashgrid(cam, self.opts, self.desc, self.pos, self.h, self.Ts[v], self.ncs[v],
+                                           grads[v], self.ws_r, self.gt)
+
+    out = {}
+    # ---- BF16 form, one 1920x1080 view of 16M samples
+    n4 = 1 << 24
+    cam4 = scenes.make_camera((0.5, 0.5, -1.2), 900.0 * 1080 / 832, 900.0 * 1080 / 832, 960.0, 540.0, 1920, 1080)
+    g4 = [dgrad(cam4, 11)]
+    p32 = Plain([cam4], n4, False)
+    ms32 = timed(lambda k: p32.run(g4, view0=0), steps)
+    img32, gt32 = p32.imgs[0].clone(), p32.gt.clone()
+    del p32
+    torch.cuda.empty_cache()
+    p16 = Plain([cam4], n4, True)
+    ms16 = timed(lambda k: p16.run(g4, view0=0), steps)
+    out["bf16_view"] = {
+        "workload": "1,048,576-leaf octree, 16,777,216 samples, 16-level 2^21x4 BF16 grid, BF16 h and image, "
+                    "1920x1080, fwd + fused bwd",
+        "ms_per_view": ms16, "gpoints_s": n4 / (ms16 * 1e-3) / 1e9,
+        "fp32_ms_per_view": ms32, "speedup_vs_fp32": ms32 / ms16,
+        "error_vs_fp32_normwise": {"image": nerr(img32, p16.imgs[0]), "grad_table": nerr(gt32, p16.gt)}}
+    del p16, img32, gt32, g4
+    torch.cuda.empty_cache()
+
+    # ---- batched BF16 form, 8 uneven views of 8M samples each
+    sizes = [(640, 480), (960, 540), (1024, 768), (1280, 832), (1280, 832), (1600, 900), (1920, 1080), (1920, 1080)]
+    cams = scenes.orbit_cameras(sizes)
+    n5 = 1 << 23
+    grads = [dgrad(q, 100 + v) for v, q in enumerate(cams)]
+    p32 = Plain(cams, n5, False)
+    ms_plain = timed(lambda k: p32.run(grads), steps)
+    imgs32 = [x.clone() for x in p32.imgs]
+    gt32 = p32.gt.clone()
+    del p32
+    torch.cuda.empty_cache()
+    vb = ViewBatch(c, l, w, tree.root_size, d16, t16, cams, n5, grads, seed=0, n_streams=4, bf16=True, tune=True)
+    vb.capture()
+    ms_batch = timed(lambda k: vb.step(), steps)
+    errs = [nerr(imgs32[v], vb.views[v]["img"]) for v in range(len(cams))]
+    out["bf16_batched_8views"] = {
+        "workload": "8 views %s, 8,388,608 samples each from one 1,048,576-leaf octree, 16-level 2^21x4 BF16 grid, "
+                    "one CUDA graph over 4 streams, autotuned tiles, fwd + fused bwd" % sizes,
+        "ms_per_step": ms_batch, "ms_per_view": ms_batch / len(cams),
+        "gpoints_s": n5 * len(cams) / (ms_batch * 1e-3) / 1e9,
+        "fp32_unbatched_ms_per_step": ms_plain, "speedup_vs_plain_fp32": ms_plain / ms_batch,
+        "tiles": [[d["opts"].tile_w, d["opts"].tile_h] for d in vb.views],
+        "error_vs_fp32_normwise": {"image_max_over_views": max(errs), "grad_table": nerr(gt32, vb.grad_table)}}
+    del vb
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_e2e(args, api, B, tree, grid, cam, g_np, res, desc, opts, dev, world, rank):
     """Same metric through the public API with host inputs: every step copies
     the octree, the table and the upstream gradient from pinned host memory
     and reads back the image and the table gradient."""
     import torch
     import torch.distributed as dist
+    from paper_2403_16862_gb300 import shard
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     hc, hl, hw = pin(tree.centers), pin(tree.levels), pin(tree.weights)
     htab, hg = pin(grid.table), pin(g_np)
@@ -368,14 +555,10 @@ def run_e2e(args, api, B, tree, grid, cam, g_np, res, desc, opts, dev, world, ra
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(args.steps):
-        step(3000 + rank * args.steps + k)
+        step(3000 + shard.view_ids(rank, world, k)[0])
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = shard.max_over_ranks(e0.elapsed_time(e1), dev)
     h2d = sum(x.numel() * x.element_size() for x in (hc, hl, hw, htab, hg))
     d2h = out_img.numel() * 4 + out_gt.numel() * 4
     return {"value": N * args.steps * world / (ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

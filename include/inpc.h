@@ -54,6 +54,18 @@ const char* inpc_version(void);
 /* Number of kernels this library has launched in this process (all devices,
  * all threads); a diagnostic for benchmarks.  Memset/memcpy are not counted. */
 uint64_t inpc_kernel_launches(void);
+/* Per-kernel device timing, a diagnostic for benchmarks and autotuning (the
+ * paper has no counterpart).  While enabled (on != 0), each kernel launch of
+ * this library that is not being captured into a CUDA graph is bracketed by
+ * two CUDA events recorded on the launch's stream; returns the previous
+ * state.  Off by default. */
+int inpc_kernel_timer_enable(int on);
+/* Waits for the recorded launches of kernel `kernel` (its function name, e.g.
+ * "k_point_grad_hash"; NULL = every kernel), stores their summed device time
+ * in *total_ms and their number in *launches, and forgets them.  Call it with
+ * no launch of this library in progress on another host thread.  Errors:
+ * INPC_ERR_INVALID_ARG (null output pointer), INPC_ERR_CUDA. */
+inpc_status inpc_kernel_timer_read(const char* kernel, double* total_ms, int64_t* launches);
 /* Copies the device status word at the start of `workspace` (any workspace
  * of this library) to *status_out after synchronising `stream`. */
 inpc_status inpc_read_device_status(const void* workspace, inpc_stream_t stream, uint32_t* status_out);

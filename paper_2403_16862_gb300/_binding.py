@@ -37,6 +37,7 @@ DECLARED = [
     "inpc_hashgrid_n_entries", "inpc_query_hashgrid", "inpc_query_hashgrid_bwd",
     "inpc_rasterize_workspace_size", "inpc_rasterize_fwd", "inpc_rasterize_bwd",
     "inpc_rasterize_bwd_hashgrid_workspace_size", "inpc_rasterize_bwd_hashgrid",
+    "inpc_kernel_timer_enable", "inpc_kernel_timer_read",
 ]
 
 
@@ -107,6 +108,8 @@ def load(path: str = LIB_PATH):
         L.inpc_rasterize_bwd_hashgrid.argtypes = [C.POINTER(InpcCamera), C.POINTER(InpcRasterOpts),
                                                   C.POINTER(InpcHashgridDesc), _P, _P, C.c_int64, _P, _P, _P, _P, _P,
                                                   _P, C.c_size_t, _P]
+        L.inpc_kernel_timer_enable.argtypes = [C.c_int]
+        L.inpc_kernel_timer_read.argtypes = [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         for name in DECLARED:
             if name not in ("inpc_last_error", "inpc_version", "inpc_kernel_launches"):
                 getattr(L, name).restype = C.c_int
@@ -129,6 +132,18 @@ def inpc_kernel_launches() -> int:
 
 
 # --------------------------------------------------- same names as the ABI ---
+def inpc_kernel_timer_enable(on: bool) -> bool:
+    return bool(load().inpc_kernel_timer_enable(1 if on else 0))
+
+
+def inpc_kernel_timer_read(kernel=None):
+    """(summed device ms, launches) of the recorded launches of `kernel`
+    (None: all kernels); the records are consumed."""
+    ms, n = C.c_double(0.0), C.c_int64(0)
+    check(load().inpc_kernel_timer_read(kernel.encode() if kernel else None, C.byref(ms), C.byref(n)))
+    return float(ms.value), int(n.value)
+
+
 def inpc_read_device_status(workspace: int, stream: int) -> int:
     out = C.c_uint32(0)
     check(load().inpc_read_device_status(workspace, stream, C.byref(out)))

@@ -1,7 +1,9 @@
 // capi.cu -- library-wide C ABI entry points: error text, version, device
 // status readback.
 #include <atomic>
+#include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -19,6 +21,54 @@ void set_last_error(const char* fmt, ...) {
   vsnprintf(buf, sizeof(buf), fmt, ap);
   va_end(ap);
   g_last_error = buf;
+}
+
+// ---------------------------------------------------------- kernel timer ---
+namespace {
+struct TimerRec {
+  const char* kernel;  // a string literal at the launch site
+  cudaEvent_t a, b;
+  bool done;           // timer_end recorded b
+};
+std::atomic<bool> g_timer_on{false};
+std::mutex g_timer_mu;
+std::vector<TimerRec> g_timer_recs;
+std::vector<cudaEvent_t> g_timer_pool;
+
+cudaEvent_t pooled_event() {
+  if (!g_timer_pool.empty()) {
+    cudaEvent_t e = g_timer_pool.back();
+    g_timer_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+}  // namespace
+
+bool timer_enabled() { return g_timer_on.load(std::memory_order_relaxed); }
+
+int timer_begin(const char* kernel, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return -1;
+  std::lock_guard<std::mutex> lk(g_timer_mu);
+  if (g_timer_recs.size() >= (1u << 20)) return -1;  // bounded: unread records are dropped
+  TimerRec r{kernel, pooled_event(), pooled_event(), false};
+  if (!r.a || !r.b || cudaEventRecord(r.a, s) != cudaSuccess) {
+    if (r.a) g_timer_pool.push_back(r.a);
+    if (r.b) g_timer_pool.push_back(r.b);
+    return -1;
+  }
+  g_timer_recs.push_back(r);
+  return (int)g_timer_recs.size() - 1;
+}
+
+void timer_end(int rec, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_timer_mu);
+  if (rec < 0 || rec >= (int)g_timer_recs.size()) return;
+  TimerRec& r = g_timer_recs[rec];
+  r.done = cudaEventRecord(r.b, s) == cudaSuccess;
 }
 
 int device_sm_count() {
@@ -51,5 +101,40 @@ extern "C" inpc_status inpc_read_device_status(const void* workspace, inpc_strea
   INPC_CUDA(cudaMemcpyAsync(&v, workspace, sizeof(v), cudaMemcpyDeviceToHost, s), "read status");
   INPC_CUDA(cudaStreamSynchronize(s), "read status sync");
   *status_out = v;
+  return INPC_OK;
+}
+
+extern "C" int inpc_kernel_timer_enable(int on) {
+  return inpc::g_timer_on.exchange(on != 0) ? 1 : 0;
+}
+
+extern "C" inpc_status inpc_kernel_timer_read(const char* kernel, double* total_ms, int64_t* launches) {
+  using namespace inpc;
+  if (!total_ms || !launches) return fail(INPC_ERR_INVALID_ARG, "inpc_kernel_timer_read: null pointer");
+  std::lock_guard<std::mutex> lk(g_timer_mu);
+  double ms_sum = 0.0;
+  int64_t count = 0;
+  std::vector<TimerRec> keep;
+  for (TimerRec& r : g_timer_recs) {
+    const bool match = !kernel || std::strcmp(kernel, r.kernel) == 0;
+    if (!match) {
+      keep.push_back(r);
+      continue;
+    }
+    if (r.done) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
+        return fail(INPC_ERR_CUDA, "inpc_kernel_timer_read: %s", cudaGetErrorString(cudaGetLastError()));
+      ms_sum += ms;
+      ++count;
+    }
+    g_timer_pool.push_back(r.a);
+    g_timer_pool.push_back(r.b);
+  }
+  // records handed out by timer_begin index this vector; read only between
+  // launches (no TimedLaunch scope open), as the header states
+  g_timer_recs.swap(keep);
+  *total_ms = ms_sum;
+  *launches = count;
   return INPC_OK;
 }

@@ -38,6 +38,34 @@ inline inpc_status check_launch(const char* what, int k = 1) {
   return INPC_OK;
 }
 
+// Per-kernel device timing (inpc_kernel_timer_enable/_read): while enabled,
+// every launch made inside a TimedLaunch scope is bracketed by two CUDA
+// events recorded on its stream.  Launches recorded into a CUDA graph are
+// not timed.  Disabled, a scope costs one relaxed atomic load.
+bool timer_enabled();
+int timer_begin(const char* kernel, cudaStream_t s);
+void timer_end(int rec, cudaStream_t s);
+
+struct TimedLaunch {
+  int rec = -1;
+  cudaStream_t s;
+  TimedLaunch(const char* kernel, cudaStream_t st) : s(st) {
+    if (timer_enabled()) rec = timer_begin(kernel, st);
+  }
+  ~TimedLaunch() {
+    if (rec >= 0) timer_end(rec, s);
+  }
+  TimedLaunch(const TimedLaunch&) = delete;
+  TimedLaunch& operator=(const TimedLaunch&) = delete;
+};
+
+// Launch statement(s) under a TimedLaunch named `kernel`.
+#define INPC_TIMED(kernel, stream, ...)               \
+  do {                                                \
+    ::inpc::TimedLaunch _timed_launch(kernel, stream); \
+    __VA_ARGS__;                                      \
+  } while (0)
+
 #define INPC_TRY(expr)                 \
   do {                                 \
     inpc_status _st = (expr);          \

@@ -143,6 +143,7 @@ extern "C" inpc_status inpc_query_hashgrid(const inpc_hashgrid_desc* g, const vo
   const dim3 grid = grid_for(n, P.n_levels, 256);
   // aligned row pairs need the table to start on a pair boundary
   const bool pairs = aligned(table, 2 * ta);
+  TimedLaunch timed("k_hash_fwd", s);
   if (g->table_dtype == INPC_F32 && g->out_dtype == INPC_F32) {
     if (pairs) k_hash_fwd<float, float, true><<<grid, 256, 0, s>>>(P, (const float*)table, pos, n, (float*)h_out);
     else k_hash_fwd<float, float, false><<<grid, 256, 0, s>>>(P, (const float*)table, pos, n, (float*)h_out);
@@ -174,6 +175,7 @@ extern "C" inpc_status inpc_query_hashgrid_bwd(const inpc_hashgrid_desc* g, cons
   if (!aligned(grad_table, 16) || !aligned(dh, 16) || !aligned(pos, 4))
     return fail(INPC_ERR_INVALID_ARG, "inpc_query_hashgrid_bwd: misaligned buffer");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  TimedLaunch timed("k_hash_bwd", s);
   k_hash_bwd<<<grid_for(n, P.n_levels, 256), 256, 0, s>>>(P, pos, dh, n, grad_table);
   return check_launch("k_hash_bwd");
 }

@@ -35,9 +35,11 @@ inline Replicas replica_plan(const GridParams& Gp, void* base) {
 
 inline size_t replica_bytes(const Replicas& r) { return (size_t)kReplicas * r.rows * 4 * sizeof(float); }
 
-__global__ void k_fold_replicas(const float4* __restrict__ rep, long long rows, float4* __restrict__ grad) {
+// Sum the replicas into the table gradient.  The add is atomic, so calls
+// for several views may accumulate into one table concurrently.
+__global__ void k_fold_replicas(const float4* __restrict__ rep, long long rows, float* __restrict__ grad) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < rows; i += (long long)gridDim.x * blockDim.x) {
-    float4 s = grad[i];
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < kReplicas; ++k) {
       const float4 v = rep[k * rows + i];
@@ -46,7 +48,7 @@ __global__ void k_fold_replicas(const float4* __restrict__ rep, long long rows, 
       s.z += v.z;
       s.w += v.w;
     }
-    grad[i] = s;
+    if (s.x != 0.f || s.y != 0.f || s.z != 0.f || s.w != 0.f) red_add_v4(grad + 4 * i, s);
   }
 }
 
@@ -122,12 +124,14 @@ inpc_status launch_point_grad_hash(const RP& P, const GridParams& Gp, const floa
   constexpr int kGroups = kThreads / GA;
   if (rep.rows > 0) INPC_CUDA(cudaMemsetAsync(rep.base, 0, replica_bytes(rep), s), "clear replicas");
   const long long grid = std::min<long long>(ceil_div(P.n, kGroups), (long long)device_sm_count() * 32);
-  k_point_grad_hash<GA, FT><<<(unsigned)std::max<long long>(grid, 1), kThreads, 0, s>>>(P, Gp, pos, feat, d_image, ws,
-                                                                                         grad_table, d_feat, rep);
+  INPC_TIMED("k_point_grad_hash", s,
+             k_point_grad_hash<GA, FT><<<(unsigned)std::max<long long>(grid, 1), kThreads, 0, s>>>(
+                 P, Gp, pos, feat, d_image, ws, grad_table, d_feat, rep));
   INPC_TRY(check_launch("k_point_grad_hash"));
   if (rep.rows > 0) {
-    k_fold_replicas<<<(unsigned)std::min<long long>(ceil_div(rep.rows, 256), device_sm_count() * 8), 256, 0, s>>>(
-        reinterpret_cast<const float4*>(rep.base), rep.rows, reinterpret_cast<float4*>(grad_table));
+    INPC_TIMED("k_fold_replicas", s,
+               k_fold_replicas<<<(unsigned)std::min<long long>(ceil_div(rep.rows, 256), device_sm_count() * 8), 256,
+                                 0, s>>>(reinterpret_cast<const float4*>(rep.base), rep.rows, grad_table));
     INPC_TRY(check_launch("k_fold_replicas"));
   }
   return INPC_OK;

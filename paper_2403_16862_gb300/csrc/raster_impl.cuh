@@ -1225,7 +1225,7 @@ inpc_status bin_fragments(const RP& P, const float* pos, const float* opacity, c
                           uint32_t cap_small, uint32_t cap_group, cudaStream_t s) {
   INPC_CUDA(cudaMemsetAsync(ws.pix_count, 0, sizeof(uint32_t) * P.n_pix, s), "clear pixel counts");
   if (P.n > 0) {
-    k_pix_count<<<point_grid(P.n), 256, 0, s>>>(P, pos, ws.pix_count);
+    INPC_TIMED("k_pix_count", s, k_pix_count<<<point_grid(P.n), 256, 0, s>>>(P, pos, ws.pix_count));
     INPC_TRY(check_launch("k_pix_count"));
   }
   INPC_TRY((scan::run<uint32_t, CountLoad, false>(CountLoad{ws.pix_count}, P.n_pix, ws.pix_start, ws.tops, s)));
@@ -1235,8 +1235,9 @@ inpc_status bin_fragments(const RP& P, const float* pos, const float* opacity, c
                                                                ws.pix_start);
   INPC_TRY(check_launch("k_classify"));
   if (P.n > 0) {
-    k_pix_scatter<FT><<<point_grid(P.n), 256, 0, s>>>(P, pos, opacity, feat, ws.pix_start, ws.pix_count, ws.keys, ws.alpha,
-                                                  ws.pslot);
+    INPC_TIMED("k_pix_scatter", s,
+               k_pix_scatter<FT><<<point_grid(P.n), 256, 0, s>>>(P, pos, opacity, feat, ws.pix_start, ws.pix_count,
+                                                                 ws.keys, ws.alpha, ws.pslot));
     INPC_TRY(check_launch("k_pix_scatter"));
   }
   return INPC_OK;
@@ -1248,12 +1249,16 @@ inpc_status launch_fwd(const RP& P, const float* pos, const float* opacity, cons
   INPC_TRY(bin_fragments(P, pos, opacity, feat, ws, 2 * GA, GA * kRegMax, s));
   static std::once_flag f2;
   set_smem(k_blend_fwd_heavy<V, GA, FT>, HeavyBuf::bytes(), f2);
-  k_blend_fwd<V, GA, FT><<<P.n_tiles, kThreads, 0, s>>>(P, feat, ws, image, T_final, n_contrib);
+  INPC_TIMED("k_blend_fwd", s,
+             k_blend_fwd<V, GA, FT><<<P.n_tiles, kThreads, 0, s>>>(P, feat, ws, image, T_final, n_contrib));
   INPC_TRY(check_launch("k_blend_fwd"));
-  k_blend_fwd_large<V, GA, FT><<<device_sm_count() * 3, kThreads, 0, s>>>(P, feat, ws, image, T_final, n_contrib);
+  INPC_TIMED("k_blend_fwd_large", s,
+             k_blend_fwd_large<V, GA, FT><<<device_sm_count() * 3, kThreads, 0, s>>>(P, feat, ws, image, T_final,
+                                                                                   n_contrib));
   INPC_TRY(check_launch("k_blend_fwd_large"));
-  k_blend_fwd_heavy<V, GA, FT><<<device_sm_count() * 4, kThreads, HeavyBuf::bytes(), s>>>(P, feat, ws, image, T_final,
-                                                                                   n_contrib);
+  INPC_TIMED("k_blend_fwd_heavy", s,
+             k_blend_fwd_heavy<V, GA, FT><<<device_sm_count() * 4, kThreads, HeavyBuf::bytes(), s>>>(
+                 P, feat, ws, image, T_final, n_contrib));
   return check_launch("k_blend_fwd_heavy");
 }
 
@@ -1262,12 +1267,14 @@ inpc_status launch_blend_bwd(const RP& P, const FT* feat, const int32_t* n_contr
                              const RasterWs& ws, cudaStream_t s) {
   static std::once_flag f2;
   set_smem(k_blend_bwd_heavy<V, GA, FT>, HeavyBuf::bytes(), f2);
-  k_blend_bwd<V, GA, FT><<<P.n_tiles, kThreads, 0, s>>>(P, feat, n_contrib, d_image, ws);
+  INPC_TIMED("k_blend_bwd", s, k_blend_bwd<V, GA, FT><<<P.n_tiles, kThreads, 0, s>>>(P, feat, n_contrib, d_image, ws));
   INPC_TRY(check_launch("k_blend_bwd"));
-  k_blend_bwd_large<V, GA, FT><<<device_sm_count() * 3, kThreads, 0, s>>>(P, feat, n_contrib, d_image, ws);
+  INPC_TIMED("k_blend_bwd_large", s,
+             k_blend_bwd_large<V, GA, FT><<<device_sm_count() * 3, kThreads, 0, s>>>(P, feat, n_contrib, d_image, ws));
   INPC_TRY(check_launch("k_blend_bwd_large"));
-  k_blend_bwd_heavy<V, GA, FT><<<device_sm_count() * 4, kThreads, HeavyBuf::bytes(), s>>>(P, feat, n_contrib, d_image,
-                                                                                           ws);
+  INPC_TIMED("k_blend_bwd_heavy", s,
+             k_blend_bwd_heavy<V, GA, FT><<<device_sm_count() * 4, kThreads, HeavyBuf::bytes(), s>>>(
+                 P, feat, n_contrib, d_image, ws));
   return check_launch("k_blend_bwd_heavy");
 }
 
@@ -1278,8 +1285,9 @@ inpc_status launch_bwd(const RP& P, const float* pos, const float* opacity, cons
   INPC_TRY((launch_blend_bwd<V, GA, FT>(P, feat, n_contrib, d_image, ws, s)));
   constexpr int kGroups = kThreads / GA;
   const long long grid = std::min<long long>(ceil_div(P.n, kGroups), (long long)device_sm_count() * 32);
-  k_point_grad<V, GA, FT><<<(unsigned)std::max<long long>(grid, 1), kThreads, 0, s>>>(P, pos, opacity, feat, d_image,
-                                                                                      ws, d_opacity, d_feat);
+  INPC_TIMED("k_point_grad", s,
+             k_point_grad<V, GA, FT><<<(unsigned)std::max<long long>(grid, 1), kThreads, 0, s>>>(
+                 P, pos, opacity, feat, d_image, ws, d_opacity, d_feat));
   return check_launch("k_point_grad");
 }
 

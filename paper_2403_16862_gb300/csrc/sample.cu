@@ -332,15 +332,17 @@ extern "C" inpc_status inpc_sample_octree(const inpc_octree* tree, uint64_t seed
   const int sl = coarse_stride_log2(L);
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   if (n_samples > 0) {
-    k_draw_count<<<(unsigned)ceil_div(n_samples, kDrawPerCta), kDrawThreads, 0, s>>>(ws.cdf, L, sl, n_samples, k0,
-                                                                                      k1, view_id, ws.counts);
+    INPC_TIMED("k_draw_count", s,
+               k_draw_count<<<(unsigned)ceil_div(n_samples, kDrawPerCta), kDrawThreads, 0, s>>>(
+                   ws.cdf, L, sl, n_samples, k0, k1, view_id, ws.counts));
     INPC_TRY(check_launch("k_draw_count"));
   }
   INPC_TRY((scan<uint32_t, CountLoad, false>(CountLoad{ws.counts}, L, ws.starts, ws.count_tops, s)));
   if (n_samples > 0) {
     const int64_t grid = std::min<int64_t>(ceil_div(n_samples, 256), (int64_t)sms * 16);
-    k_place<<<(unsigned)grid, 256, 0, s>>>(ws.starts, L, sl, n_samples, k0, k1, view_id, tree->centers,
-                                           tree->levels, tree->root_size, leaf_idx_out, pos_out);
+    INPC_TIMED("k_place", s,
+               k_place<<<(unsigned)grid, 256, 0, s>>>(ws.starts, L, sl, n_samples, k0, k1, view_id, tree->centers,
+                                                      tree->levels, tree->root_size, leaf_idx_out, pos_out));
     INPC_TRY(check_launch("k_place"));
   }
   if (leaf_counts_out)
