@@ -35,11 +35,13 @@ N_SAMPLES = 4_194_304
 LOG2_T = 19
 W, H = 1280, 832
 C = 64
+SCALE = 1  # --scale k: the profiling case (N / k^2 samples, image and focal length / k)
 
 
 def workload_config(extra=None):
-    cfg = {"workload": "INPC view fwd+bwd: 65,536-leaf octree, 4,194,304 samples, 16-level 2^19x4 FP32 hash grid, "
-                       "head mode (64 ch), 1280x832, dImage ~ N(0,1)",
+    cfg = {"workload": "INPC view fwd+bwd: 65,536-leaf octree, %s samples, 16-level 2^19x4 FP32 hash grid, "
+                       "head mode (64 ch), %dx%d, dImage ~ N(0,1)%s"
+                       % (format(N_SAMPLES, ","), W, H, "" if SCALE == 1 else " (profiling case, scale 1/%d)" % SCALE),
            "n_leaves": N_LEAVES, "n_samples": N_SAMPLES, "image": [W, H], "channels": C, "log2_T": LOG2_T,
            "l2": "flushed (256 MiB write) before every timed step; per-step working set > 1 GB"}
     if extra:
@@ -53,7 +55,8 @@ def make_scene():
     tree = scenes.make_octree(0, N_LEAVES)
     res = scenes.geometric_resolutions(16, 16, 4096)
     grid = scenes.make_hashgrid(1, api.hashgrid_n_entries(res, LOG2_T), res, LOG2_T)
-    cam = scenes.make_camera((0.5, 0.5, -1.2), 900.0, 900.0, 640.0, 416.0, W, H)
+    f = 900.0 / SCALE
+    cam = scenes.make_camera((0.5, 0.5, -1.2), f, f, W / 2.0, H / 2.0, W, H)
     g = scenes.upstream_grad(2, (H, W, C))
     return tree, res, grid, cam, g
 
@@ -221,10 +224,19 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the BF16 (16M points, 1920x1080) and batched BF16 (8 views) forms")
+    ap.add_argument("--scale", type=int, default=1,
+                    help="profiling case: N / k^2 samples, image and focal length / k (same fragments per pixel)")
     ap.add_argument("--unfused", action="store_true",
                     help="separate rasterizer backward and grid adjoint (materialises dh)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.scale != 1:
+        global SCALE, N_SAMPLES, W, H
+        k = args.scale
+        if k < 1 or W % k or H % k:
+            ap.error("--scale must divide 1280 and 832")
+        SCALE, N_SAMPLES, W, H = k, N_SAMPLES // (k * k), W // k, H // k
+        args.no_forms = True
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -367,7 +379,7 @@ def main():
             "kernels_ms": {k: round(v[0], 4) for k, v in sorted(kernel_ms.items(), key=lambda kv: -kv[1][0])},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if achieved else None,
-                         "traffic": TRAFFIC.get(dom) if not args.unfused else None,
+                         "traffic": TRAFFIC.get(dom) if not args.unfused and SCALE == 1 else None,
                          "peak_kind": peak_kind + " (copy bandwidth)", "launch_ms": dom_ms,
                          "algorithmic_bytes": dom_bytes, **atomic_ceiling(dom, N, dom_ms)},
             "step_roofline": {"algorithmic_bytes": total_bytes,
