@@ -216,7 +216,11 @@ typedef enum {
  *                 transmittance and every gradient stay FP32
  *   t_min         blending stops after the fragment that takes T below it (1e-4)
  *   alpha_max     splat opacity clamp, alpha = min(alpha_h w, alpha_max), < 1 (0.99)
- *   tile_w/tile_h screen tile in pixels, tile_w * tile_h <= 256; 0 = default 16 x 16 */
+ *   tile_w/tile_h screen tile in pixels, tile_w * tile_h <= 256; 0 = default 16 x 8
+ *                 (groups pixels into CTAs; never changes a result)
+ * Alignment: feat and image 16 bytes when n_channels % 4 == 0 (FP32) or
+ * n_channels = 64 (BF16), 8 bytes for other BF16 multiples of 4, else their
+ * element size; d_image / d_feat 16 bytes when n_channels % 4 == 0. */
 typedef struct {
   int32_t opacity_mode;
   int32_t n_channels;
@@ -250,9 +254,12 @@ inpc_status inpc_rasterize_fwd(const inpc_camera* cam, const inpc_raster_opts* o
                                int32_t* n_contrib, void* workspace, size_t workspace_bytes, inpc_stream_t stream);
 
 /* Backward of inpc_rasterize_fwd (App. A.6) for upstream d_image [H, W, F]
- * (float32).  Per pixel the blended fragments are revisited back to front,
- * recovering T_k = T_{k+1} / (1 - alpha_k) from T_final (no per-fragment
- * storage).  Writes (does not accumulate):
+ * (float32).  Per pixel, T_k is recomputed from the fragments' alphas by the
+ * forward's own front-to-back product (the same rounding, no division by
+ * 1 - alpha; nothing stored between the calls), then the blended fragments
+ * are revisited back to front with the suffix sums
+ * S_k = sum_{j>k} T_j alpha_j (c_j . g):
+ * dL/dalpha_k = T_k (c_k . g) - S_k / (1 - alpha_k).  Writes (does not accumulate):
  *   d_feat     float32 [n, F]: sum of the point's splat gradients T_k alpha_k g;
  *              in FROM_CH0 mode column 0 is d alpha_h * exp(h0) exp(-exp(h0))
  *   d_opacity  float32 [n] (GIVEN mode; may be NULL in FROM_CH0 mode):

@@ -157,7 +157,7 @@ extern "C" inpc_status inpc_rasterize_bwd(const inpc_camera* cam, const inpc_ras
     return fail(INPC_ERR_INVALID_ARG, "null pointer");
   if (!P.head && (!opacity || !d_opacity)) return fail(INPC_ERR_INVALID_ARG, "opacity and d_opacity required");
   const size_t va = P.F % 4 == 0 ? 16 : 4;
-  const size_t vf = P.F % 4 == 0 ? (P.bf16 ? 8 : 16) : (P.bf16 ? 2 : 4);
+  const size_t vf = P.F % 4 == 0 ? (P.bf16 && P.F != 64 ? 8 : 16) : (P.bf16 ? 2 : 4);
   if (!aligned(feat, vf) || !aligned(d_image, va) || !aligned(d_feat, va))
     return fail(INPC_ERR_INVALID_ARG, "feat/d_image/d_feat misaligned");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -197,7 +197,7 @@ extern "C" inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const
   if (n == 0) return INPC_OK;
   if (!pos || !feat || !T_final || !n_contrib || !d_image || !grad_table)
     return fail(INPC_ERR_INVALID_ARG, "null pointer");
-  const size_t vf = P.bf16 ? 8 : 16;
+  const size_t vf = P.bf16 && P.F != 64 ? 8 : 16;
   if (!aligned(feat, vf) || !aligned(d_image, 16) || !aligned(grad_table, 16) || (d_feat && !aligned(d_feat, 16)))
     return fail(INPC_ERR_INVALID_ARG, "feat/d_image/grad_table/d_feat misaligned");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

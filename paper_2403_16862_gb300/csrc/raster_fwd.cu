@@ -24,7 +24,7 @@ extern "C" inpc_status inpc_rasterize_fwd(const inpc_camera* cam, const inpc_ras
   if (!image || !T_final || !n_contrib) return fail(INPC_ERR_INVALID_ARG, "null output");
   if (n > 0 && (!pos || !feat)) return fail(INPC_ERR_INVALID_ARG, "null pos or feat");
   if (n > 0 && !P.head && !opacity) return fail(INPC_ERR_INVALID_ARG, "opacity required in INPC_OPACITY_GIVEN mode");
-  const size_t va = P.F % 4 == 0 ? (P.bf16 ? 8 : 16) : (P.bf16 ? 2 : 4);
+  const size_t va = P.F % 4 == 0 ? (P.bf16 && P.F != 64 ? 8 : 16) : (P.bf16 ? 2 : 4);
   if (!aligned(feat, va) || !aligned(image, va) || !aligned(pos, 4))
     return fail(INPC_ERR_INVALID_ARG, "feat/image must be %zu-byte aligned", va);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -584,10 +584,212 @@ __device__ __forceinline__ void load_sorted(const Group<GA>& G, const unsigned l
 __device__ __forceinline__ long long reg_id(unsigned long long k) { return (long long)((k >> 8) & kIdMask); }
 __device__ __forceinline__ uint32_t reg_pos(unsigned long long k) { return (uint32_t)(k & 0xFF); }
 
+// ------------------------------------------- 64 channels: fragment slots ---
+// For F = 64 on a 32-lane group the gather-reduce runs on 8 fragment slots
+// of 4 lanes: lane (slot f = lane / 4, part q = lane % 4) reads 16 channels
+// of the feature row of fragment 8p + f in pass p with 16-byte loads (4
+// FP32 chunks of 4 channels, chunk 4i + q; or 2 BF16 chunks of 8 channels),
+// so one pass moves 8 rows with 4 (FP32) or 2 (BF16) loads per lane.  The
+// forward accumulates per slot and reduce-scatters over the slots at the
+// end of the pixel (each lane then holds 2 channels); the backward's dot
+// products c_j . g are per slot sums over 16 channels plus two shuffles.
+template <class FT>
+struct Slot64;
+
+template <>
+struct Slot64<float> {
+  // channel of element e (0..15) of part q
+  __device__ static int channel(int q, int e) { return 16 * (e >> 2) + 4 * q + (e & 3); }
+  __device__ static void load(const float* __restrict__ row, int q, float (&c)[16]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(row + 4 * (4 * i + q)));
+      c[4 * i + 0] = t.x;
+      c[4 * i + 1] = t.y;
+      c[4 * i + 2] = t.z;
+      c[4 * i + 3] = t.w;
+    }
+  }
+  __device__ static void store2(float* __restrict__ row, int ch, float a, float b) {
+    __stcs(reinterpret_cast<float2*>(row + ch), make_float2(a, b));
+  }
+};
+
+template <>
+struct Slot64<__nv_bfloat16> {
+  __device__ static int channel(int q, int e) { return 32 * (e >> 3) + 8 * q + (e & 7); }
+  __device__ static void load(const __nv_bfloat16* __restrict__ row, int q, float (&c)[16]) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const uint4 raw = __ldg(reinterpret_cast<const uint4*>(row + 8 * (4 * i + q)));
+      const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        c[8 * i + 2 * k] = __uint_as_float(w[k] << 16);
+        c[8 * i + 2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+      }
+    }
+  }
+  __device__ static void store2(__nv_bfloat16* __restrict__ row, int ch, float a, float b) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    __stcs(reinterpret_cast<unsigned int*>(row + ch), *reinterpret_cast<unsigned int*>(&v));
+  }
+};
+
+// The upstream gradient (FP32) of this lane's 16 channels, in the layout of FT.
+template <class FT>
+__device__ __forceinline__ void load_grad16(const float* __restrict__ g, int q, float (&out)[16]) {
+#pragma unroll
+  for (int e = 0; e < 16; e += 4) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(g + Slot64<FT>::channel(q, e)));
+    out[e] = t.x;
+    out[e + 1] = t.y;
+    out[e + 2] = t.z;
+    out[e + 3] = t.w;
+  }
+}
+
+template <class FT, int R>
+__device__ void blend_fwd_slots(const Group<32>& G, const RP& P, const RasterWs& ws, uint32_t s0, int m,
+                                long long pix, const FT* __restrict__ feat, FT* __restrict__ image,
+                                float* __restrict__ T_final, int32_t* __restrict__ n_contrib) {
+  unsigned long long key[R];
+  load_sorted<32, R>(G, ws.keys, s0, m, key);
+  const int q = G.lg & 3, f = G.lg >> 2;
+  float acc[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) acc[e] = 0.f;
+  float T = 1.0f;
+  int cnt = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int b = r * 32;
+    if (b >= m) break;
+    const bool valid = b + G.lg < m;
+    const float a = valid ? ws.alpha[s0 + reg_pos(key[r])] : 0.f;
+    const uint32_t id = valid ? (uint32_t)reg_id(key[r]) : 0u;
+    const ChunkT<32> ct = chunk_transmittance<32>(G, P, a, valid, min(32, m - b), T);
+    const float wk = __fmul_rn(ct.Tk, a);
+#pragma unroll 2
+    for (int p = 0; p * 8 < ct.take; ++p) {
+      const int j = 8 * p + f;
+      const uint32_t idj = __shfl_sync(0xffffffffu, id, j);
+      const float wj = __shfl_sync(0xffffffffu, wk, j);
+      if (j < ct.take) {
+        float c[16];
+        Slot64<FT>::load(feat + 64ll * idj, q, c);
+        if (P.head && q == 0) c[0] = 1.0f;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = __fmaf_rn(wj, c[e], acc[e]);
+      }
+    }
+    cnt += ct.take;
+    T = G.bcast(ct.Tn, ct.take - 1);
+    if (ct.stop) break;
+  }
+  // reduce-scatter over the 8 slots (lane bits 4, 3, 2)
+  const int h4 = (G.lg >> 4) & 1, h3 = (G.lg >> 3) & 1, h2 = (G.lg >> 2) & 1;
+  float r8[8], r4[4], r2[2];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float send = h4 ? acc[k] : acc[8 + k];
+    const float keep = h4 ? acc[8 + k] : acc[k];
+    r8[k] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, 16));
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float send = h3 ? r8[k] : r8[4 + k];
+    const float keep = h3 ? r8[4 + k] : r8[k];
+    r4[k] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, 8));
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = h2 ? r4[k] : r4[2 + k];
+    const float keep = h2 ? r4[2 + k] : r4[k];
+    r2[k] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, 4));
+  }
+  const int e0 = 8 * h4 + 4 * h3 + 2 * h2;
+  Slot64<FT>::store2(image + pix * 64, Slot64<FT>::channel(q, e0), r2[0], r2[1]);
+  if (G.lg == 0) {
+    T_final[pix] = T;
+    n_contrib[pix] = cnt;
+  }
+}
+
+template <class FT, int R>
+__device__ void blend_bwd_slots(const Group<32>& G, const RP& P, const RasterWs& ws, uint32_t s0, int m, int nb,
+                                long long pix, const FT* __restrict__ feat, const float* __restrict__ d_image) {
+  unsigned long long key[R];
+  load_sorted<32, R>(G, ws.keys, s0, m, key);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int k = r * 32 + G.lg;
+    if (k >= nb && k < m) ws.fscal[s0 + reg_pos(key[r])] = make_float2(0.f, 0.f);
+  }
+  if (nb == 0) return;
+  float a[R], Tc[R];
+  float T = 1.0f;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    a[r] = 0.f;
+    Tc[r] = T;
+    const int b = r * 32;
+    if (b < nb) {
+      const bool valid = b + G.lg < nb;
+      a[r] = valid ? ws.alpha[s0 + reg_pos(key[r])] : 0.f;
+      const ChunkT<32> ct = chunk_transmittance<32>(G, P, a[r], valid, min(32, nb - b), T);
+      T = G.bcast(ct.Tn, ct.take - 1);
+    }
+  }
+  const int q = G.lg & 3, f = G.lg >> 2;
+  float g[16];
+  load_grad16<FT>(d_image + pix * 64, q, g);
+  float S = 0.f;
+#pragma unroll
+  for (int r = R - 1; r >= 0; --r) {
+    const int b = r * 32;
+    if (b >= nb) continue;
+    const bool valid = b + G.lg < nb;
+    const uint32_t id = valid ? (uint32_t)reg_id(key[r]) : 0u;
+    const ChunkT<32> ct = chunk_transmittance<32>(G, P, a[r], valid, min(32, nb - b), Tc[r]);
+    float mydot = 0.f;
+#pragma unroll 2
+    for (int p = 0; p * 8 < ct.take; ++p) {
+      const int j = 8 * p + f;
+      const uint32_t idj = __shfl_sync(0xffffffffu, id, j);
+      float part = 0.f;
+      if (j < ct.take) {
+        float c[16];
+        Slot64<FT>::load(feat + 64ll * idj, q, c);
+        if (P.head && q == 0) c[0] = 1.0f;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) part = __fmaf_rn(c[e], g[e], part);
+      }
+      part = __fadd_rn(part, __shfl_xor_sync(0xffffffffu, part, 1));
+      part = __fadd_rn(part, __shfl_xor_sync(0xffffffffu, part, 2));
+      // fragment 8p + s's dot product goes to lane 8p + s (from slot s's lane 4s)
+      const float v = __shfl_sync(0xffffffffu, part, (4 * (G.lg - 8 * p)) & 31);
+      if (G.lg >= 8 * p && G.lg < 8 * p + 8) mydot = v;
+    }
+    const bool mine = G.lg < ct.take;
+    const float wk = mine ? __fmul_rn(ct.Tk, a[r]) : 0.f;
+    const float term = __fmul_rn(wk, mydot);
+    const float suf = G.suffix_scan(term);             // this chunk, at or behind k
+    const float Sk = __fadd_rn(S, G.shift_down(suf));  // strictly behind k
+    const float da = __fsub_rn(__fmul_rn(ct.Tk, mydot), __fdiv_rn(Sk, __fsub_rn(1.0f, a[r])));
+    if (mine) ws.fscal[s0 + reg_pos(key[r])] = make_float2(wk, da);
+    S = __fadd_rn(S, G.bcast(suf, 0));
+  }
+}
+
 template <int V, int GA, class FT, int R>
 __device__ void blend_fwd_reg(const Group<GA>& G, const RP& P, const RasterWs& ws, uint32_t s0, int m, long long pix,
                               const FT* __restrict__ feat, FT* __restrict__ image, float* __restrict__ T_final,
                               int32_t* __restrict__ n_contrib) {
+  if constexpr (V == 2 && GA == 32) {  // F = 64
+    blend_fwd_slots<FT, R>(G, P, ws, s0, m, pix, feat, image, T_final, n_contrib);
+    return;
+  }
   unsigned long long key[R];
   load_sorted<GA, R>(G, ws.keys, s0, m, key);
   const int ch = G.lg * V;
@@ -648,7 +850,7 @@ __device__ __forceinline__ void pixel_batch(const Group<GA>& G, const RP& P, con
 // Tile-order kernel for small buckets (at most 2 registers per lane): high
 // occupancy, the offsets of GA pixels fetched with one load per lane.
 template <int V, int GA, class FT>
-__global__ void __launch_bounds__(kThreads, 6) k_blend_fwd(RP P, const FT* __restrict__ feat, RasterWs ws,
+__global__ void __launch_bounds__(kThreads, 4) k_blend_fwd(RP P, const FT* __restrict__ feat, RasterWs ws,
                                                          FT* __restrict__ image, float* __restrict__ T_final,
                                                          int32_t* __restrict__ n_contrib) {
   constexpr int kGroups = kThreads / GA;
@@ -698,6 +900,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_fwd_large(RP P, const FT*
 template <int V, int GA, class FT, int R>
 __device__ void blend_bwd_reg(const Group<GA>& G, const RP& P, const RasterWs& ws, uint32_t s0, int m, int nb,
                               long long pix, const FT* __restrict__ feat, const float* __restrict__ d_image) {
+  if constexpr (V == 2 && GA == 32) {  // F = 64
+    blend_bwd_slots<FT, R>(G, P, ws, s0, m, nb, pix, feat, d_image);
+    return;
+  }
   unsigned long long key[R];
   load_sorted<GA, R>(G, ws.keys, s0, m, key);
 #pragma unroll
@@ -760,7 +966,7 @@ __device__ void blend_bwd_reg(const Group<GA>& G, const RP& P, const RasterWs& w
 }
 
 template <int V, int GA, class FT>
-__global__ void __launch_bounds__(kThreads, 6) k_blend_bwd(RP P, const FT* __restrict__ feat,
+__global__ void __launch_bounds__(kThreads, 4) k_blend_bwd(RP P, const FT* __restrict__ feat,
                                                          const int32_t* __restrict__ n_contrib,
                                                          const float* __restrict__ d_image, RasterWs ws) {
   constexpr int kGroups = kThreads / GA;
