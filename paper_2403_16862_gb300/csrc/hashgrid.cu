@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(256) k_hash_fwd(GridParams P, const TT* __rest
   const int l0 = blockIdx.y * kLevelGroup;
   const int gl = min(kLevelGroup, P.n_levels - l0);
   const long long total = n * gl;
+  const uint64_t keep = l2_evict_last();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const long long p = i / gl;
@@ -53,15 +54,15 @@ __global__ void __launch_bounds__(256) k_hash_fwd(GridParams P, const TT* __rest
       const uint32_t r1 = vertex_row(P, l, cx + 1, cy + by, cz + bz);
       float4 t0, t1;
       if (kPairs && (r0 ^ r1) == 1u) {
-        load_row_pair<TT>(tab, r0 & ~1u, t0, t1);
+        load_row_pair<TT>(tab, r0 & ~1u, t0, t1, keep);
         if (r0 & 1u) {
           const float4 tmp = t0;
           t0 = t1;
           t1 = tmp;
         }
       } else {
-        t0 = load_row<TT>(tab, r0);
-        t1 = load_row<TT>(tab, r1);
+        t0 = load_row<TT>(tab, r0, keep);
+        t1 = load_row<TT>(tab, r1, keep);
       }
       const float wyz = gy[by] * gz[bz];
       const float w0 = gx[0] * wyz, w1 = gx[1] * wyz;

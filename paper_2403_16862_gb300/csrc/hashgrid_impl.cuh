@@ -82,6 +82,19 @@ __device__ __forceinline__ uint32_t vertex_row(const GridParams& P, int l, uint3
   return (x ^ (y * 2654435761u) ^ (z * 805459861u)) & P.hash_mask;
 }
 
+// L2 eviction priorities: the table gradient (and the table in the query)
+// is kept with evict_last while data read once streams through with
+// evict_first, so the rows that receive reductions or gathers stay resident.
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
 template <class TT>
 __device__ __forceinline__ float4 load_row(const TT* __restrict__ table, long long row);
 
@@ -128,6 +141,54 @@ __device__ __forceinline__ void load_row_pair<__nv_bfloat16>(const __nv_bfloat16
   b.w = __uint_as_float(raw.w & 0xFFFF0000u);
 }
 
+// The same loads with an L2 eviction-priority policy.
+template <class TT>
+__device__ __forceinline__ float4 load_row(const TT* __restrict__ table, long long row, uint64_t pol);
+
+template <>
+__device__ __forceinline__ float4 load_row<float>(const float* __restrict__ table, long long row, uint64_t pol) {
+  float4 r;
+  asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+               : "l"(table + 4 * row), "l"(pol));
+  return r;
+}
+
+template <>
+__device__ __forceinline__ float4 load_row<__nv_bfloat16>(const __nv_bfloat16* __restrict__ table, long long row,
+                                                          uint64_t pol) {
+  uint32_t x, y;
+  asm("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(x), "=r"(y)
+               : "l"(table + 4 * row), "l"(pol));
+  return make_float4(__uint_as_float(x << 16), __uint_as_float(x & 0xFFFF0000u), __uint_as_float(y << 16),
+                     __uint_as_float(y & 0xFFFF0000u));
+}
+
+template <class TT>
+__device__ __forceinline__ void load_row_pair(const TT* __restrict__ table, uint32_t even_row, float4& a, float4& b,
+                                              uint64_t pol);
+
+template <>
+__device__ __forceinline__ void load_row_pair<float>(const float* __restrict__ table, uint32_t even_row, float4& a,
+                                                     float4& b, uint64_t pol) {
+  asm("ld.global.nc.L2::cache_hint.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+               : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+               : "l"(table + 4ull * even_row), "l"(pol));
+}
+
+template <>
+__device__ __forceinline__ void load_row_pair<__nv_bfloat16>(const __nv_bfloat16* __restrict__ table,
+                                                             uint32_t even_row, float4& a, float4& b, uint64_t pol) {
+  uint32_t w[4];
+  asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+               : "l"(table + 4ull * even_row), "l"(pol));
+  a = make_float4(__uint_as_float(w[0] << 16), __uint_as_float(w[0] & 0xFFFF0000u), __uint_as_float(w[1] << 16),
+                  __uint_as_float(w[1] & 0xFFFF0000u));
+  b = make_float4(__uint_as_float(w[2] << 16), __uint_as_float(w[2] & 0xFFFF0000u), __uint_as_float(w[3] << 16),
+                  __uint_as_float(w[3] & 0xFFFF0000u));
+}
+
 template <class OT>
 __device__ __forceinline__ void store_out(OT* __restrict__ out, long long idx4, float4 v);
 
@@ -149,6 +210,25 @@ __device__ __forceinline__ void store_out<__nv_bfloat16>(__nv_bfloat16* __restri
 __device__ __forceinline__ void red_add_v4(float* addr, float4 v) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
                : "memory");
+}
+
+__device__ __forceinline__ void red_add_v4(float* addr, float4 v, uint64_t pol) {
+  asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(addr), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ uint4 ld_hint_u4(const void* p, uint64_t pol) {
+  uint4 r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ float2 ld_hint_f2(const void* p, uint64_t pol) {
+  float2 r;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(r.x), "=f"(r.y)
+               : "l"(p), "l"(pol));
+  return r;
 }
 
 }  // namespace

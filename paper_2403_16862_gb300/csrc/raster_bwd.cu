@@ -64,8 +64,9 @@ __global__ void __launch_bounds__(kThreads) k_point_grad_hash(RP P, GridParams G
   const int ch = 4 * l;
   const bool active = l < Gp.n_levels;
   const long long g0 = (long long)blockIdx.x * kGroups + threadIdx.x / GA;
+  const uint64_t keep = l2_evict_last(), stream = l2_evict_first();
   for (long long id = g0; id < P.n; id += (long long)gridDim.x * kGroups) {
-    const uint4 sl = __ldg(reinterpret_cast<const uint4*>(ws.pslot) + id);
+    const uint4 sl = ld_hint_u4(reinterpret_cast<const uint4*>(ws.pslot) + id, stream);
     const uint32_t slots[4] = {sl.x, sl.y, sl.z, sl.w};
     float dc[4] = {0.f, 0.f, 0.f, 0.f};
     if ((sl.x & sl.y & sl.z & sl.w) != kNoSlot) {
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(kThreads) k_point_grad_hash(RP P, GridParams G
       const float ah = point_alpha_h(P, nullptr, feat, id, &e_h0);
       float2 sc[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) sc[k] = slots[k] == kNoSlot ? make_float2(0.f, 0.f) : __ldg(ws.fscal + slots[k]);
+      for (int k = 0; k < 4; ++k) sc[k] = slots[k] == kNoSlot ? make_float2(0.f, 0.f) : ld_hint_f2(ws.fscal + slots[k], stream);
       float dah = 0.f;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kThreads) k_point_grad_hash(RP P, GridParams G
       const int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
       const float w = gx[bx] * gy[by] * gz[bz];
       const uint32_t row = vertex_row(Gp, l, cx + bx, cy + by, cz + bz);
-      red_add_v4(gl + 4ull * row, make_float4(w * dc[0], w * dc[1], w * dc[2], w * dc[3]));
+      red_add_v4(gl + 4ull * row, make_float4(w * dc[0], w * dc[1], w * dc[2], w * dc[3]), keep);
     }
   }
 }

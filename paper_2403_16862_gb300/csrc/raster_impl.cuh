@@ -75,6 +75,7 @@ struct RasterWs {
   uint32_t* va;
   unsigned long long* kb;    // [4n] global-sort scratch, then per-fragment (T_k, c_k . g)
   uint32_t* vb;
+  uint2* order;              // [4n] per pixel, the blended prefix in blending order: (bucket position, point)
   size_t bytes;
 };
 
@@ -98,6 +99,7 @@ RasterWs carve(void* base, long long n_pix, long long n) {
   w.va = c.take<uint32_t>(nf);
   w.kb = c.take<unsigned long long>(nf);
   w.vb = c.take<uint32_t>(nf);
+  w.order = c.take<uint2>(nf);
   w.bytes = c.bytes();
   return w;
 }
@@ -220,6 +222,34 @@ __global__ void k_classify(const uint32_t* __restrict__ pix_start, long long n_p
   const uint32_t m = end - pix_start[q];
   if (m > cap_large) heavy[atomicAdd(heavy_count, 1u)] = (uint32_t)q;
   else if (m > cap_small) large[atomicAdd(large_count, 1u)] = (uint32_t)q;
+}
+
+// Backward classes by blended count (the forward's n_contrib, clamped to the
+// bucket): the tile kernel takes nb <= cap_small, the list kernels the rest.
+__global__ void k_classify_bwd(const int32_t* __restrict__ n_contrib, const uint32_t* __restrict__ pix_start,
+                               long long n_pix, uint32_t cap_small, uint32_t cap_large, uint32_t* __restrict__ heavy,
+                               uint32_t* heavy_count, uint32_t* __restrict__ large, uint32_t* large_count) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= n_pix) return;
+  const int c = n_contrib[q];
+  const uint32_t m = pix_start[q + 1] - pix_start[q];
+  const uint32_t nb = c < 0 ? 0u : min((uint32_t)c, m);
+  if (nb > cap_large) heavy[atomicAdd(heavy_count, 1u)] = (uint32_t)q;
+  else if (nb > cap_small) large[atomicAdd(large_count, 1u)] = (uint32_t)q;
+}
+
+__device__ __forceinline__ int blended_count(const int32_t* __restrict__ n_contrib, long long q, int m) {
+  const int c = n_contrib[q];
+  return c < 0 ? 0 : min(c, m);
+}
+
+// Entry k of a pixel's blended prefix; an entry the forward did not write
+// (only reachable with a mismatched n_contrib) is clamped into the bucket.
+__device__ __forceinline__ uint2 order_at(const RP& P, const RasterWs& ws, uint32_t s0, int m, int k) {
+  uint2 o = ws.order[s0 + k];
+  if (o.x >= (uint32_t)m) o.x = 0;
+  if ((long long)o.y >= P.n) o.y = 0;
+  return o;
 }
 
 // ------------------------------------------------------------- ordering ---
@@ -670,6 +700,7 @@ __device__ void blend_fwd_slots(const Group<32>& G, const RP& P, const RasterWs&
     const uint32_t id = valid ? (uint32_t)reg_id(key[r]) : 0u;
     const ChunkT<32> ct = chunk_transmittance<32>(G, P, a, valid, min(32, m - b), T);
     const float wk = __fmul_rn(ct.Tk, a);
+    if (G.lg < ct.take) ws.order[s0 + b + G.lg] = make_uint2(reg_pos(key[r]), id);
 #pragma unroll 2
     for (int p = 0; p * 8 < ct.take; ++p) {
       const int j = 8 * p + f;
@@ -719,24 +750,25 @@ __device__ void blend_fwd_slots(const Group<32>& G, const RP& P, const RasterWs&
 template <class FT, int R>
 __device__ void blend_bwd_slots(const Group<32>& G, const RP& P, const RasterWs& ws, uint32_t s0, int m, int nb,
                                 long long pix, const FT* __restrict__ feat, const float* __restrict__ d_image) {
-  unsigned long long key[R];
-  load_sorted<32, R>(G, ws.keys, s0, m, key);
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int k = r * 32 + G.lg;
-    if (k >= nb && k < m) ws.fscal[s0 + reg_pos(key[r])] = make_float2(0.f, 0.f);
-  }
   if (nb == 0) return;
+  uint32_t slot[R], idr[R];
   float a[R], Tc[R];
   float T = 1.0f;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     a[r] = 0.f;
     Tc[r] = T;
+    slot[r] = 0;
+    idr[r] = 0;
     const int b = r * 32;
     if (b < nb) {
       const bool valid = b + G.lg < nb;
-      a[r] = valid ? ws.alpha[s0 + reg_pos(key[r])] : 0.f;
+      if (valid) {
+        const uint2 o = order_at(P, ws, s0, m, b + G.lg);
+        slot[r] = o.x;
+        idr[r] = o.y;
+        a[r] = ws.alpha[s0 + o.x];
+      }
       const ChunkT<32> ct = chunk_transmittance<32>(G, P, a[r], valid, min(32, nb - b), T);
       T = G.bcast(ct.Tn, ct.take - 1);
     }
@@ -750,7 +782,7 @@ __device__ void blend_bwd_slots(const Group<32>& G, const RP& P, const RasterWs&
     const int b = r * 32;
     if (b >= nb) continue;
     const bool valid = b + G.lg < nb;
-    const uint32_t id = valid ? (uint32_t)reg_id(key[r]) : 0u;
+    const uint32_t id = idr[r];
     const ChunkT<32> ct = chunk_transmittance<32>(G, P, a[r], valid, min(32, nb - b), Tc[r]);
     float mydot = 0.f;
 #pragma unroll 2
@@ -777,7 +809,7 @@ __device__ void blend_bwd_slots(const Group<32>& G, const RP& P, const RasterWs&
     const float suf = G.suffix_scan(term);             // this chunk, at or behind k
     const float Sk = __fadd_rn(S, G.shift_down(suf));  // strictly behind k
     const float da = __fsub_rn(__fmul_rn(ct.Tk, mydot), __fdiv_rn(Sk, __fsub_rn(1.0f, a[r])));
-    if (mine) ws.fscal[s0 + reg_pos(key[r])] = make_float2(wk, da);
+    if (mine) ws.fscal[s0 + slot[r]] = make_float2(wk, da);
     S = __fadd_rn(S, G.bcast(suf, 0));
   }
 }
@@ -807,6 +839,7 @@ __device__ void blend_fwd_reg(const Group<GA>& G, const RP& P, const RasterWs& w
     const long long id = valid ? reg_id(key[r]) : 0;
     const ChunkT<GA> ct = chunk_transmittance<GA>(G, P, a, valid, min(GA, m - b), T);
     const float wk = __fmul_rn(ct.Tk, a);
+    if (G.lg < ct.take) ws.order[s0 + b + G.lg] = make_uint2(reg_pos(key[r]), (uint32_t)id);
 #pragma unroll 8
     for (int j = 0; j < ct.take; ++j) {
       const long long idj = G.bcast(id, j);
@@ -904,25 +937,26 @@ __device__ void blend_bwd_reg(const Group<GA>& G, const RP& P, const RasterWs& w
     blend_bwd_slots<FT, R>(G, P, ws, s0, m, nb, pix, feat, d_image);
     return;
   }
-  unsigned long long key[R];
-  load_sorted<GA, R>(G, ws.keys, s0, m, key);
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int k = r * GA + G.lg;
-    if (k >= nb && k < m) ws.fscal[s0 + reg_pos(key[r])] = make_float2(0.f, 0.f);
-  }
   if (nb == 0) return;
   const int ch = G.lg * V;
+  uint32_t slot[R], idr[R];
   float a[R], Tc[R];
   float T = 1.0f;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     a[r] = 0.f;
     Tc[r] = T;
+    slot[r] = 0;
+    idr[r] = 0;
     const int b = r * GA;
     if (b < nb) {
       const bool valid = b + G.lg < nb;
-      a[r] = valid ? ws.alpha[s0 + reg_pos(key[r])] : 0.f;
+      if (valid) {
+        const uint2 o = order_at(P, ws, s0, m, b + G.lg);
+        slot[r] = o.x;
+        idr[r] = o.y;
+        a[r] = ws.alpha[s0 + o.x];
+      }
       const ChunkT<GA> ct = chunk_transmittance<GA>(G, P, a[r], valid, min(GA, nb - b), T);
       T = G.bcast(ct.Tn, ct.take - 1);
     }
@@ -938,7 +972,7 @@ __device__ void blend_bwd_reg(const Group<GA>& G, const RP& P, const RasterWs& w
     const int b = r * GA;
     if (b >= nb) continue;
     const bool valid = b + G.lg < nb;
-    const long long id = valid ? reg_id(key[r]) : 0;
+    const long long id = idr[r];
     const ChunkT<GA> ct = chunk_transmittance<GA>(G, P, a[r], valid, min(GA, nb - b), Tc[r]);
     float mydot = 0.f;
 #pragma unroll 2
@@ -960,7 +994,7 @@ __device__ void blend_bwd_reg(const Group<GA>& G, const RP& P, const RasterWs& w
     const float suf = G.suffix_scan(term);             // this chunk, at or behind k
     const float Sk = __fadd_rn(S, G.shift_down(suf));  // strictly behind k
     const float da = __fsub_rn(__fmul_rn(ct.Tk, mydot), __fdiv_rn(Sk, __fsub_rn(1.0f, a[r])));
-    if (mine) ws.fscal[s0 + reg_pos(key[r])] = make_float2(wk, da);
+    if (mine) ws.fscal[s0 + slot[r]] = make_float2(wk, da);
     S = __fadd_rn(S, G.bcast(suf, 0));
   }
 }
@@ -980,14 +1014,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_bwd(RP P, const FT* __res
     int ml;
     long long ql;
     pixel_batch<GA>(G, P, ws, tx, ty, b + G.lg * kGroups, s0l, ml, ql);
-    const int nbl = ml > 0 ? min(ml, (int)n_contrib[ql]) : 0;
+    const int nbl = ml > 0 ? blended_count(n_contrib, ql, ml) : 0;
     for (int j = 0; j < GA && b + j * kGroups < npix; ++j) {
+      const int nb = G.bcast(nbl, j);
+      if (nb <= 0 || nb > 2 * GA) continue;  // nothing blended, or another class
       const int m = G.bcast(ml, j);
-      if (m <= 0 || m > 2 * GA) continue;
       const uint32_t s0 = G.bcast(s0l, j);
       const long long q = G.bcast(ql, j);
-      const int nb = G.bcast(nbl, j);
-      if (m <= GA) blend_bwd_reg<V, GA, FT, 1>(G, P, ws, s0, m, nb, q, feat, d_image);
+      if (nb <= GA) blend_bwd_reg<V, GA, FT, 1>(G, P, ws, s0, m, nb, q, feat, d_image);
       else blend_bwd_reg<V, GA, FT, 2>(G, P, ws, s0, m, nb, q, feat, d_image);
     }
   }
@@ -1004,8 +1038,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_bwd_large(RP P, const FT*
     const long long q = ws.large[h];
     const uint32_t s0 = ws.pix_start[q];
     const int m = (int)(ws.pix_start[q + 1] - s0);
-    const int nb = min(m, (int)n_contrib[q]);
-    if (m <= 4 * GA) blend_bwd_reg<V, GA, FT, 4>(G, P, ws, s0, m, nb, q, feat, d_image);
+    const int nb = blended_count(n_contrib, q, m);
+    if (nb <= 4 * GA) blend_bwd_reg<V, GA, FT, 4>(G, P, ws, s0, m, nb, q, feat, d_image);
     else blend_bwd_reg<V, GA, FT, kRegMax>(G, P, ws, s0, m, nb, q, feat, d_image);
   }
 }
@@ -1226,6 +1260,8 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const FT* __
       auto key_at = [&](int k) { return B.K[B.idx[k]]; };
       auto alpha_at = [&](int k) { return B.A[B.idx[k]]; };
       const int n = cta_transmittance(P, alpha_at, m, [&](int k, float v) { B.Tk[k] = v; }, H, &T);
+      for (int k = threadIdx.x; k < n; k += kThreads)
+        ws.order[s0 + k] = make_uint2(B.idx[k], (uint32_t)(B.K[B.idx[k]] & kIdMask));
       __syncthreads();
       blend_fwd_cta<V, GA, FT>(P, key_at, alpha_at, [&](int k) { return B.Tk[k]; }, n, T, q, feat, image, T_final,
                            n_contrib, H);
@@ -1236,6 +1272,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const FT* __
       auto key_at = [&](int k) { return ka[k]; };
       auto alpha_at = [&](int k) { return ws.alpha[s0 + va[k]]; };
       const int n = cta_transmittance(P, alpha_at, m, [&](int k, float v) { tmp[k].x = v; }, H, &T);
+      for (int k = threadIdx.x; k < n; k += kThreads) ws.order[s0 + k] = make_uint2(va[k], (uint32_t)(ka[k] & kIdMask));
       __syncthreads();
       blend_fwd_cta<V, GA, FT>(P, key_at, alpha_at, [&](int k) { return tmp[k].x; }, n, T, q, feat, image, T_final,
                            n_contrib, H);
@@ -1244,40 +1281,45 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const FT* __
   }
 }
 
+// Backward of the pixels with more than kRegMax * GA blended fragments: the
+// whole CTA on one pixel, over the blended prefix the forward recorded (no
+// sort); T_k and c_k . g in shared memory (or, beyond kHeavyKeys, in the
+// global scratch kb).
+struct HeavyBwdBuf {
+  float* Tk;
+  float* D;
+  __device__ explicit HeavyBwdBuf(unsigned char* dyn) {
+    Tk = reinterpret_cast<float*>(dyn);
+    D = Tk + kHeavyKeys;
+  }
+  static constexpr size_t bytes() { return (size_t)kHeavyKeys * 8; }
+};
+
 template <int V, int GA, class FT>
 __global__ void __launch_bounds__(kThreads) k_blend_bwd_heavy(RP P, const FT* __restrict__ feat,
                                                                const int32_t* __restrict__ n_contrib,
                                                                const float* __restrict__ d_image, RasterWs ws) {
   extern __shared__ __align__(16) unsigned char dyn[];
-  __shared__ SortSmem S;
   __shared__ HeavySmem H;
-  const HeavyBuf B(dyn);
+  const HeavyBwdBuf B(dyn);
   const uint32_t n_heavy = *ws.heavy_count;
   for (uint32_t h = blockIdx.x; h < n_heavy; h += gridDim.x) {
     const long long q = ws.heavy[h];
     const uint32_t s0 = ws.pix_start[q];
     const int m = (int)(ws.pix_start[q + 1] - s0);
-    const int nb = min(m, (int)n_contrib[q]);
-    cta_order_bucket(ws, s0, m, B, S);
+    const int nb = blended_count(n_contrib, q, m);
+    auto key_at = [&](int k) { return (unsigned long long)order_at(P, ws, s0, m, k).y; };
+    auto alpha_at = [&](int k) { return ws.alpha[s0 + order_at(P, ws, s0, m, k).x]; };
+    auto slot_at = [&](int k) { return s0 + order_at(P, ws, s0, m, k).x; };
     float T;
-    if (m <= kHeavyKeys) {
-      auto key_at = [&](int k) { return B.K[B.idx[k]]; };
-      auto alpha_at = [&](int k) { return B.A[B.idx[k]]; };
-      auto slot_at = [&](int k) { return s0 + B.idx[k]; };
-      for (int k = nb + (int)threadIdx.x; k < m; k += kThreads) ws.fscal[slot_at(k)] = make_float2(0.f, 0.f);
+    if (nb <= kHeavyKeys) {
       cta_transmittance(P, alpha_at, nb, [&](int k, float v) { B.Tk[k] = v; }, H, &T);
       __syncthreads();
       blend_bwd_cta<V, GA, FT>(P, key_at, alpha_at, slot_at, [&](int k) { return B.Tk[k]; },
                            [&](int k, float v) { B.D[k] = v; }, [&](int k) { return B.D[k]; }, nb, q, feat, d_image,
                            ws.fscal, H);
     } else {
-      const unsigned long long* ka = ws.ka + s0;
-      const uint32_t* va = ws.va + s0;
       float2* tmp = reinterpret_cast<float2*>(ws.kb + s0);
-      auto key_at = [&](int k) { return ka[k]; };
-      auto alpha_at = [&](int k) { return ws.alpha[s0 + va[k]]; };
-      auto slot_at = [&](int k) { return s0 + va[k]; };
-      for (int k = nb + (int)threadIdx.x; k < m; k += kThreads) ws.fscal[slot_at(k)] = make_float2(0.f, 0.f);
       cta_transmittance(P, alpha_at, nb, [&](int k, float v) { tmp[k].x = v; }, H, &T);
       __syncthreads();
       blend_bwd_cta<V, GA, FT>(P, key_at, alpha_at, slot_at, [&](int k) { return tmp[k].x; },
@@ -1471,15 +1513,21 @@ inpc_status launch_fwd(const RP& P, const float* pos, const float* opacity, cons
 template <int V, int GA, class FT>
 inpc_status launch_blend_bwd(const RP& P, const FT* feat, const int32_t* n_contrib, const float* d_image,
                              const RasterWs& ws, cudaStream_t s) {
-  static std::once_flag f2;
-  set_smem(k_blend_bwd_heavy<V, GA, FT>, HeavyBuf::bytes(), f2);
+  // fragments that were not blended keep zero scalars
+  INPC_CUDA(cudaMemsetAsync(ws.fscal, 0, sizeof(float2) * std::max<long long>(4 * P.n, 1), s), "clear fscal");
+  INPC_CUDA(cudaMemsetAsync(ws.heavy_count, 0, 2 * sizeof(uint32_t), s), "clear class counts");
+  INPC_TIMED("k_classify_bwd", s,
+             k_classify_bwd<<<(unsigned)ceil_div(P.n_pix, 256), 256, 0, s>>>(
+                 n_contrib, ws.pix_start, P.n_pix, 2 * GA, GA * kRegMax, ws.heavy, ws.heavy_count, ws.large,
+                 ws.large_count));
+  INPC_TRY(check_launch("k_classify_bwd"));
   INPC_TIMED("k_blend_bwd", s, k_blend_bwd<V, GA, FT><<<P.n_tiles, kThreads, 0, s>>>(P, feat, n_contrib, d_image, ws));
   INPC_TRY(check_launch("k_blend_bwd"));
   INPC_TIMED("k_blend_bwd_large", s,
              k_blend_bwd_large<V, GA, FT><<<device_sm_count() * 3, kThreads, 0, s>>>(P, feat, n_contrib, d_image, ws));
   INPC_TRY(check_launch("k_blend_bwd_large"));
   INPC_TIMED("k_blend_bwd_heavy", s,
-             k_blend_bwd_heavy<V, GA, FT><<<device_sm_count() * 4, kThreads, HeavyBuf::bytes(), s>>>(
+             k_blend_bwd_heavy<V, GA, FT><<<device_sm_count() * 4, kThreads, HeavyBwdBuf::bytes(), s>>>(
                  P, feat, n_contrib, d_image, ws));
   return check_launch("k_blend_bwd_heavy");
 }
