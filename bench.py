@@ -81,7 +81,7 @@ KERNELS = ["k_draw_count", "k_place", "k_hash_fwd", "k_pix_count", "k_pix_scatte
 
 # DRAM bytes per launch of the dominant kernel on the full workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); see profiles/.
-TRAFFIC = {"k_point_grad_hash": 2.358428e9 + 1.331076e9}
+TRAFFIC = {"k_point_grad_hash": 2.45e9 + 0.68856e9}
 
 
 def kernel_bytes(kernel, n, n_entries, n_frag, n_pix):

@@ -1214,16 +1214,117 @@ struct HeavyBuf {
   float* A;
   uint16_t* idx;
   float* Tk;
-  float* D;
+  uint32_t* pos;  // bucket position of a selected candidate
   __device__ explicit HeavyBuf(unsigned char* dyn) {
     K = reinterpret_cast<unsigned long long*>(dyn);
     A = reinterpret_cast<float*>(K + kHeavyKeys);
     Tk = A + kHeavyKeys;
-    D = Tk + kHeavyKeys;
-    idx = reinterpret_cast<uint16_t*>(D + kHeavyKeys);
+    pos = reinterpret_cast<uint32_t*>(Tk + kHeavyKeys);
+    idx = reinterpret_cast<uint16_t*>(pos + kHeavyKeys);
   }
   static constexpr size_t bytes() { return (size_t)kHeavyKeys * (8 + 4 + 4 + 4 + 2); }
 };
+
+// Front selection for the forward CTA path.  Blending stops once T drops
+// below t_min, which on these buckets takes well under kSelectWant
+// fragments, so only the front of a large bucket needs ordering: a
+// 256-bin histogram of the FP32 depth bits (range [min, max] of the bucket,
+// bins of 2^shift, monotone in depth) gives the smallest bin b* whose
+// cumulative count reaches kSelectWant; every key in bins <= b* is nearer
+// than every key above, so those C candidates are an exact prefix of the
+// order.  They are sorted in shared memory.  Returns C, or 0 when the
+// prefix does not fit (C > kHeavyKeys); the caller blends the candidates
+// and falls back to the full sort when they do not reach t_min.
+constexpr int kSelectWant = 256;
+
+struct SelSmem {
+  uint32_t dmin, dmax;
+  int bstar, count, fill;
+};
+
+__device__ int cta_select_front(const RasterWs& ws, uint32_t s0, int m, const HeavyBuf& B, SortSmem& S,
+                                SelSmem& X) {
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    X.dmin = 0xFFFFFFFFu;
+    X.dmax = 0u;
+    X.fill = 0;
+  }
+  // the sweeps load kUnroll keys per thread before using them, so that the
+  // loads of a sweep are in flight together
+  constexpr int kUnroll = 8;
+  uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+  for (int i0 = threadIdx.x; i0 < m; i0 += kUnroll * kThreads) {
+    uint32_t d[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = i0 + u * kThreads;
+      d[u] = i < m ? (uint32_t)(__ldg(ws.keys + s0 + i) >> kIdBits) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+      if (i0 + u * kThreads < m) {
+        lo = min(lo, d[u]);
+        hi = max(hi, d[u]);
+      }
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  __syncthreads();
+  if (lane == 0) {
+    atomicMin(&X.dmin, lo);
+    atomicMax(&X.dmax, hi);
+  }
+  S.hist[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t dmin = X.dmin, span = X.dmax - X.dmin;
+  int shift = 0;
+  while ((span >> shift) > 255u) ++shift;
+  for (int i0 = threadIdx.x; i0 < m; i0 += kUnroll * kThreads) {
+    uint32_t d[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = i0 + u * kThreads;
+      d[u] = i < m ? (uint32_t)(__ldg(ws.keys + s0 + i) >> kIdBits) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+      if (i0 + u * kThreads < m) atomicAdd(&S.hist[(d[u] - dmin) >> shift], 1u);
+  }
+  __syncthreads();
+  const uint32_t h = S.hist[threadIdx.x];
+  const uint32_t ex = cta_excl_scan256(h, S.warp_sums);  // bins below this thread's bin
+  if (ex < (uint32_t)kSelectWant && ex + h >= (uint32_t)kSelectWant) {
+    X.bstar = threadIdx.x;
+    X.count = (int)(ex + h);
+  }
+  __syncthreads();
+  const int C = X.count;
+  const uint32_t bstar = (uint32_t)X.bstar;
+  if (C > kHeavyKeys) return 0;
+  for (int i0 = threadIdx.x; i0 < m; i0 += kUnroll * kThreads) {
+    unsigned long long key[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = i0 + u * kThreads;
+      key[u] = i < m ? __ldg(ws.keys + s0 + i) : ~0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = i0 + u * kThreads;
+      if (i < m && (((uint32_t)(key[u] >> kIdBits) - dmin) >> shift) <= bstar) {
+        const int slot = atomicAdd(&X.fill, 1);
+        B.K[slot] = key[u];
+        B.A[slot] = ws.alpha[s0 + i];
+        B.pos[slot] = (uint32_t)i;
+        B.idx[slot] = (uint16_t)slot;
+      }
+    }
+  }
+  __syncthreads();
+  bitonic_sort_idx(B.K, B.idx, C, threadIdx.x, kThreads, [] { __syncthreads(); });
+  return C;
+}
 
 // Sort one large bucket: in shared memory (m <= kHeavyKeys) through the
 // index array, or in global memory (ka/va) beyond that.
@@ -1232,6 +1333,7 @@ __device__ void cta_order_bucket(const RasterWs& ws, uint32_t s0, int m, const H
     for (int j = threadIdx.x; j < m; j += kThreads) {
       B.K[j] = ws.keys[s0 + j];
       B.A[j] = ws.alpha[s0 + j];
+      B.pos[j] = (uint32_t)j;
       B.idx[j] = (uint16_t)j;
     }
     __syncthreads();
@@ -1248,20 +1350,39 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const FT* __
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ SortSmem S;
   __shared__ HeavySmem H;
+  __shared__ SelSmem X;
   const HeavyBuf B(dyn);
   const uint32_t n_heavy = *ws.heavy_count;
   for (uint32_t h = blockIdx.x; h < n_heavy; h += gridDim.x) {
     const long long q = ws.heavy[h];
     const uint32_t s0 = ws.pix_start[q];
     const int m = (int)(ws.pix_start[q + 1] - s0);
-    cta_order_bucket(ws, s0, m, B, S);
     float T;
+    if (m > 2 * kSelectWant) {
+      const int C = cta_select_front(ws, s0, m, B, S, X);
+      if (C > 0) {
+        auto key_at = [&](int k) { return B.K[B.idx[k]]; };
+        auto alpha_at = [&](int k) { return B.A[B.idx[k]]; };
+        const int n = cta_transmittance(P, alpha_at, C, [&](int k, float v) { B.Tk[k] = v; }, H, &T);
+        if (T < P.t_min || C == m) {  // the candidates reach the stop: the prefix is all that blends
+          for (int k = threadIdx.x; k < n; k += kThreads)
+            ws.order[s0 + k] = make_uint2(B.pos[B.idx[k]], (uint32_t)(B.K[B.idx[k]] & kIdMask));
+          __syncthreads();
+          blend_fwd_cta<V, GA, FT>(P, key_at, alpha_at, [&](int k) { return B.Tk[k]; }, n, T, q, feat, image,
+                               T_final, n_contrib, H);
+          __syncthreads();
+          continue;
+        }
+        __syncthreads();
+      }
+    }
+    cta_order_bucket(ws, s0, m, B, S);
     if (m <= kHeavyKeys) {
       auto key_at = [&](int k) { return B.K[B.idx[k]]; };
       auto alpha_at = [&](int k) { return B.A[B.idx[k]]; };
       const int n = cta_transmittance(P, alpha_at, m, [&](int k, float v) { B.Tk[k] = v; }, H, &T);
       for (int k = threadIdx.x; k < n; k += kThreads)
-        ws.order[s0 + k] = make_uint2(B.idx[k], (uint32_t)(B.K[B.idx[k]] & kIdMask));
+        ws.order[s0 + k] = make_uint2(B.pos[B.idx[k]], (uint32_t)(B.K[B.idx[k]] & kIdMask));
       __syncthreads();
       blend_fwd_cta<V, GA, FT>(P, key_at, alpha_at, [&](int k) { return B.Tk[k]; }, n, T, q, feat, image, T_final,
                            n_contrib, H);
