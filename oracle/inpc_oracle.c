@@ -16,7 +16,10 @@
  *                 transmittance 1e-4 and Algorithm 1's stage order;
  *   backward      App. A.6 "During optimization ..." (per-splat gradients
  *                 combined into per-point gradients), written here as the
- *                 plain analytic derivative of the forward definition.
+ *                 plain analytic derivative of the forward definition;
+ *   octree        Sec. 3.1 "Probability Updates" (Eq. 2, Eq. 3, with the
+ *                 per-point blending weights of App. A.6), "Subdivision" and
+ *                 "Pruning", App. A.4 leaf layout.
  *
  * Readings where the paper is silent (all listed in the design notes):
  *   - leaf weights are quantised to integers q_i = rint(w_i / max w * 2^29)
@@ -42,7 +45,15 @@
  *   - alpha = min(alpha_h * w, alpha_max); blending stops after the fragment
  *     whose update takes T below t_min (that fragment is included);
  *   - a point's feature gradient is the plain sum of its splat gradients; its
- *     opacity gradient sums the splat gradients times dalpha/dalpha_h.
+ *     opacity gradient sums the splat gradients times dalpha/dalpha_h;
+ *   - a point's blending weight for the octree updates is the sum of its
+ *     splats' T_k alpha_k weighted by their bilinear weights (App. A.6); a
+ *     splat that is not blended contributes 0, a culled point has weight 0;
+ *   - Eq. 2/3 range over all points drawn from the leaf in the step; a leaf
+ *     without points only decays; subdivision replaces a leaf by its 8
+ *     children in place (x fastest, then y, then z: Morton order within the
+ *     parent) and happens only if the resulting leaf count stays below the
+ *     cap; pruning keeps the order of the surviving leaves.
  */
 #include <math.h>
 #include <stdint.h>
@@ -684,4 +695,127 @@ int64_t oracle_fragment_lists(const oracle_camera* cam, const float* pos, int64_
   }
   free_lists(&L);
   return total;
+}
+
+/* ------------------------------------------------------------ octree ---- */
+
+/* Per-point blending weights for the probability updates (Sec. 3.1 Eq. 2/3
+ * use b_j = T_j alpha_j; App. A.6 combines a point's four splat weights by
+ * their bilinear weights): b[p] = sum_k w_k T_k alpha_k over the point's
+ * blended splats.  pix_sum (optional, [H*W]) = sum over the pixel's blended
+ * fragments of T_k alpha_k (which telescopes to 1 - T_final). */
+int oracle_point_weights(const oracle_camera* cam, const oracle_raster_opts* o, const float* pos,
+                         const double* opacity, const double* feat, int64_t n, double* b, double* pix_sum) {
+  frag_lists L;
+  int st = build_lists(cam, pos, n, &L);
+  if (st != ORACLE_OK) { free_lists(&L); return st; }
+  for (int64_t p = 0; p < n; ++p) b[p] = 0.0;
+  for (int64_t q = 0; q < L.n_pix; ++q) {
+    double T = 1.0, sum = 0.0;
+    for (int64_t k = L.start[q]; k < L.start[q + 1]; ++k) {
+      const frag_rec* r = &L.frags[k];
+      int64_t pi[4], pj[4];
+      double w[4];
+      oracle_splat_corners(L.fu[r->id], L.fv[r->id], pi, pj, w);
+      double a = point_alpha(o, opacity, feat, r->id) * w[r->corner];
+      if (a > o->alpha_max) a = o->alpha_max;
+      b[r->id] += w[r->corner] * (T * a);
+      sum += T * a;
+      T = T * (1.0 - a);
+      if (T < o->t_min) break;
+    }
+    if (pix_sum) pix_sum[q] = sum;
+  }
+  free_lists(&L);
+  return ORACLE_OK;
+}
+
+/* Eq. 2 and Eq. 3 for one step: for every leaf i, with B_i the weights b of
+ * the points drawn from it,
+ *   p_i = max(lambda_u p_i, max B_i),  q_i = max(lambda_u q_i, max B_i - min B_i);
+ * a leaf with no point only decays.  The b are FP32 values (the
+ * rasterizer's output type); max, min and their difference are taken in
+ * FP64. */
+int oracle_octree_update(const int32_t* leaf_idx, const float* b, int64_t n, double* p, double* q,
+                         int64_t n_leaves, double lambda_u) {
+  double* bmax = (double*)malloc(sizeof(double) * (size_t)(n_leaves > 0 ? n_leaves : 1));
+  double* bmin = (double*)malloc(sizeof(double) * (size_t)(n_leaves > 0 ? n_leaves : 1));
+  uint8_t* seen = (uint8_t*)calloc((size_t)(n_leaves > 0 ? n_leaves : 1), 1);
+  if (!bmax || !bmin || !seen) { free(bmax); free(bmin); free(seen); return ORACLE_ERR_NOMEM; }
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t i = leaf_idx[j];
+    if (i < 0 || i >= n_leaves) { free(bmax); free(bmin); free(seen); return ORACLE_ERR_ARG; }
+    double v = (double)b[j];
+    if (!seen[i]) { bmax[i] = v; bmin[i] = v; seen[i] = 1; }
+    else {
+      if (v > bmax[i]) bmax[i] = v;
+      if (v < bmin[i]) bmin[i] = v;
+    }
+  }
+  for (int64_t i = 0; i < n_leaves; ++i) {
+    double dp = lambda_u * p[i], dq = lambda_u * q[i];
+    if (seen[i]) {
+      double spread = bmax[i] - bmin[i];
+      p[i] = bmax[i] > dp ? bmax[i] : dp;
+      q[i] = spread > dq ? spread : dq;
+    } else {
+      p[i] = dp;
+      q[i] = dq;
+    }
+  }
+  free(bmax); free(bmin); free(seen);
+  return ORACLE_OK;
+}
+
+/* Subdivision (Sec. 3.1): every leaf with q_i > tau_s is replaced, in place,
+ * by its 8 children (level l + 1, centers c + (d - 1/2) * root * 2^-(l+1)
+ * per axis for d in {0, 1}, child k = dx + 2 dy + 4 dz), which inherit p_i
+ * and start with q = 0 -- unless the resulting leaf count would reach
+ * max_leaves, in which case nothing is subdivided.  Outputs need room for
+ * 8 n_leaves entries; returns the new leaf count (negative on error). */
+int64_t oracle_octree_subdivide(const float* centers, const int32_t* levels, const double* p, const double* q,
+                                int64_t n_leaves, double root_size, double tau_s, int64_t max_leaves,
+                                float* centers_out, int32_t* levels_out, double* p_out, double* q_out) {
+  int64_t n_split = 0;
+  for (int64_t i = 0; i < n_leaves; ++i) if (q[i] > tau_s) ++n_split;
+  int split = n_leaves + 7 * n_split < max_leaves;
+  int64_t o = 0;
+  for (int64_t i = 0; i < n_leaves; ++i) {
+    if (!(split && q[i] > tau_s)) {
+      for (int d = 0; d < 3; ++d) centers_out[3 * o + d] = centers[3 * i + d];
+      levels_out[o] = levels[i];
+      p_out[o] = p[i];
+      q_out[o] = q[i];
+      ++o;
+      continue;
+    }
+    double child = root_size * ldexp(1.0, -(levels[i] + 1));  /* child edge */
+    for (int k = 0; k < 8; ++k) {
+      int dxyz[3] = {k & 1, (k >> 1) & 1, (k >> 2) & 1};
+      for (int d = 0; d < 3; ++d)
+        centers_out[3 * o + d] = (float)((double)centers[3 * i + d] + ((double)dxyz[d] - 0.5) * child);
+      levels_out[o] = levels[i] + 1;
+      p_out[o] = p[i];
+      q_out[o] = 0.0;
+      ++o;
+    }
+  }
+  return o;
+}
+
+/* Pruning (Sec. 3.1): leaves with p_i < tau_p are removed; the others keep
+ * their order.  Returns the new leaf count. */
+int64_t oracle_octree_prune(const float* centers, const int32_t* levels, const double* p, const double* q,
+                            int64_t n_leaves, double tau_p, float* centers_out, int32_t* levels_out,
+                            double* p_out, double* q_out) {
+  int64_t o = 0;
+  for (int64_t i = 0; i < n_leaves; ++i) {
+    if (p[i] < tau_p) continue;
+    for (int d = 0; d < 3; ++d) centers_out[3 * o + d] = centers[3 * i + d];
+    levels_out[o] = levels[i];
+    p_out[o] = p[i];
+    q_out[o] = q[i];
+    ++o;
+  }
+  return o;
 }

@@ -95,6 +95,16 @@ def lib():
             L.oracle_raster_bwd.restype = C.c_int
             L.oracle_fragment_lists.argtypes = [C.POINTER(OracleCamera), _P, C.c_int64, _P, _P, _P, _P]
             L.oracle_fragment_lists.restype = C.c_int64
+            L.oracle_point_weights.argtypes = [C.POINTER(OracleCamera), C.POINTER(OracleRasterOpts), _P, _P, _P,
+                                               C.c_int64, _P, _P]
+            L.oracle_point_weights.restype = C.c_int
+            L.oracle_octree_update.argtypes = [_P, _P, C.c_int64, _P, _P, C.c_int64, C.c_double]
+            L.oracle_octree_update.restype = C.c_int
+            L.oracle_octree_subdivide.argtypes = [_P, _P, _P, _P, C.c_int64, C.c_double, C.c_double, C.c_int64,
+                                                  _P, _P, _P, _P]
+            L.oracle_octree_subdivide.restype = C.c_int64
+            L.oracle_octree_prune.argtypes = [_P, _P, _P, _P, C.c_int64, C.c_double, _P, _P, _P, _P]
+            L.oracle_octree_prune.restype = C.c_int64
             _lib = L
     return _lib
 
@@ -349,3 +359,67 @@ def fragment_lists(cam, pos):
     dep = np.zeros(max(total, 1), np.float32)
     lib().oracle_fragment_lists(C.byref(cs), _ptr(p), n, _ptr(cnt), _ptr(ids), _ptr(cor), _ptr(dep))
     return cnt.reshape(cam.height, cam.width), ids[:total], cor[:total], dep[:total]
+
+
+# ------------------------------------------------------------------ octree ---
+def point_weights(cam, pos, feat, opacity=None, head_mode=False, t_min=1e-4, alpha_max=0.99, with_pixel_sums=False):
+    """Per-point blending weights b [N] for the probability updates
+    (Sec. 3.1 Eq. 2/3 with App. A.6's bilinear-weighted combination); with
+    ``with_pixel_sums`` also the per-pixel sum of T_k alpha_k [H,W]."""
+    p = _f32(pos)
+    f = _f64(feat)
+    n, F = f.shape
+    op = _f64(opacity) if opacity is not None else None
+    if not head_mode and op is None:
+        raise ValueError("opacity required unless head_mode")
+    b = np.zeros(n, np.float64)
+    ps = np.zeros((cam.height, cam.width), np.float64) if with_pixel_sums else None
+    cs = camera_struct(cam)
+    o = _opts(F, head_mode, t_min, alpha_max, 0.0)
+    st = lib().oracle_point_weights(C.byref(cs), C.byref(o), _ptr(p), _ptr(op), _ptr(f), n, _ptr(b), _ptr(ps))
+    if st != 0:
+        raise OracleError("point_weights failed (%d)" % st)
+    return (b, ps) if with_pixel_sums else b
+
+
+def octree_update(leaf_idx, b, p, q, lambda_u=0.9968):
+    """Eq. 2 / Eq. 3 for one step; returns the new (p, q) (float64)."""
+    li = _i32(leaf_idx)
+    bb = _f32(b)
+    pp = _f64(p).copy()
+    qq = _f64(q).copy()
+    st = lib().oracle_octree_update(_ptr(li), _ptr(bb), li.shape[0], _ptr(pp), _ptr(qq), pp.shape[0],
+                                    float(lambda_u))
+    if st != 0:
+        raise OracleError("octree_update failed (%d)" % st)
+    return pp, qq
+
+
+def octree_subdivide(centers, levels, p, q, root_size=1.0, tau_s=0.5, max_leaves=256 ** 3):
+    """Sec. 3.1 subdivision; returns (centers, levels, p, q) of the new leaves."""
+    c = _f32(centers)
+    lv = _i32(levels)
+    pp, qq = _f64(p), _f64(q)
+    L = lv.shape[0]
+    co = np.zeros((8 * max(L, 1), 3), np.float32)
+    lo = np.zeros(8 * max(L, 1), np.int32)
+    po = np.zeros(8 * max(L, 1), np.float64)
+    qo = np.zeros(8 * max(L, 1), np.float64)
+    n = lib().oracle_octree_subdivide(_ptr(c), _ptr(lv), _ptr(pp), _ptr(qq), L, float(root_size), float(tau_s),
+                                      int(max_leaves), _ptr(co), _ptr(lo), _ptr(po), _ptr(qo))
+    return co[:n], lo[:n], po[:n], qo[:n]
+
+
+def octree_prune(centers, levels, p, q, tau_p=0.01):
+    """Sec. 3.1 pruning; returns (centers, levels, p, q) of the kept leaves."""
+    c = _f32(centers)
+    lv = _i32(levels)
+    pp, qq = _f64(p), _f64(q)
+    L = lv.shape[0]
+    co = np.zeros((max(L, 1), 3), np.float32)
+    lo = np.zeros(max(L, 1), np.int32)
+    po = np.zeros(max(L, 1), np.float64)
+    qo = np.zeros(max(L, 1), np.float64)
+    n = lib().oracle_octree_prune(_ptr(c), _ptr(lv), _ptr(pp), _ptr(qq), L, float(tau_p), _ptr(co), _ptr(lo),
+                                  _ptr(po), _ptr(qo))
+    return co[:n], lo[:n], po[:n], qo[:n]
