@@ -44,6 +44,8 @@ typedef enum {
 /* Device status bits (inpc_read_device_status). */
 #define INPC_DEV_BAD_WEIGHT 0x1u   /* a leaf weight was negative, NaN or infinite */
 #define INPC_DEV_NO_WEIGHT 0x2u    /* no leaf weight was positive */
+#define INPC_DEV_BAD_LEAF 0x4u      /* inpc_octree_update: a leaf index outside [0, n_leaves) (ignored) */
+#define INPC_DEV_BAD_BLEND_WEIGHT 0x8u /* inpc_octree_update: a negative or NaN weight (counted as 0) */
 
 typedef enum { INPC_F32 = 0, INPC_BF16 = 1 } inpc_dtype;
 
@@ -293,6 +295,79 @@ inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const inpc_raste
                                         const float* T_final, const int32_t* n_contrib, const float* d_image,
                                         float* grad_table, float* d_feat, void* workspace, size_t workspace_bytes,
                                         inpc_stream_t stream);
+
+/* ======================================================================== */
+/* (d) Octree maintenance (Sec. 3.1 "Probability Updates", "Subdivision",   */
+/*     "Pruning"; App. A.4)                                                  */
+/* ======================================================================== */
+
+/* Per-point blending weights for the probability updates: Eq. 2 takes the
+ * transmitted blending weight T alpha of every point, and App. A.6 combines
+ * a point's four splat weights by their bilinear weights:
+ *   b[p] = sum over the point's blended splats k of w_k T_k alpha_k
+ * (0 for splats that were not blended and for culled points).  T_k is
+ * recomputed from the forward's recorded blending order with the forward's
+ * own product scan, so it is bitwise the forward's.
+ *   cam, opts, pos, n, n_contrib, workspace: those of the inpc_rasterize_fwd
+ *              call (the workspace unmodified since; its per-fragment
+ *              scratch of the backward is reused, so call this before or
+ *              after inpc_rasterize_bwd, not while it runs)
+ *   b_out      float32 [n], written
+ * Errors: INPC_ERR_INVALID_ARG (null pointer, workspace too small). */
+inpc_status inpc_rasterize_point_weights(const inpc_camera* cam, const inpc_raster_opts* opts, const float* pos,
+                                         int64_t n, const int32_t* n_contrib, float* b_out, void* workspace,
+                                         size_t workspace_bytes, inpc_stream_t stream);
+
+/* Probability updates after one step (Eq. 2 and Eq. 3): for every leaf i,
+ * with B_i the weights b of the points drawn from leaf i in this step,
+ *   p_i = max(lambda_u p_i, max B_i),   q_i = max(lambda_u q_i, max B_i - min B_i),
+ * max / min over FP32 values, the update in FP64; a leaf no point was drawn
+ * from only decays (p_i = lambda_u p_i, q_i = lambda_u q_i).  The paper uses
+ * lambda_u = 0.9968 (and skips updates in the first 100 iterations, a
+ * schedule left to the caller).
+ *   leaf_idx   int32 [n]: leaf of each point (inpc_sample_octree's output)
+ *   b          float32 [n]: inpc_rasterize_point_weights' output (>= 0;
+ *              negative or NaN values count as 0 and set
+ *              INPC_DEV_BAD_BLEND_WEIGHT; out-of-range leaves are ignored
+ *              and set INPC_DEV_BAD_LEAF in the workspace status)
+ *   p, q       float64 [n_leaves], updated in place (p is the octree's
+ *              sampling weight array)
+ *   workspace  inpc_octree_update_workspace_size(n_leaves) bytes, 256-aligned
+ * n_leaves in [1, 2^24]; lambda_u in [0, 1].  Asynchronous. */
+inpc_status inpc_octree_update_workspace_size(int64_t n_leaves, size_t* bytes);
+inpc_status inpc_octree_update(const int32_t* leaf_idx, const float* b, int64_t n, double* p, double* q,
+                               int64_t n_leaves, double lambda_u, void* workspace, size_t workspace_bytes,
+                               inpc_stream_t stream);
+
+/* Subdivision (Sec. 3.1): every leaf with q_i > tau_s (0.5 in the paper) is
+ * replaced, in its place in the list, by its 8 children: level l_i + 1,
+ * centers c_i + (d - 1/2) root_size 2^-(l_i+1) per axis for d in {0, 1},
+ * child k = d_x + 2 d_y + 4 d_z (Morton order within the parent, so a
+ * Morton-ordered list stays Morton-ordered); children inherit p_i and start
+ * with q = 0.  If the resulting leaf count would not stay below max_leaves
+ * (256^3 in the paper, for the sampler's precision), no leaf is subdivided
+ * and the tree is copied unchanged.
+ *   tree       input leaves (weights = p); q float64 [n_leaves]
+ *   *_out      output leaves (centers float32 [cap, 3], levels int32 [cap],
+ *              p_out, q_out float64 [cap]); cap = out_capacity, at most
+ *              8 n_leaves are ever needed
+ *   n_out      receives the new leaf count
+ *   workspace  inpc_octree_refine_workspace_size(n_leaves) bytes
+ * Synchronises `stream` (the output count decides the capacity check).
+ * Errors: INPC_ERR_INVALID_ARG, INPC_ERR_CAPACITY (out_capacity too small;
+ * nothing written). */
+inpc_status inpc_octree_refine_workspace_size(int64_t n_leaves, size_t* bytes);
+inpc_status inpc_octree_subdivide(const inpc_octree* tree, const double* q, double tau_s, int64_t max_leaves,
+                                  float* centers_out, int32_t* levels_out, double* p_out, double* q_out,
+                                  int64_t out_capacity, int64_t* n_out, void* workspace, size_t workspace_bytes,
+                                  inpc_stream_t stream);
+
+/* Pruning (Sec. 3.1): leaves with p_i < tau_p (0.01 in the paper) are
+ * removed; the others keep their order.  Arguments and errors as for
+ * inpc_octree_subdivide (at most n_leaves outputs). */
+inpc_status inpc_octree_prune(const inpc_octree* tree, const double* q, double tau_p, float* centers_out,
+                              int32_t* levels_out, double* p_out, double* q_out, int64_t out_capacity,
+                              int64_t* n_out, void* workspace, size_t workspace_bytes, inpc_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -24,6 +24,8 @@ STATUS_NAMES = {0: "INPC_OK", 1: "INPC_ERR_INVALID_ARG", 2: "INPC_ERR_CUDA", 3: 
 
 INPC_DEV_BAD_WEIGHT = 0x1
 INPC_DEV_NO_WEIGHT = 0x2
+INPC_DEV_BAD_LEAF = 0x4
+INPC_DEV_BAD_BLEND_WEIGHT = 0x8
 
 INPC_F32 = 0
 INPC_BF16 = 1
@@ -38,6 +40,8 @@ DECLARED = [
     "inpc_rasterize_workspace_size", "inpc_rasterize_fwd", "inpc_rasterize_bwd",
     "inpc_rasterize_bwd_hashgrid_workspace_size", "inpc_rasterize_bwd_hashgrid",
     "inpc_kernel_timer_enable", "inpc_kernel_timer_read",
+    "inpc_rasterize_point_weights", "inpc_octree_update_workspace_size", "inpc_octree_update",
+    "inpc_octree_refine_workspace_size", "inpc_octree_subdivide", "inpc_octree_prune",
 ]
 
 
@@ -108,6 +112,15 @@ def load(path: str = LIB_PATH):
         L.inpc_rasterize_bwd_hashgrid.argtypes = [C.POINTER(InpcCamera), C.POINTER(InpcRasterOpts),
                                                   C.POINTER(InpcHashgridDesc), _P, _P, C.c_int64, _P, _P, _P, _P, _P,
                                                   _P, C.c_size_t, _P]
+        L.inpc_rasterize_point_weights.argtypes = [C.POINTER(InpcCamera), C.POINTER(InpcRasterOpts), _P, C.c_int64,
+                                                   _P, _P, _P, C.c_size_t, _P]
+        L.inpc_octree_update_workspace_size.argtypes = [C.c_int64, C.POINTER(C.c_size_t)]
+        L.inpc_octree_update.argtypes = [_P, _P, C.c_int64, _P, _P, C.c_int64, C.c_double, _P, C.c_size_t, _P]
+        L.inpc_octree_refine_workspace_size.argtypes = [C.c_int64, C.POINTER(C.c_size_t)]
+        L.inpc_octree_subdivide.argtypes = [C.POINTER(InpcOctree), _P, C.c_double, C.c_int64, _P, _P, _P, _P,
+                                            C.c_int64, C.POINTER(C.c_int64), _P, C.c_size_t, _P]
+        L.inpc_octree_prune.argtypes = [C.POINTER(InpcOctree), _P, C.c_double, _P, _P, _P, _P, C.c_int64,
+                                        C.POINTER(C.c_int64), _P, C.c_size_t, _P]
         L.inpc_kernel_timer_enable.argtypes = [C.c_int]
         L.inpc_kernel_timer_read.argtypes = [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         for name in DECLARED:
@@ -218,3 +231,43 @@ def inpc_rasterize_bwd_hashgrid(cam: InpcCamera, opts: InpcRasterOpts, desc: Inp
     check(load().inpc_rasterize_bwd_hashgrid(C.byref(cam), C.byref(opts), C.byref(desc), pos, feat, n, T_final,
                                              n_contrib, d_image, grad_table, d_feat, workspace, workspace_bytes,
                                              stream))
+
+
+def inpc_rasterize_point_weights(cam: InpcCamera, opts: InpcRasterOpts, pos: int, n: int, n_contrib: int, b_out: int,
+                                 workspace: int, workspace_bytes: int, stream: int):
+    check(load().inpc_rasterize_point_weights(C.byref(cam), C.byref(opts), pos, n, n_contrib, b_out, workspace,
+                                              workspace_bytes, stream))
+
+
+def inpc_octree_update_workspace_size(n_leaves: int) -> int:
+    out = C.c_size_t(0)
+    check(load().inpc_octree_update_workspace_size(n_leaves, C.byref(out)))
+    return int(out.value)
+
+
+def inpc_octree_update(leaf_idx: int, b: int, n: int, p: int, q: int, n_leaves: int, lambda_u: float,
+                       workspace: int, workspace_bytes: int, stream: int):
+    check(load().inpc_octree_update(leaf_idx, b, n, p, q, n_leaves, lambda_u, workspace, workspace_bytes, stream))
+
+
+def inpc_octree_refine_workspace_size(n_leaves: int) -> int:
+    out = C.c_size_t(0)
+    check(load().inpc_octree_refine_workspace_size(n_leaves, C.byref(out)))
+    return int(out.value)
+
+
+def inpc_octree_subdivide(tree: InpcOctree, q: int, tau_s: float, max_leaves: int, centers_out: int,
+                          levels_out: int, p_out: int, q_out: int, out_capacity: int, workspace: int,
+                          workspace_bytes: int, stream: int) -> int:
+    n = C.c_int64(0)
+    check(load().inpc_octree_subdivide(C.byref(tree), q, tau_s, max_leaves, centers_out, levels_out, p_out, q_out,
+                                       out_capacity, C.byref(n), workspace, workspace_bytes, stream))
+    return int(n.value)
+
+
+def inpc_octree_prune(tree: InpcOctree, q: int, tau_p: float, centers_out: int, levels_out: int, p_out: int,
+                      q_out: int, out_capacity: int, workspace: int, workspace_bytes: int, stream: int) -> int:
+    n = C.c_int64(0)
+    check(load().inpc_octree_prune(C.byref(tree), q, tau_p, centers_out, levels_out, p_out, q_out, out_capacity,
+                                   C.byref(n), workspace, workspace_bytes, stream))
+    return int(n.value)

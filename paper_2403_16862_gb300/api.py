@@ -266,3 +266,59 @@ def render_view(tree_t, root_size, desc, table, cam, seed, view_id, n_samples, o
         opts = RasterOptions(n_channels=desc.n_levels * desc.n_feats, head_mode=True)
     image, T_final, n_contrib = Rasterize.apply(pos, h, None, cam, opts)
     return image, T_final, n_contrib, pos
+
+
+# ------------------------------------------------------ octree maintenance ---
+def point_weights(cam, opts: RasterOptions, pos, n_contrib, ws, out=None):
+    """Per-point blending weights b [N] (float32) of the forward that used
+    ``ws`` and produced ``n_contrib`` (Sec. 3.1 Eq. 2 / App. A.6)."""
+    n = pos.shape[0]
+    b = out if out is not None else torch.empty(n, dtype=torch.float32, device=pos.device)
+    _need(n_contrib, torch.int32, "n_contrib")
+    B.inpc_rasterize_point_weights(camera(cam), opts.c(), _ptr(pos), n, _ptr(n_contrib), _ptr(b), ws.data_ptr(),
+                                   ws.numel(), _stream())
+    return b
+
+
+def octree_update(leaf_idx, b, p, q, lambda_u: float = 0.9968, ws=None):
+    """Eq. 2 / Eq. 3 in place on p, q (float64 [L]) from the points' leaves
+    and blending weights."""
+    _need(leaf_idx, torch.int32, "leaf_idx")
+    _need(b, torch.float32, "b")
+    _need(p, torch.float64, "p")
+    _need(q, torch.float64, "q")
+    L = p.shape[0]
+    need = B.inpc_octree_update_workspace_size(L)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, p.device)
+    B.inpc_octree_update(_ptr(leaf_idx), _ptr(b), leaf_idx.shape[0], _ptr(p), _ptr(q), L, float(lambda_u),
+                         ws.data_ptr(), ws.numel(), _stream())
+    return p, q
+
+
+def _refine(fn, centers, levels, p, q, root_size, cap, *args):
+    _need(centers, torch.float32, "centers")
+    _need(levels, torch.int32, "levels")
+    _need(p, torch.float64, "p")
+    _need(q, torch.float64, "q")
+    L = levels.shape[0]
+    dev = centers.device
+    co = torch.empty(cap, 3, dtype=torch.float32, device=dev)
+    lo = torch.empty(cap, dtype=torch.int32, device=dev)
+    po = torch.empty(cap, dtype=torch.float64, device=dev)
+    qo = torch.empty(cap, dtype=torch.float64, device=dev)
+    ws = workspace(B.inpc_octree_refine_workspace_size(L), dev)
+    tree = B.InpcOctree(_ptr(centers), _ptr(levels), _ptr(p), float(root_size), L)
+    n = fn(tree, _ptr(q), *args, _ptr(co), _ptr(lo), _ptr(po), _ptr(qo), cap, ws.data_ptr(), ws.numel(), _stream())
+    return co[:n], lo[:n], po[:n], qo[:n]
+
+
+def octree_subdivide(centers, levels, p, q, root_size: float, tau_s: float = 0.5, max_leaves: int = 256 ** 3):
+    """Sec. 3.1 subdivision; returns the new (centers, levels, p, q)."""
+    return _refine(B.inpc_octree_subdivide, centers, levels, p, q, root_size, 8 * levels.shape[0], float(tau_s),
+                   int(max_leaves))
+
+
+def octree_prune(centers, levels, p, q, root_size: float, tau_p: float = 0.01):
+    """Sec. 3.1 pruning; returns the kept (centers, levels, p, q)."""
+    return _refine(B.inpc_octree_prune, centers, levels, p, q, root_size, levels.shape[0], float(tau_p))
