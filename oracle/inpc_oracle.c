@@ -19,7 +19,9 @@
  *                 plain analytic derivative of the forward definition;
  *   octree        Sec. 3.1 "Probability Updates" (Eq. 2, Eq. 3, with the
  *                 per-point blending weights of App. A.6), "Subdivision" and
- *                 "Pruning", App. A.4 leaf layout.
+ *                 "Pruning", App. A.4 leaf layout;
+ *   view sampling Sec. 3.2 "Viewpoint-Specific Sampling" (Eq. 4) with App.
+ *                 A.4 "Depth Calculation" and "Ensuring Sample Count".
  *
  * Readings where the paper is silent (all listed in the design notes):
  *   - leaf weights are quantised to integers q_i = rint(w_i / max w * 2^29)
@@ -53,7 +55,15 @@
  *     without points only decays; subdivision replaces a leaf by its 8
  *     children in place (x fastest, then y, then z: Morton order within the
  *     parent) and happens only if the resulting leaf count stays below the
- *     cap; pruning keeps the order of the surviving leaves.
+ *     cap; pruning keeps the order of the surviving leaves;
+ *   - a leaf is visible unless all 8 corners of its cube lie outside one
+ *     plane of the view frustum (near < z < far, 0 <= u < W, 0 <= v < H),
+ *     in FP64 camera coordinates with a fixed operation order; d_i uses the
+ *     leaf center's view-space z; the level factor 2^(l lambda_l) is exp2;
+ *   - a sample is in view when its FP32 position projects (the rasterizer's
+ *     FP32 projection) strictly between near and far and into [0, W) x [0, H);
+ *     round r of the re-sampling redraws every sample not in view, in place,
+ *     with Philox purposes 2 + 2r (leaf) and 3 + 2r (position).
  */
 #include <math.h>
 #include <stdint.h>
@@ -818,4 +828,97 @@ int64_t oracle_octree_prune(const float* centers, const int32_t* levels, const d
     ++o;
   }
   return o;
+}
+
+/* ------------------------------------------------- view-specific sampling */
+
+/* Camera coordinates of a world point in FP64, evaluated left to right. */
+static void cam_space(const oracle_camera* cam, const double x[3], double xc[3]) {
+  for (int k = 0; k < 3; ++k)
+    xc[k] = (double)cam->R[3 * k] * x[0] + (double)cam->R[3 * k + 1] * x[1] + (double)cam->R[3 * k + 2] * x[2] +
+            (double)cam->t[k];
+}
+
+/* Frustum culling of a leaf cube (center c, edge e): culled iff all corners
+ * are outside one of the six planes. */
+static int box_visible(const oracle_camera* cam, const float* c, double e) {
+  int out[6] = {1, 1, 1, 1, 1, 1};
+  for (int k = 0; k < 8; ++k) {
+    double x[3] = {(double)c[0] + ((k & 1) ? 0.5 : -0.5) * e, (double)c[1] + ((k & 2) ? 0.5 : -0.5) * e,
+                   (double)c[2] + ((k & 4) ? 0.5 : -0.5) * e};
+    double xc[3];
+    cam_space(cam, x, xc);
+    if (!(xc[2] <= (double)cam->near_plane)) out[0] = 0;
+    if (!(xc[2] >= (double)cam->far_plane)) out[1] = 0;
+    if (!((double)cam->fx * xc[0] + (double)cam->cx * xc[2] < 0.0)) out[2] = 0;
+    if (!((double)cam->fx * xc[0] + ((double)cam->cx - (double)cam->width) * xc[2] >= 0.0)) out[3] = 0;
+    if (!((double)cam->fy * xc[1] + (double)cam->cy * xc[2] < 0.0)) out[4] = 0;
+    if (!((double)cam->fy * xc[1] + ((double)cam->cy - (double)cam->height) * xc[2] >= 0.0)) out[5] = 0;
+  }
+  for (int i = 0; i < 6; ++i) if (out[i]) return 0;
+  return 1;
+}
+
+/* Eq. 4: w_i = 1_visible p_i / (d_i 2^(l_i lambda_l)) with the view depth
+ * d_i = max(|z_view - near| / far, tau_d) (App. A.4). */
+int oracle_view_weights(const float* centers, const int32_t* levels, const double* p, int64_t n_leaves,
+                        double root_size, const oracle_camera* cam, double lambda_l, double tau_d, double* w_out) {
+  for (int64_t i = 0; i < n_leaves; ++i) {
+    double e = ldexp(root_size, -levels[i]);
+    if (!box_visible(cam, centers + 3 * i, e)) { w_out[i] = 0.0; continue; }
+    double c[3] = {(double)centers[3 * i], (double)centers[3 * i + 1], (double)centers[3 * i + 2]};
+    double xc[3];
+    cam_space(cam, c, xc);
+    double d = fabs(xc[2] - (double)cam->near_plane) / (double)cam->far_plane;
+    if (d < tau_d) d = tau_d;
+    w_out[i] = p[i] / (d * exp2((double)levels[i] * lambda_l));
+  }
+  return ORACLE_OK;
+}
+
+/* A sample is in view when the rasterizer's FP32 projection keeps it and it
+ * falls inside the image rectangle. */
+int oracle_point_in_view(const oracle_camera* cam, const float* p) {
+  float u, v, d;
+  if (!oracle_project(cam, p, &u, &v, &d)) return 0;
+  return u >= 0.0f && u < (float)cam->width && v >= 0.0f && v < (float)cam->height;
+}
+
+/* App. A.4 "Ensuring Sample Count": up to max_rounds rounds; in round r every
+ * sample j not in view gets a new leaf (draw with Philox counter (j, view,
+ * 2 + 2r) over the CDF of w) and a new position (counter (j, view, 3 + 2r)),
+ * in place.  n_left receives the number of samples still not in view. */
+int oracle_resample_view(const float* centers, const int32_t* levels, const double* w, int64_t n_leaves,
+                         double root_size, const oracle_camera* cam, uint64_t seed, uint32_t view_id, int64_t n,
+                         int32_t max_rounds, int32_t* leaf, float* pos, int64_t* n_left) {
+  double* cdf = (double*)malloc(sizeof(double) * (size_t)(n_leaves > 0 ? n_leaves : 1));
+  if (!cdf) return ORACLE_ERR_NOMEM;
+  double Qd = 0.0;
+  int st = oracle_build_cdf(w, n_leaves, cdf, &Qd);
+  if (st != ORACLE_OK) { free(cdf); return st; }
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int32_t r = 0; r < max_rounds; ++r) {
+    int64_t redrawn = 0;
+    for (int64_t j = 0; j < n; ++j) {
+      if (oracle_point_in_view(cam, pos + 3 * j)) continue;
+      uint32_t c0[4] = {(uint32_t)j, (uint32_t)((uint64_t)j >> 32), view_id, 2u + 2u * (uint32_t)r};
+      uint32_t r4[4];
+      oracle_philox4x32_10(key, c0, r4);
+      uint64_t b = ((uint64_t)(r4[1] & 0x1FFFFFu) << 32) | (uint64_t)r4[0];
+      int64_t i = oracle_search_cdf(cdf, n_leaves, (double)oracle_scale_draw(b, (uint64_t)Qd));
+      uint32_t c1[4] = {(uint32_t)j, (uint32_t)((uint64_t)j >> 32), view_id, 3u + 2u * (uint32_t)r};
+      oracle_philox4x32_10(key, c1, r4);
+      double edge = ldexp(root_size, -levels[i]);
+      for (int d = 0; d < 3; ++d)
+        pos[3 * j + d] = (float)((double)centers[3 * i + d] + (ldexp((double)(r4[d] >> 8), -24) - 0.5) * edge);
+      leaf[j] = (int32_t)i;
+      ++redrawn;
+    }
+    if (redrawn == 0) break;
+  }
+  int64_t left = 0;
+  for (int64_t j = 0; j < n; ++j) left += !oracle_point_in_view(cam, pos + 3 * j);
+  *n_left = left;
+  free(cdf);
+  return ORACLE_OK;
 }

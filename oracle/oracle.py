@@ -105,6 +105,14 @@ def lib():
             L.oracle_octree_subdivide.restype = C.c_int64
             L.oracle_octree_prune.argtypes = [_P, _P, _P, _P, C.c_int64, C.c_double, _P, _P, _P, _P]
             L.oracle_octree_prune.restype = C.c_int64
+            L.oracle_view_weights.argtypes = [_P, _P, _P, C.c_int64, C.c_double, C.POINTER(OracleCamera),
+                                              C.c_double, C.c_double, _P]
+            L.oracle_view_weights.restype = C.c_int
+            L.oracle_point_in_view.argtypes = [C.POINTER(OracleCamera), _P]
+            L.oracle_point_in_view.restype = C.c_int
+            L.oracle_resample_view.argtypes = [_P, _P, _P, C.c_int64, C.c_double, C.POINTER(OracleCamera),
+                                               C.c_uint64, C.c_uint32, C.c_int64, C.c_int32, _P, _P, _P]
+            L.oracle_resample_view.restype = C.c_int
             _lib = L
     return _lib
 
@@ -423,3 +431,44 @@ def octree_prune(centers, levels, p, q, tau_p=0.01):
     n = lib().oracle_octree_prune(_ptr(c), _ptr(lv), _ptr(pp), _ptr(qq), L, float(tau_p), _ptr(co), _ptr(lo),
                                   _ptr(po), _ptr(qo))
     return co[:n], lo[:n], po[:n], qo[:n]
+
+
+# ---------------------------------------------------- view-specific sampling ---
+def view_weights(tree, cam, p=None, lambda_l=0.5, tau_d=1e-8):
+    """Eq. 4 view-specific leaf weights (float64 [L]); p defaults to the
+    tree's weights."""
+    c = _f32(tree.centers)
+    lv = _i32(tree.levels)
+    pp = _f64(tree.weights if p is None else p)
+    w = np.zeros(lv.shape[0], np.float64)
+    cs = camera_struct(cam)
+    st = lib().oracle_view_weights(_ptr(c), _ptr(lv), _ptr(pp), lv.shape[0], float(tree.root_size), C.byref(cs),
+                                   float(lambda_l), float(tau_d), _ptr(w))
+    if st != 0:
+        raise OracleError("view_weights failed (%d)" % st)
+    return w
+
+
+def points_in_view(cam, pos):
+    p = _f32(pos)
+    cs = camera_struct(cam)
+    return np.array([lib().oracle_point_in_view(C.byref(cs), _ptr(p[j])) for j in range(p.shape[0])], bool)
+
+
+def sample_view(tree, w, cam, seed: int, view_id: int, n_samples: int, max_rounds: int = 8):
+    """Sampling with the view weights w, then the re-sampling rounds of App.
+    A.4; returns (leaf int32 [N], pos float32 [N,3], samples left not in view)."""
+    view_tree = type(tree)(centers=tree.centers, levels=tree.levels, weights=np.asarray(w, np.float64),
+                           root_size=tree.root_size)
+    leaf, pos64, _ = sample_octree(view_tree, seed, view_id, n_samples)
+    leaf = _i32(leaf).copy()
+    pos = pos64.astype(np.float32)
+    left = C.c_int64(0)
+    cs = camera_struct(cam)
+    c, lv, ww = _f32(tree.centers), _i32(tree.levels), _f64(w)
+    st = lib().oracle_resample_view(_ptr(c), _ptr(lv), _ptr(ww), lv.shape[0], float(tree.root_size), C.byref(cs),
+                                    int(seed), int(view_id), n_samples, int(max_rounds), _ptr(leaf), _ptr(pos),
+                                    C.byref(left))
+    if st != 0:
+        raise OracleError("resample_view failed (%d)" % st)
+    return leaf, pos, int(left.value)
