@@ -296,6 +296,37 @@ inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const inpc_raste
                                         float* grad_table, float* d_feat, void* workspace, size_t workspace_bytes,
                                         inpc_stream_t stream);
 
+/* View-specific leaf weights (Sec. 3.2 Eq. 4 with App. A.4 "Depth
+ * Calculation"): w_i = 1_visible p_i / (d_i 2^(l_i lambda_l)), where
+ *   - a leaf is visible unless all 8 corners of its cube lie outside one
+ *     plane of the view frustum (near < z < far, 0 <= u < W, 0 <= v < H);
+ *   - d_i = max(|z_i - near| / far, tau_d), z_i the view-space depth of the
+ *     leaf center;
+ *   - 2^(l lambda_l) is evaluated on the host (exp2, levels 0..63; leaves
+ *     with other levels get weight 0).
+ * FP64 throughout with a fixed operation order (camera coordinates
+ * ((R_k0 x + R_k1 y) + R_k2 z) + t_k).  The paper uses lambda_l = 0.5 and
+ * tau_d = 1e-8.  tree->weights holds p; w_out float64 [n_leaves].
+ * Errors: INPC_ERR_INVALID_ARG (null pointer, bad camera, tau_d <= 0). */
+inpc_status inpc_view_weights(const inpc_octree* tree, const inpc_camera* cam, double lambda_l, double tau_d,
+                              double* w_out, inpc_stream_t stream);
+
+/* Viewpoint-specific sampling with the re-sampling of App. A.4 ("Ensuring
+ * Sample Count"): inpc_sample_octree with tree->weights = the view weights
+ * (inpc_view_weights), then up to max_rounds rounds in which every sample
+ * whose position is not in view (the rasterizer's FP32 projection keeps it
+ * and it lands in [0, W) x [0, H)) draws, in place, a new leaf from the same
+ * distribution (Philox counter (j, view, 2 + 2r)) and a new position in it
+ * (counter (j, view, 3 + 2r)); samples already in view never change.
+ *   n_left  optional device uint32: the number of samples still not in view
+ *           after the last round
+ * max_rounds in [0, 64]; other arguments, workspace and errors as for
+ * inpc_sample_octree.  Asynchronous. */
+inpc_status inpc_sample_octree_view(const inpc_octree* tree, const inpc_camera* cam, uint64_t seed,
+                                    uint32_t view_id, int64_t n_samples, int32_t max_rounds, int32_t* leaf_idx_out,
+                                    float* pos_out, uint32_t* n_left, void* workspace, size_t workspace_bytes,
+                                    inpc_stream_t stream);
+
 /* ======================================================================== */
 /* (d) Octree maintenance (Sec. 3.1 "Probability Updates", "Subdivision",   */
 /*     "Pruning"; App. A.4)                                                  */

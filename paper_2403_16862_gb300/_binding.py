@@ -42,6 +42,7 @@ DECLARED = [
     "inpc_kernel_timer_enable", "inpc_kernel_timer_read",
     "inpc_rasterize_point_weights", "inpc_octree_update_workspace_size", "inpc_octree_update",
     "inpc_octree_refine_workspace_size", "inpc_octree_subdivide", "inpc_octree_prune",
+    "inpc_view_weights", "inpc_sample_octree_view",
 ]
 
 
@@ -121,6 +122,9 @@ def load(path: str = LIB_PATH):
                                             C.c_int64, C.POINTER(C.c_int64), _P, C.c_size_t, _P]
         L.inpc_octree_prune.argtypes = [C.POINTER(InpcOctree), _P, C.c_double, _P, _P, _P, _P, C.c_int64,
                                         C.POINTER(C.c_int64), _P, C.c_size_t, _P]
+        L.inpc_view_weights.argtypes = [C.POINTER(InpcOctree), C.POINTER(InpcCamera), C.c_double, C.c_double, _P, _P]
+        L.inpc_sample_octree_view.argtypes = [C.POINTER(InpcOctree), C.POINTER(InpcCamera), C.c_uint64, C.c_uint32,
+                                              C.c_int64, C.c_int32, _P, _P, _P, _P, C.c_size_t, _P]
         L.inpc_kernel_timer_enable.argtypes = [C.c_int]
         L.inpc_kernel_timer_read.argtypes = [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         for name in DECLARED:
@@ -271,3 +275,14 @@ def inpc_octree_prune(tree: InpcOctree, q: int, tau_p: float, centers_out: int, 
     check(load().inpc_octree_prune(C.byref(tree), q, tau_p, centers_out, levels_out, p_out, q_out, out_capacity,
                                    C.byref(n), workspace, workspace_bytes, stream))
     return int(n.value)
+
+
+def inpc_view_weights(tree: InpcOctree, cam: InpcCamera, lambda_l: float, tau_d: float, w_out: int, stream: int):
+    check(load().inpc_view_weights(C.byref(tree), C.byref(cam), lambda_l, tau_d, w_out, stream))
+
+
+def inpc_sample_octree_view(tree: InpcOctree, cam: InpcCamera, seed: int, view_id: int, n_samples: int,
+                            max_rounds: int, leaf_idx_out: int, pos_out: int, n_left, workspace: int,
+                            workspace_bytes: int, stream: int):
+    check(load().inpc_sample_octree_view(C.byref(tree), C.byref(cam), seed, view_id, n_samples, max_rounds,
+                                         leaf_idx_out, pos_out, n_left, workspace, workspace_bytes, stream))

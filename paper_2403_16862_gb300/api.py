@@ -322,3 +322,40 @@ def octree_subdivide(centers, levels, p, q, root_size: float, tau_s: float = 0.5
 def octree_prune(centers, levels, p, q, root_size: float, tau_p: float = 0.01):
     """Sec. 3.1 pruning; returns the kept (centers, levels, p, q)."""
     return _refine(B.inpc_octree_prune, centers, levels, p, q, root_size, levels.shape[0], float(tau_p))
+
+
+# -------------------------------------------------- view-specific sampling ---
+def view_weights(centers, levels, p, root_size: float, cam, lambda_l: float = 0.5, tau_d: float = 1e-8, out=None):
+    """Eq. 4 view-specific leaf weights (float64 [L])."""
+    _need(centers, torch.float32, "centers")
+    _need(levels, torch.int32, "levels")
+    _need(p, torch.float64, "p")
+    L = levels.shape[0]
+    w = out if out is not None else torch.empty(L, dtype=torch.float64, device=p.device)
+    tree = B.InpcOctree(_ptr(centers), _ptr(levels), _ptr(p), float(root_size), L)
+    B.inpc_view_weights(tree, camera(cam), float(lambda_l), float(tau_d), _ptr(w), _stream())
+    return w
+
+
+def sample_octree_view(centers, levels, view_w, root_size: float, cam, seed: int, view_id: int, n_samples: int,
+                       max_rounds: int = 8, ws=None, out=None):
+    """Sampling from the view weights with the re-sampling rounds of App. A.4;
+    returns (leaf_idx, pos, n_left) with n_left a device int32 scalar."""
+    _need(centers, torch.float32, "centers")
+    _need(levels, torch.int32, "levels")
+    _need(view_w, torch.float64, "view weights")
+    L = levels.shape[0]
+    dev = centers.device
+    need = B.inpc_sample_workspace_size(L, n_samples)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    if out is None:
+        leaf = torch.empty(n_samples, dtype=torch.int32, device=dev)
+        pos = torch.empty(n_samples, 3, dtype=torch.float32, device=dev)
+    else:
+        leaf, pos = out
+    n_left = torch.zeros(1, dtype=torch.int32, device=dev)
+    tree = B.InpcOctree(_ptr(centers), _ptr(levels), _ptr(view_w), float(root_size), L)
+    B.inpc_sample_octree_view(tree, camera(cam), seed, view_id, n_samples, int(max_rounds), _ptr(leaf), _ptr(pos),
+                              _ptr(n_left), ws.data_ptr(), ws.numel(), _stream())
+    return leaf, pos, n_left

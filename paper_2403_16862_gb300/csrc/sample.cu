@@ -11,6 +11,7 @@
 //   k_scan_*      exclusive scan of counts -> first output slot of each leaf
 //   k_place       slot -> leaf (two-level search), Philox position
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 
@@ -284,6 +285,109 @@ __global__ void k_check_total(const double* cdf, int64_t L, uint32_t* status) {
   if (threadIdx.x == 0 && !(cdf[L - 1] > 0.0)) raise_status(status, INPC_DEV_NO_WEIGHT);
 }
 
+// ------------------------------------------------ view-specific sampling ---
+// Eq. 4 per leaf: frustum culling of the leaf cube (all 8 corners outside
+// one plane), view depth d = max(|z - near| / far, tau_d) of the center and
+// the level factor 2^(l lambda_l) from a host table; FP64 with explicit
+// round-to-nearest operations in a fixed order.
+constexpr int kMaxViewLevel = 63;
+
+struct LevelFactors {
+  double f[kMaxViewLevel + 1];  // 2^(l lambda_l)
+};
+
+__device__ __forceinline__ double dmad(double a, double b, double c) { return __dadd_rn(__dmul_rn(a, b), c); }
+
+__device__ __forceinline__ void cam_space_d(const Cam& c, const double x[3], double xc[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    xc[k] = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)c.R[3 * k], x[0]), __dmul_rn((double)c.R[3 * k + 1], x[1])),
+                                __dmul_rn((double)c.R[3 * k + 2], x[2])),
+                      (double)c.t[k]);
+}
+
+__global__ void k_view_weights(inpc_octree t, Cam cam, LevelFactors lf, double tau_d, double* __restrict__ w_out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < t.n_leaves;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int l = t.levels[i];
+    if (l < 0 || l > kMaxViewLevel) {
+      w_out[i] = 0.0;
+      continue;
+    }
+    const double e = ldexp((double)t.root_size, -l);
+    const double c[3] = {(double)t.centers[3 * i], (double)t.centers[3 * i + 1], (double)t.centers[3 * i + 2]};
+    bool out[6] = {true, true, true, true, true, true};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const double x[3] = {dmad((k & 1) ? 0.5 : -0.5, e, c[0]), dmad((k & 2) ? 0.5 : -0.5, e, c[1]),
+                           dmad((k & 4) ? 0.5 : -0.5, e, c[2])};
+      double xc[3];
+      cam_space_d(cam, x, xc);
+      if (!(xc[2] <= (double)cam.near_plane)) out[0] = false;
+      if (!(xc[2] >= (double)cam.far_plane)) out[1] = false;
+      if (!(__dadd_rn(__dmul_rn((double)cam.fx, xc[0]), __dmul_rn((double)cam.cx, xc[2])) < 0.0)) out[2] = false;
+      if (!(__dadd_rn(__dmul_rn((double)cam.fx, xc[0]), __dmul_rn(__dsub_rn((double)cam.cx, (double)cam.W), xc[2])) >= 0.0))
+        out[3] = false;
+      if (!(__dadd_rn(__dmul_rn((double)cam.fy, xc[1]), __dmul_rn((double)cam.cy, xc[2])) < 0.0)) out[4] = false;
+      if (!(__dadd_rn(__dmul_rn((double)cam.fy, xc[1]), __dmul_rn(__dsub_rn((double)cam.cy, (double)cam.H), xc[2])) >= 0.0))
+        out[5] = false;
+    }
+    if (out[0] || out[1] || out[2] || out[3] || out[4] || out[5]) {
+      w_out[i] = 0.0;
+      continue;
+    }
+    double xc[3];
+    cam_space_d(cam, c, xc);
+    double d = __ddiv_rn(fabs(__dsub_rn(xc[2], (double)cam.near_plane)), (double)cam.far_plane);
+    if (d < tau_d) d = tau_d;
+    w_out[i] = __ddiv_rn(t.weights[i], __dmul_rn(d, lf.f[l]));
+  }
+}
+
+// A sample is in view when the rasterizer's FP32 projection keeps it and it
+// lands in [0, W) x [0, H).
+__device__ __forceinline__ bool in_view(const Cam& c, const float* p) {
+  float u, v, d;
+  if (!project_point(c, p[0], p[1], p[2], u, v, d)) return false;
+  return u >= 0.0f && u < (float)c.W && v >= 0.0f && v < (float)c.H;
+}
+
+// One re-sampling round: every sample not in view draws a new leaf from the
+// CDF (Philox purpose 2 + 2 round) and a new position in it (3 + 2 round).
+__global__ void k_resample_round(const double* __restrict__ cdf, int64_t L, Cam cam, int64_t n, uint32_t k0,
+                                 uint32_t k1, uint32_t view_id, uint32_t round, const float* __restrict__ centers,
+                                 const int32_t* __restrict__ levels, float root_size, int32_t* __restrict__ leaf_out,
+                                 float* __restrict__ pos_out) {
+  const uint64_t Qi = (uint64_t)cdf[L - 1];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    if (in_view(cam, pos_out + 3 * k)) continue;
+    const U32x4 r = philox4x32_10((uint32_t)k, (uint32_t)((uint64_t)k >> 32), view_id, 2u + 2u * round, k0, k1);
+    const uint64_t b = ((uint64_t)(r.y & 0x1FFFFFu) << 32) | (uint64_t)r.x;
+    const uint64_t lo = b * Qi, hi = __umul64hi(b, Qi);
+    const double key = (double)((hi << 11) | (lo >> 53));
+    int64_t a = 0, z = L - 1;  // smallest i with cdf[i] > key
+    while (a < z) {
+      const int64_t mid = (a + z) >> 1;
+      if (cdf[mid] > key) z = mid; else a = mid + 1;
+    }
+    const int64_t leaf = a;
+    const U32x4 r2 = philox4x32_10((uint32_t)k, (uint32_t)((uint64_t)k >> 32), view_id, 3u + 2u * round, k0, k1);
+    const float edge = ldexpf(root_size, -levels[leaf]);
+    leaf_out[k] = (int32_t)leaf;
+    pos_out[3 * k + 0] = __fmaf_rn(__fsub_rn((float)(r2.x >> 8) * 0x1p-24f, 0.5f), edge, centers[3 * leaf + 0]);
+    pos_out[3 * k + 1] = __fmaf_rn(__fsub_rn((float)(r2.y >> 8) * 0x1p-24f, 0.5f), edge, centers[3 * leaf + 1]);
+    pos_out[3 * k + 2] = __fmaf_rn(__fsub_rn((float)(r2.z >> 8) * 0x1p-24f, 0.5f), edge, centers[3 * leaf + 2]);
+  }
+}
+
+__global__ void k_count_out_of_view(Cam cam, int64_t n, const float* __restrict__ pos, uint32_t* n_left) {
+  uint32_t c = 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    c += in_view(cam, pos + 3 * k) ? 0u : 1u;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(n_left, c);
+}
+
 int coarse_stride_log2(int64_t L) {
   int s = 0;
   while (ceil_div(L, (int64_t)1 << s) > kCoarse) ++s;
@@ -348,5 +452,59 @@ extern "C" inpc_status inpc_sample_octree(const inpc_octree* tree, uint64_t seed
   if (leaf_counts_out)
     INPC_CUDA(cudaMemcpyAsync(leaf_counts_out, ws.counts, sizeof(uint32_t) * L, cudaMemcpyDeviceToDevice, s),
               "copy counts");
+  return INPC_OK;
+}
+
+extern "C" inpc_status inpc_view_weights(const inpc_octree* tree, const inpc_camera* cam, double lambda_l,
+                                         double tau_d, double* w_out, inpc_stream_t stream) {
+  if (!tree || !cam || !w_out) return fail(INPC_ERR_INVALID_ARG, "inpc_view_weights: null pointer");
+  if (!tree->centers || !tree->levels || !tree->weights)
+    return fail(INPC_ERR_INVALID_ARG, "inpc_view_weights: null octree array");
+  if (tree->n_leaves < 1 || tree->n_leaves > (int64_t(1) << 24))
+    return fail(INPC_ERR_INVALID_ARG, "n_leaves must be in [1, 2^24]");
+  if (!(tree->root_size > 0.0f)) return fail(INPC_ERR_INVALID_ARG, "root_size must be positive");
+  if (!(cam->near_plane > 0.0f) || !(cam->far_plane > cam->near_plane) || cam->width < 1 || cam->height < 1)
+    return fail(INPC_ERR_INVALID_ARG, "bad camera");
+  if (!(tau_d > 0.0) || !std::isfinite(lambda_l)) return fail(INPC_ERR_INVALID_ARG, "need tau_d > 0, finite lambda_l");
+  LevelFactors lf;
+  for (int l = 0; l <= kMaxViewLevel; ++l) lf.f[l] = std::exp2((double)l * lambda_l);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t grid = std::min<int64_t>(ceil_div(tree->n_leaves, 256), (int64_t)device_sm_count() * 8);
+  INPC_TIMED("k_view_weights", s,
+             k_view_weights<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(*tree, to_cam(*cam), lf, tau_d,
+                                                                                w_out));
+  return check_launch("k_view_weights");
+}
+
+extern "C" inpc_status inpc_sample_octree_view(const inpc_octree* tree, const inpc_camera* cam, uint64_t seed,
+                                               uint32_t view_id, int64_t n_samples, int32_t max_rounds,
+                                               int32_t* leaf_idx_out, float* pos_out, uint32_t* n_left,
+                                               void* workspace, size_t workspace_bytes, inpc_stream_t stream) {
+  if (!cam) return fail(INPC_ERR_INVALID_ARG, "inpc_sample_octree_view: camera is null");
+  if (max_rounds < 0 || max_rounds > 64) return fail(INPC_ERR_INVALID_ARG, "max_rounds must be in [0, 64]");
+  if (!(cam->near_plane > 0.0f) || !(cam->far_plane > cam->near_plane) || cam->width < 1 || cam->height < 1)
+    return fail(INPC_ERR_INVALID_ARG, "bad camera");
+  INPC_TRY(inpc_sample_octree(tree, seed, view_id, n_samples, leaf_idx_out, pos_out, nullptr, workspace,
+                              workspace_bytes, stream));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const SampleWs ws = carve(workspace, tree->n_leaves);
+  const Cam c = to_cam(*cam);
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(n_samples, 256), (int64_t)device_sm_count() * 16));
+  if (n_samples > 0)
+    for (int32_t r = 0; r < max_rounds; ++r) {
+      INPC_TIMED("k_resample_round", s,
+                 k_resample_round<<<(unsigned)grid, 256, 0, s>>>(ws.cdf, tree->n_leaves, c, n_samples, k0, k1, view_id,
+                                                                (uint32_t)r, tree->centers, tree->levels,
+                                                                tree->root_size, leaf_idx_out, pos_out));
+      INPC_TRY(check_launch("k_resample_round"));
+    }
+  if (n_left) {
+    INPC_CUDA(cudaMemsetAsync(n_left, 0, sizeof(uint32_t), s), "clear n_left");
+    if (n_samples > 0) {
+      k_count_out_of_view<<<(unsigned)grid, 256, 0, s>>>(c, n_samples, pos_out, n_left);
+      INPC_TRY(check_launch("k_count_out_of_view"));
+    }
+  }
   return INPC_OK;
 }
