@@ -21,7 +21,10 @@
  *                 per-point blending weights of App. A.6), "Subdivision" and
  *                 "Pruning", App. A.4 leaf layout;
  *   view sampling Sec. 3.2 "Viewpoint-Specific Sampling" (Eq. 4) with App.
- *                 A.4 "Depth Calculation" and "Ensuring Sample Count".
+ *                 A.4 "Depth Calculation" and "Ensuring Sample Count";
+ *   pre-extraction Sec. 3.2 "Viewpoint-Independent Sampling" (Eq. 4 without
+ *                 visibility and depth, multinomial counts, 3D Halton
+ *                 positions).
  *
  * Readings where the paper is silent (all listed in the design notes):
  *   - leaf weights are quantised to integers q_i = rint(w_i / max w * 2^29)
@@ -63,7 +66,11 @@
  *   - a sample is in view when its FP32 position projects (the rasterizer's
  *     FP32 projection) strictly between near and far and into [0, W) x [0, H);
  *     round r of the re-sampling redraws every sample not in view, in place,
- *     with Philox purposes 2 + 2r (leaf) and 3 + 2r (position).
+ *     with Philox purposes 2 + 2r (leaf) and 3 + 2r (position);
+ *   - pre-extraction: the k-th sample of a leaf (k = 0, 1, ...) sits at
+ *     c + (h - 1/2) * edge with h the Halton point of index k + 1 in bases
+ *     (2, 3, 5) (index 0 would be the cube's corner); each radical inverse
+ *     is an exact fraction n / b^m divided once in FP64.
  */
 #include <math.h>
 #include <stdint.h>
@@ -920,5 +927,52 @@ int oracle_resample_view(const float* centers, const int32_t* levels, const doub
   for (int64_t j = 0; j < n; ++j) left += !oracle_point_in_view(cam, pos + 3 * j);
   *n_left = left;
   free(cdf);
+  return ORACLE_OK;
+}
+
+/* ------------------------------------------------------ pre-extraction --- */
+
+/* Eq. 4 without the visibility indicator and the depth: w_i = p_i / 2^(l_i lambda_l). */
+int oracle_level_weights(const int32_t* levels, const double* p, int64_t n_leaves, double lambda_l, double* w_out) {
+  for (int64_t i = 0; i < n_leaves; ++i) w_out[i] = p[i] / exp2((double)levels[i] * lambda_l);
+  return ORACLE_OK;
+}
+
+/* Radical inverse of i in base b (the van der Corput sequence): the digits
+ * of i mirrored behind the radix point, as the exact fraction num / b^m,
+ * divided once. */
+double oracle_radical_inverse(uint32_t b, uint64_t i) {
+  uint64_t num = 0, den = 1;
+  while (i > 0) {
+    num = num * b + i % b;
+    den *= b;
+    i /= b;
+  }
+  return (double)num / (double)den;
+}
+
+/* Viewpoint-independent pre-extraction: the per-leaf counts of N draws with
+ * replacement from w (the same draws as oracle_sample_octree: Philox purpose
+ * 0), leaf-grouped output, and Halton positions (see the readings above),
+ * rounded once from FP64 to FP32. */
+int oracle_sample_halton(const float* centers, const int32_t* levels, const double* w, int64_t n_leaves,
+                         double root_size, uint64_t seed, int64_t n_samples, int32_t* leaf_out, float* pos_out) {
+  int64_t* counts = (int64_t*)calloc((size_t)(n_leaves > 0 ? n_leaves : 1), sizeof(int64_t));
+  double* dummy = (double*)malloc(sizeof(double) * 3 * (size_t)(n_samples > 0 ? n_samples : 1));
+  if (!counts || !dummy) { free(counts); free(dummy); return ORACLE_ERR_NOMEM; }
+  int st = oracle_sample_octree(centers, levels, w, n_leaves, root_size, seed, 0u, n_samples, leaf_out, dummy,
+                                counts);
+  free(dummy);
+  if (st != ORACLE_OK) { free(counts); return st; }
+  int64_t slot = 0;
+  const uint32_t bases[3] = {2u, 3u, 5u};
+  for (int64_t i = 0; i < n_leaves; ++i) {
+    double edge = ldexp(root_size, -levels[i]);
+    for (int64_t k = 0; k < counts[i]; ++k, ++slot)
+      for (int d = 0; d < 3; ++d)
+        pos_out[3 * slot + d] =
+            (float)((double)centers[3 * i + d] + (oracle_radical_inverse(bases[d], (uint64_t)k + 1) - 0.5) * edge);
+  }
+  free(counts);
   return ORACLE_OK;
 }

@@ -113,6 +113,12 @@ def lib():
             L.oracle_resample_view.argtypes = [_P, _P, _P, C.c_int64, C.c_double, C.POINTER(OracleCamera),
                                                C.c_uint64, C.c_uint32, C.c_int64, C.c_int32, _P, _P, _P]
             L.oracle_resample_view.restype = C.c_int
+            L.oracle_level_weights.argtypes = [_P, _P, C.c_int64, C.c_double, _P]
+            L.oracle_level_weights.restype = C.c_int
+            L.oracle_radical_inverse.argtypes = [C.c_uint32, C.c_uint64]
+            L.oracle_radical_inverse.restype = C.c_double
+            L.oracle_sample_halton.argtypes = [_P, _P, _P, C.c_int64, C.c_double, C.c_uint64, C.c_int64, _P, _P]
+            L.oracle_sample_halton.restype = C.c_int
             _lib = L
     return _lib
 
@@ -472,3 +478,29 @@ def sample_view(tree, w, cam, seed: int, view_id: int, n_samples: int, max_round
     if st != 0:
         raise OracleError("resample_view failed (%d)" % st)
     return leaf, pos, int(left.value)
+
+
+# ------------------------------------------------------------ pre-extraction ---
+def level_weights(levels, p, lambda_l=0.5):
+    """Eq. 4 without visibility and depth: p / 2^(l lambda_l)."""
+    lv = _i32(levels)
+    pp = _f64(p)
+    w = np.zeros(lv.shape[0], np.float64)
+    lib().oracle_level_weights(_ptr(lv), _ptr(pp), lv.shape[0], float(lambda_l), _ptr(w))
+    return w
+
+
+def radical_inverse(base: int, i: int) -> float:
+    return float(lib().oracle_radical_inverse(int(base), int(i)))
+
+
+def sample_halton(tree, w, seed: int, n_samples: int):
+    """Viewpoint-independent pre-extraction: (leaf int32 [N], pos float32 [N,3])."""
+    c, lv, ww = _f32(tree.centers), _i32(tree.levels), _f64(w)
+    leaf = np.zeros(max(n_samples, 1), np.int32)
+    pos = np.zeros((max(n_samples, 1), 3), np.float32)
+    st = lib().oracle_sample_halton(_ptr(c), _ptr(lv), _ptr(ww), lv.shape[0], float(tree.root_size), int(seed),
+                                    n_samples, _ptr(leaf), _ptr(pos))
+    if st != 0:
+        raise OracleError("sample_halton failed (%d)" % st)
+    return leaf[:n_samples], pos[:n_samples]
