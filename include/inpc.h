@@ -327,6 +327,30 @@ inpc_status inpc_sample_octree_view(const inpc_octree* tree, const inpc_camera* 
                                     float* pos_out, uint32_t* n_left, void* workspace, size_t workspace_bytes,
                                     inpc_stream_t stream);
 
+/* Viewpoint-independent pre-extraction (Sec. 3.2): leaf weights of Eq. 4
+ * without the visibility indicator and the depth, w_i = p_i / 2^(l_i lambda_l)
+ * (2^(l lambda_l) by exp2 on the host for levels 0..63; other levels get 0),
+ * FP64.  tree->weights holds p; w_out float64 [n_leaves]. */
+inpc_status inpc_level_weights(const inpc_octree* tree, double lambda_l, double* w_out, inpc_stream_t stream);
+
+/* Pre-extraction sampling: the per-leaf counts of n_samples draws with
+ * replacement from tree->weights (exactly inpc_sample_octree's draws with
+ * view_id 0), leaf-grouped output, and the k-th sample of a leaf (k = 0, 1,
+ * ...) placed at c + (h - 1/2) root_size 2^-l with h the 3D Halton point of
+ * index k + 1 (radical inverses in bases 2, 3, 5, each the exact fraction
+ * n / b^m divided once in FP64), rounded once to FP32.  Arguments,
+ * workspace and errors as for inpc_sample_octree. */
+inpc_status inpc_sample_octree_halton(const inpc_octree* tree, uint64_t seed, int64_t n_samples,
+                                      int32_t* leaf_idx_out, float* pos_out, int32_t* leaf_counts_out,
+                                      void* workspace, size_t workspace_bytes, inpc_stream_t stream);
+
+/* Inference multisampling (Sec. 3.2): several point clouds are rasterized and
+ * their feature images averaged per pixel.  acc[i] += scale * image[i] for
+ * i < n_elems (FP32 accumulator; image of dtype INPC_F32 or INPC_BF16), one
+ * rounding per element (FMA). */
+inpc_status inpc_accumulate_image(const void* image, int32_t dtype, int64_t n_elems, float scale, float* acc,
+                                  inpc_stream_t stream);
+
 /* ======================================================================== */
 /* (d) Octree maintenance (Sec. 3.1 "Probability Updates", "Subdivision",   */
 /*     "Pruning"; App. A.4)                                                  */

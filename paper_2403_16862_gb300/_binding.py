@@ -43,6 +43,7 @@ DECLARED = [
     "inpc_rasterize_point_weights", "inpc_octree_update_workspace_size", "inpc_octree_update",
     "inpc_octree_refine_workspace_size", "inpc_octree_subdivide", "inpc_octree_prune",
     "inpc_view_weights", "inpc_sample_octree_view",
+    "inpc_level_weights", "inpc_sample_octree_halton", "inpc_accumulate_image",
 ]
 
 
@@ -125,6 +126,10 @@ def load(path: str = LIB_PATH):
         L.inpc_view_weights.argtypes = [C.POINTER(InpcOctree), C.POINTER(InpcCamera), C.c_double, C.c_double, _P, _P]
         L.inpc_sample_octree_view.argtypes = [C.POINTER(InpcOctree), C.POINTER(InpcCamera), C.c_uint64, C.c_uint32,
                                               C.c_int64, C.c_int32, _P, _P, _P, _P, C.c_size_t, _P]
+        L.inpc_level_weights.argtypes = [C.POINTER(InpcOctree), C.c_double, _P, _P]
+        L.inpc_sample_octree_halton.argtypes = [C.POINTER(InpcOctree), C.c_uint64, C.c_int64, _P, _P, _P, _P,
+                                                C.c_size_t, _P]
+        L.inpc_accumulate_image.argtypes = [_P, C.c_int32, C.c_int64, C.c_float, _P, _P]
         L.inpc_kernel_timer_enable.argtypes = [C.c_int]
         L.inpc_kernel_timer_read.argtypes = [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         for name in DECLARED:
@@ -286,3 +291,17 @@ def inpc_sample_octree_view(tree: InpcOctree, cam: InpcCamera, seed: int, view_i
                             workspace_bytes: int, stream: int):
     check(load().inpc_sample_octree_view(C.byref(tree), C.byref(cam), seed, view_id, n_samples, max_rounds,
                                          leaf_idx_out, pos_out, n_left, workspace, workspace_bytes, stream))
+
+
+def inpc_level_weights(tree: InpcOctree, lambda_l: float, w_out: int, stream: int):
+    check(load().inpc_level_weights(C.byref(tree), lambda_l, w_out, stream))
+
+
+def inpc_sample_octree_halton(tree: InpcOctree, seed: int, n_samples: int, leaf_idx_out: int, pos_out: int,
+                              leaf_counts_out, workspace: int, workspace_bytes: int, stream: int):
+    check(load().inpc_sample_octree_halton(C.byref(tree), seed, n_samples, leaf_idx_out, pos_out, leaf_counts_out,
+                                           workspace, workspace_bytes, stream))
+
+
+def inpc_accumulate_image(image: int, dtype: int, n_elems: int, scale: float, acc: int, stream: int):
+    check(load().inpc_accumulate_image(image, dtype, n_elems, scale, acc, stream))

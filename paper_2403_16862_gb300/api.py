@@ -359,3 +359,66 @@ def sample_octree_view(centers, levels, view_w, root_size: float, cam, seed: int
     B.inpc_sample_octree_view(tree, camera(cam), seed, view_id, n_samples, int(max_rounds), _ptr(leaf), _ptr(pos),
                               _ptr(n_left), ws.data_ptr(), ws.numel(), _stream())
     return leaf, pos, n_left
+
+
+# ---------------------------------------------------------- pre-extraction ---
+def level_weights(levels, p, lambda_l: float = 0.5, out=None):
+    """Eq. 4 without visibility and depth: p / 2^(l lambda_l) (float64 [L])."""
+    _need(levels, torch.int32, "levels")
+    _need(p, torch.float64, "p")
+    L = levels.shape[0]
+    w = out if out is not None else torch.empty(L, dtype=torch.float64, device=p.device)
+    tree = B.InpcOctree(None, _ptr(levels), _ptr(p), 1.0, L)
+    B.inpc_level_weights(tree, float(lambda_l), _ptr(w), _stream())
+    return w
+
+
+def sample_octree_halton(centers, levels, weights, root_size: float, seed: int, n_samples: int, ws=None, out=None):
+    """Viewpoint-independent pre-extraction: (leaf_idx int32 [N], pos float32 [N,3])."""
+    _need(centers, torch.float32, "centers")
+    _need(levels, torch.int32, "levels")
+    _need(weights, torch.float64, "weights")
+    L = levels.shape[0]
+    dev = centers.device
+    need = B.inpc_sample_workspace_size(L, n_samples)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    if out is None:
+        leaf = torch.empty(n_samples, dtype=torch.int32, device=dev)
+        pos = torch.empty(n_samples, 3, dtype=torch.float32, device=dev)
+    else:
+        leaf, pos = out
+    tree = B.InpcOctree(_ptr(centers), _ptr(levels), _ptr(weights), float(root_size), L)
+    B.inpc_sample_octree_halton(tree, seed, n_samples, _ptr(leaf), _ptr(pos), None, ws.data_ptr(), ws.numel(),
+                                _stream())
+    return leaf, pos
+
+
+def accumulate_image(image, acc, scale: float):
+    """acc += scale * image (FP32 accumulator; image FP32 or BF16)."""
+    _need(acc, torch.float32, "acc")
+    if image.shape != acc.shape or not image.is_contiguous():
+        raise ValueError("image and acc must have the same shape (contiguous)")
+    dt = B.INPC_BF16 if image.dtype == torch.bfloat16 else B.INPC_F32
+    if dt == B.INPC_F32:
+        _need(image, torch.float32, "image")
+    B.inpc_accumulate_image(image.data_ptr(), dt, image.numel(), float(scale), _ptr(acc), _stream())
+    return acc
+
+
+def multisample_render(tree_t, root_size: float, desc, table, cam, seed: int, n_samples: int, k: int = 4,
+                       opts=None, lambda_l: float = 0.5, max_rounds: int = 8):
+    """Inference multisampling (Sec. 3.2): k view-specific point clouds (view
+    ids 0..k-1 of this seed), each queried and rasterized, their feature
+    images averaged per pixel.  Returns the FP32 average image."""
+    c, l, p = tree_t
+    opts = opts or RasterOptions(n_channels=desc.n_levels * desc.n_feats, head_mode=True)
+    w = view_weights(c, l, p, root_size, cam, lambda_l=lambda_l)
+    acc = torch.zeros(cam.height, cam.width, opts.n_channels, dtype=torch.float32, device=c.device)
+    ws_r = None
+    for v in range(k):
+        _, pos, _ = sample_octree_view(c, l, w, root_size, cam, seed, v, n_samples, max_rounds=max_rounds)
+        h = query_hashgrid(desc, table, pos)
+        img, _, _, ws_r = rasterize_fwd(cam, opts, pos, h, ws=ws_r)
+        accumulate_image(img, acc, 1.0 / k)
+    return acc

@@ -13,6 +13,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace inpc {
@@ -388,6 +390,59 @@ __global__ void k_count_out_of_view(Cam cam, int64_t n, const float* __restrict_
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(n_left, c);
 }
 
+// --------------------------------------------------------- pre-extraction ---
+// Radical inverse of i in base b: the digits of i mirrored behind the radix
+// point, as the exact fraction num / b^m (both below 2^53 for i < 2^31 and
+// b <= 5), divided once.
+__device__ __forceinline__ double radical_inverse(uint32_t b, uint64_t i) {
+  uint64_t num = 0, den = 1;
+  while (i > 0) {
+    num = num * b + i % b;
+    den *= b;
+    i /= b;
+  }
+  return __ddiv_rn((double)num, (double)den);
+}
+
+// Slot k -> leaf (as k_place), then the Halton point of index (k - first
+// slot of the leaf) + 1 in bases (2, 3, 5) inside the leaf, rounded once
+// from FP64 to FP32.
+__global__ void __launch_bounds__(256) k_place_halton(const uint32_t* __restrict__ starts, int64_t L,
+                                                      int stride_log2, int64_t n, const float* __restrict__ centers,
+                                                      const int32_t* __restrict__ levels, float root_size,
+                                                      int32_t* __restrict__ leaf_out, float* __restrict__ pos_out) {
+  __shared__ uint32_t coarse[kCoarse];
+  int n_coarse;
+  load_coarse<uint32_t>(starts, L, stride_log2, coarse, n_coarse);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t leaf = upper_bound2<uint32_t>(starts, L, coarse, n_coarse, stride_log2, (uint32_t)k) - 1;
+    if (leaf < 0) leaf = 0;
+    const uint64_t j = (uint64_t)(k - (int64_t)starts[leaf]) + 1;
+    const double edge = ldexp((double)root_size, -levels[leaf]);
+    const uint32_t bases[3] = {2u, 3u, 5u};
+    leaf_out[k] = (int32_t)leaf;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      pos_out[3 * k + d] = __double2float_rn(
+          __dadd_rn((double)centers[3 * leaf + d], __dmul_rn(__dsub_rn(radical_inverse(bases[d], j), 0.5), edge)));
+  }
+}
+
+__global__ void k_level_weights(const int32_t* __restrict__ levels, const double* __restrict__ p, int64_t L,
+                                LevelFactors lf, double* __restrict__ w_out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L; i += (int64_t)gridDim.x * blockDim.x) {
+    const int l = levels[i];
+    w_out[i] = (l < 0 || l > kMaxViewLevel) ? 0.0 : __ddiv_rn(p[i], lf.f[l]);
+  }
+}
+
+// acc += scale * image (the per-pixel average of several feature images).
+template <class T>
+__global__ void k_accumulate(const T* __restrict__ img, float* __restrict__ acc, int64_t n, float scale) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc[i] = __fmaf_rn(scale, (float)img[i], acc[i]);
+}
+
 int coarse_stride_log2(int64_t L) {
   int s = 0;
   while (ceil_div(L, (int64_t)1 << s) > kCoarse) ++s;
@@ -408,10 +463,64 @@ extern "C" inpc_status inpc_sample_workspace_size(int64_t n_leaves, int64_t n_sa
   return INPC_OK;
 }
 
+namespace inpc {
+namespace {
+inpc_status sample_impl(const inpc_octree* tree, uint64_t seed, uint32_t view_id, int64_t n_samples,
+                        int32_t* leaf_idx_out, float* pos_out, int32_t* leaf_counts_out, void* workspace,
+                        size_t workspace_bytes, inpc_stream_t stream, bool halton);
+}  // namespace
+}  // namespace inpc
+
 extern "C" inpc_status inpc_sample_octree(const inpc_octree* tree, uint64_t seed, uint32_t view_id,
                                           int64_t n_samples, int32_t* leaf_idx_out, float* pos_out,
                                           int32_t* leaf_counts_out, void* workspace, size_t workspace_bytes,
                                           inpc_stream_t stream) {
+  return sample_impl(tree, seed, view_id, n_samples, leaf_idx_out, pos_out, leaf_counts_out, workspace,
+                     workspace_bytes, stream, false);
+}
+
+extern "C" inpc_status inpc_sample_octree_halton(const inpc_octree* tree, uint64_t seed, int64_t n_samples,
+                                                 int32_t* leaf_idx_out, float* pos_out, int32_t* leaf_counts_out,
+                                                 void* workspace, size_t workspace_bytes, inpc_stream_t stream) {
+  return sample_impl(tree, seed, 0u, n_samples, leaf_idx_out, pos_out, leaf_counts_out, workspace, workspace_bytes,
+                     stream, true);
+}
+
+extern "C" inpc_status inpc_level_weights(const inpc_octree* tree, double lambda_l, double* w_out,
+                                          inpc_stream_t stream) {
+  if (!tree || !tree->levels || !tree->weights || !w_out) return fail(INPC_ERR_INVALID_ARG, "null pointer");
+  if (tree->n_leaves < 1 || tree->n_leaves > (int64_t(1) << 24))
+    return fail(INPC_ERR_INVALID_ARG, "n_leaves must be in [1, 2^24]");
+  if (!std::isfinite(lambda_l)) return fail(INPC_ERR_INVALID_ARG, "lambda_l must be finite");
+  LevelFactors lf;
+  for (int l = 0; l <= kMaxViewLevel; ++l) lf.f[l] = std::exp2((double)l * lambda_l);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t grid = std::min<int64_t>(ceil_div(tree->n_leaves, 256), (int64_t)device_sm_count() * 8);
+  k_level_weights<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, s>>>(tree->levels, tree->weights, tree->n_leaves,
+                                                                       lf, w_out);
+  return check_launch("k_level_weights");
+}
+
+extern "C" inpc_status inpc_accumulate_image(const void* image, int32_t dtype, int64_t n_elems, float scale,
+                                             float* acc, inpc_stream_t stream) {
+  if (n_elems < 0) return fail(INPC_ERR_INVALID_ARG, "n_elems < 0");
+  if (n_elems == 0) return INPC_OK;
+  if (!image || !acc) return fail(INPC_ERR_INVALID_ARG, "null pointer");
+  if (dtype != INPC_F32 && dtype != INPC_BF16) return fail(INPC_ERR_UNSUPPORTED, "dtype must be INPC_F32 or INPC_BF16");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const unsigned grid =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n_elems, 256), (int64_t)device_sm_count() * 16));
+  if (dtype == INPC_F32) k_accumulate<float><<<grid, 256, 0, s>>>(static_cast<const float*>(image), acc, n_elems, scale);
+  else
+    k_accumulate<__nv_bfloat16><<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(image), acc, n_elems, scale);
+  return check_launch("k_accumulate");
+}
+
+namespace inpc {
+namespace {
+inpc_status sample_impl(const inpc_octree* tree, uint64_t seed, uint32_t view_id, int64_t n_samples,
+                        int32_t* leaf_idx_out, float* pos_out, int32_t* leaf_counts_out, void* workspace,
+                        size_t workspace_bytes, inpc_stream_t stream, bool halton) {
   if (!tree) return fail(INPC_ERR_INVALID_ARG, "inpc_sample_octree: tree is null");
   const int64_t L = tree->n_leaves;
   size_t need = 0;
@@ -444,16 +553,25 @@ extern "C" inpc_status inpc_sample_octree(const inpc_octree* tree, uint64_t seed
   INPC_TRY((scan<uint32_t, CountLoad, false>(CountLoad{ws.counts}, L, ws.starts, ws.count_tops, s)));
   if (n_samples > 0) {
     const int64_t grid = std::min<int64_t>(ceil_div(n_samples, 256), (int64_t)sms * 16);
-    INPC_TIMED("k_place", s,
-               k_place<<<(unsigned)grid, 256, 0, s>>>(ws.starts, L, sl, n_samples, k0, k1, view_id, tree->centers,
-                                                      tree->levels, tree->root_size, leaf_idx_out, pos_out));
-    INPC_TRY(check_launch("k_place"));
+    if (halton) {
+      INPC_TIMED("k_place_halton", s,
+                 k_place_halton<<<(unsigned)grid, 256, 0, s>>>(ws.starts, L, sl, n_samples, tree->centers,
+                                                               tree->levels, tree->root_size, leaf_idx_out, pos_out));
+      INPC_TRY(check_launch("k_place_halton"));
+    } else {
+      INPC_TIMED("k_place", s,
+                 k_place<<<(unsigned)grid, 256, 0, s>>>(ws.starts, L, sl, n_samples, k0, k1, view_id, tree->centers,
+                                                        tree->levels, tree->root_size, leaf_idx_out, pos_out));
+      INPC_TRY(check_launch("k_place"));
+    }
   }
   if (leaf_counts_out)
     INPC_CUDA(cudaMemcpyAsync(leaf_counts_out, ws.counts, sizeof(uint32_t) * L, cudaMemcpyDeviceToDevice, s),
               "copy counts");
   return INPC_OK;
 }
+}  // namespace
+}  // namespace inpc
 
 extern "C" inpc_status inpc_view_weights(const inpc_octree* tree, const inpc_camera* cam, double lambda_l,
                                          double tau_d, double* w_out, inpc_stream_t stream) {
