@@ -24,7 +24,11 @@
  *                 A.4 "Depth Calculation" and "Ensuring Sample Count";
  *   pre-extraction Sec. 3.2 "Viewpoint-Independent Sampling" (Eq. 4 without
  *                 visibility and depth, multinomial counts, 3D Halton
- *                 positions).
+ *                 positions);
+ *   SH head       Sec. 3.3: spherical contraction of the query positions,
+ *                 opacity from the first feature, degree-2 spherical
+ *                 harmonics on the next 36 features giving a 4D
+ *                 view-dependent color per point, and its derivative.
  *
  * Readings where the paper is silent (all listed in the design notes):
  *   - leaf weights are quantised to integers q_i = rint(w_i / max w * 2^29)
@@ -70,7 +74,16 @@
  *   - pre-extraction: the k-th sample of a leaf (k = 0, 1, ...) sits at
  *     c + (h - 1/2) * edge with h the Halton point of index k + 1 in bases
  *     (2, 3, 5) (index 0 would be the cube's corner); each radical inverse
- *     is an exact fraction n / b^m divided once in FP64.
+ *     is an exact fraction n / b^m divided once in FP64;
+ *   - contraction (mip-NeRF 360): y = (x - center) / radius, contract(y) = y
+ *     for |y| <= 1, else (2 - 1/|y|) y / |y|; query position contract(y)/4 +
+ *     1/2 in [0, 1]^3.  Evaluated in FP32 with a fixed operation order on both
+ *     sides, since it decides the grid cells;
+ *   - SH head: direction d = (x - camera center) / |x - camera center|; real
+ *     orthonormal SH of degree 2, Y_0 = sqrt(1/(4 pi)); Y_1..3 = sqrt(3/(4 pi))
+ *     (y, z, x); Y_4..8 = sqrt(15/(4 pi)) xy, sqrt(15/(4 pi)) yz,
+ *     sqrt(5/(16 pi)) (3 z^2 - 1), sqrt(15/(4 pi)) xz, sqrt(15/(16 pi))
+ *     (x^2 - y^2); color channel c = sum_k Y_k(d) h[1 + 9 c + k].
  */
 #include <math.h>
 #include <stdint.h>
@@ -974,5 +987,91 @@ int oracle_sample_halton(const float* centers, const int32_t* levels, const doub
             (float)((double)centers[3 * i + d] + (oracle_radical_inverse(bases[d], (uint64_t)k + 1) - 0.5) * edge);
   }
   free(counts);
+  return ORACLE_OK;
+}
+
+/* --------------------------------------------------------------- SH head --- */
+
+/* Spherical contraction (mip-NeRF 360) in FP32, fixed order:
+ * y = (x - center) / radius; r = sqrt(fma(y2, y2, fma(y1, y1, y0 * y0)));
+ * s = r <= 1 ? 1 : (2 - 1 / r) / r; q = fma(y * s, 1/4, 1/2). */
+int oracle_contract(const float* pos, int64_t n, const float* center, float radius, float* out) {
+  for (int64_t p = 0; p < n; ++p) {
+    float y[3];
+    for (int d = 0; d < 3; ++d) y[d] = (pos[3 * p + d] - center[d]) / radius;
+    float r = sqrtf(fmaf(y[2], y[2], fmaf(y[1], y[1], y[0] * y[0])));
+    float sc = 1.0f;
+    if (r > 1.0f) sc = (2.0f - 1.0f / r) / r;
+    for (int d = 0; d < 3; ++d) out[3 * p + d] = fmaf(y[d] * sc, 0.25f, 0.5f);
+  }
+  return ORACLE_OK;
+}
+
+/* The 9 real orthonormal SH of degree <= 2 at the unit vector d. */
+void oracle_sh_basis(const double* d, double* Y) {
+  const double pi = acos(-1.0);
+  double x = d[0], y = d[1], z = d[2];
+  Y[0] = sqrt(1.0 / (4.0 * pi));
+  double c1 = sqrt(3.0 / (4.0 * pi));
+  Y[1] = c1 * y;
+  Y[2] = c1 * z;
+  Y[3] = c1 * x;
+  double c2 = sqrt(15.0 / (4.0 * pi));
+  Y[4] = c2 * x * y;
+  Y[5] = c2 * y * z;
+  Y[6] = sqrt(5.0 / (16.0 * pi)) * (3.0 * z * z - 1.0);
+  Y[7] = c2 * x * z;
+  Y[8] = sqrt(15.0 / (16.0 * pi)) * (x * x - y * y);
+}
+
+static void view_dir(const oracle_camera* cam, const float* p, double* d) {
+  /* camera center o = -R^T t */
+  double o[3];
+  for (int k = 0; k < 3; ++k)
+    o[k] = -((double)cam->R[k] * cam->t[0] + (double)cam->R[3 + k] * cam->t[1] + (double)cam->R[6 + k] * cam->t[2]);
+  double v[3] = {(double)p[0] - o[0], (double)p[1] - o[1], (double)p[2] - o[2]};
+  double len = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  for (int k = 0; k < 3; ++k) d[k] = len > 0.0 ? v[k] / len : (k == 2 ? 1.0 : 0.0);
+}
+
+/* Head forward (Sec. 3.3): alpha = 1 - exp(-exp(h0)); color_c = sum_k Y_k h[1 + 9c + k]
+ * (c < 4); abs_out (optional) = sum_k |Y_k h[1 + 9c + k]|.  h is [n, F], F >= 37. */
+int oracle_sh_head_fwd(const oracle_camera* cam, const float* pos, const double* h, int64_t n, int32_t F,
+                       double* alpha, double* color, double* abs_out) {
+  if (F < 37) return ORACLE_ERR_ARG;
+  for (int64_t p = 0; p < n; ++p) {
+    double d[3], Y[9];
+    view_dir(cam, pos + 3 * p, d);
+    oracle_sh_basis(d, Y);
+    alpha[p] = 1.0 - exp(-exp(h[p * F]));
+    for (int c = 0; c < 4; ++c) {
+      double s = 0.0, a = 0.0;
+      for (int k = 0; k < 9; ++k) {
+        s += Y[k] * h[p * F + 1 + 9 * c + k];
+        a += fabs(Y[k] * h[p * F + 1 + 9 * c + k]);
+      }
+      color[4 * p + c] = s;
+      if (abs_out) abs_out[4 * p + c] = a;
+    }
+  }
+  return ORACLE_OK;
+}
+
+/* Head backward: dh[0] = d_alpha exp(h0) exp(-exp(h0)); dh[1 + 9c + k] =
+ * Y_k d_color_c; every other channel 0.  abs_out (optional) = |terms|. */
+int oracle_sh_head_bwd(const oracle_camera* cam, const float* pos, const double* h, int64_t n, int32_t F,
+                       const double* d_alpha, const double* d_color, double* dh, double* abs_out) {
+  if (F < 37) return ORACLE_ERR_ARG;
+  for (int64_t p = 0; p < n; ++p) {
+    double d[3], Y[9];
+    view_dir(cam, pos + 3 * p, d);
+    oracle_sh_basis(d, Y);
+    for (int f = 0; f < F; ++f) dh[p * F + f] = 0.0;
+    double e = exp(h[p * F]);
+    dh[p * F] = d_alpha[p] * e * exp(-e);
+    for (int c = 0; c < 4; ++c)
+      for (int k = 0; k < 9; ++k) dh[p * F + 1 + 9 * c + k] = Y[k] * d_color[4 * p + c];
+    if (abs_out) for (int f = 0; f < F; ++f) abs_out[p * F + f] = fabs(dh[p * F + f]);
+  }
   return ORACLE_OK;
 }

@@ -119,6 +119,14 @@ def lib():
             L.oracle_radical_inverse.restype = C.c_double
             L.oracle_sample_halton.argtypes = [_P, _P, _P, C.c_int64, C.c_double, C.c_uint64, C.c_int64, _P, _P]
             L.oracle_sample_halton.restype = C.c_int
+            L.oracle_contract.argtypes = [_P, C.c_int64, _P, C.c_float, _P]
+            L.oracle_contract.restype = C.c_int
+            L.oracle_sh_basis.argtypes = [_P, _P]
+            L.oracle_sh_basis.restype = None
+            L.oracle_sh_head_fwd.argtypes = [C.POINTER(OracleCamera), _P, _P, C.c_int64, C.c_int32, _P, _P, _P]
+            L.oracle_sh_head_fwd.restype = C.c_int
+            L.oracle_sh_head_bwd.argtypes = [C.POINTER(OracleCamera), _P, _P, C.c_int64, C.c_int32, _P, _P, _P, _P]
+            L.oracle_sh_head_bwd.restype = C.c_int
             _lib = L
     return _lib
 
@@ -504,3 +512,47 @@ def sample_halton(tree, w, seed: int, n_samples: int):
     if st != 0:
         raise OracleError("sample_halton failed (%d)" % st)
     return leaf[:n_samples], pos[:n_samples]
+
+
+# ------------------------------------------------------------------- SH head ---
+def contract(pos, center, radius):
+    """Spherical contraction into [0, 1]^3 (FP32, the kernel's operation order)."""
+    p = _f32(pos)
+    c = _f32(center)
+    out = np.zeros_like(p)
+    lib().oracle_contract(_ptr(p), p.shape[0], _ptr(c), float(radius), _ptr(out))
+    return out
+
+
+def sh_basis(d):
+    dd = _f64(d)
+    Y = np.zeros(9, np.float64)
+    lib().oracle_sh_basis(_ptr(dd), _ptr(Y))
+    return Y
+
+
+def sh_head_fwd(cam, pos, h, with_abs=False):
+    """(alpha [N], color [N,4][, abs [N,4]]) of the degree-2 SH head."""
+    p = _f32(pos)
+    hh = _f64(h)
+    n, F = hh.shape
+    a = np.zeros(n, np.float64)
+    col = np.zeros((n, 4), np.float64)
+    ab = np.zeros((n, 4), np.float64) if with_abs else None
+    cs = camera_struct(cam)
+    if lib().oracle_sh_head_fwd(C.byref(cs), _ptr(p), _ptr(hh), n, F, _ptr(a), _ptr(col), _ptr(ab)) != 0:
+        raise OracleError("sh_head_fwd failed")
+    return (a, col, ab) if with_abs else (a, col)
+
+
+def sh_head_bwd(cam, pos, h, d_alpha, d_color, with_abs=False):
+    p = _f32(pos)
+    hh = _f64(h)
+    n, F = hh.shape
+    da, dc = _f64(d_alpha), _f64(d_color)
+    dh = np.zeros((n, F), np.float64)
+    ab = np.zeros((n, F), np.float64) if with_abs else None
+    cs = camera_struct(cam)
+    if lib().oracle_sh_head_bwd(C.byref(cs), _ptr(p), _ptr(hh), n, F, _ptr(da), _ptr(dc), _ptr(dh), _ptr(ab)) != 0:
+        raise OracleError("sh_head_bwd failed")
+    return (dh, ab) if with_abs else dh
