@@ -352,6 +352,40 @@ inpc_status inpc_accumulate_image(const void* image, int32_t dtype, int64_t n_el
                                   inpc_stream_t stream);
 
 /* ======================================================================== */
+/* (e) View-dependent head (Sec. 3.3)                                        */
+/* ======================================================================== */
+
+/* Spherical contraction of the query positions (Sec. 3.3, mip-NeRF 360):
+ * y = (x - center) / radius; contract(y) = y for |y| <= 1, else
+ * (2 - 1/|y|) y / |y|; out = contract(y) / 4 + 1/2, in [0, 1]^3.  FP32 with a
+ * fixed operation order: y_d = (x_d - c_d) / radius;
+ * r = sqrt(fma(y2, y2, fma(y1, y1, y0 * y0))); s = (2 - 1/r) / r for r > 1;
+ * out_d = fma(y_d * s, 1/4, 1/2).  pos, out float32 [n, 3] (may alias);
+ * center float32 [3] (host). */
+inpc_status inpc_contract_positions(const float* pos, int64_t n, const float* center, float radius, float* out,
+                                   inpc_stream_t stream);
+
+/* Appearance head: alpha_h = 1 - exp(-exp(h0)) and a 4D view-dependent
+ * color from degree-2 real orthonormal spherical harmonics of the viewing
+ * direction d = (x - o) / |x - o| (o the camera center):
+ *   color_c = sum_{k<9} Y_k(d) h[1 + 9 c + k],  c < 4
+ * with Y_0 = sqrt(1/4pi), Y_1..3 = sqrt(3/4pi) (y, z, x), Y_4..8 =
+ * sqrt(15/4pi) xy, sqrt(15/4pi) yz, sqrt(5/16pi)(3z^2 - 1), sqrt(15/4pi) xz,
+ * sqrt(15/16pi)(x^2 - y^2).  h [n, n_channels] of h_dtype (n_channels >= 37:
+ * 1 opacity + 36 SH coefficients; further channels unused); alpha_out
+ * float32 [n]; color_out float32 [n, 4] (16-byte aligned).  The outputs feed
+ * inpc_rasterize_fwd in INPC_OPACITY_GIVEN mode with 4 channels. */
+inpc_status inpc_sh_head_fwd(const inpc_camera* cam, const float* pos, const void* h, int32_t h_dtype, int64_t n,
+                             int32_t n_channels, float* alpha_out, float* color_out, inpc_stream_t stream);
+
+/* Derivative of inpc_sh_head_fwd: dh[0] = d_alpha exp(h0) exp(-exp(h0)),
+ * dh[1 + 9c + k] = Y_k(d) d_color_c, every other channel 0; dh_out float32
+ * [n, n_channels], written. */
+inpc_status inpc_sh_head_bwd(const inpc_camera* cam, const float* pos, const void* h, int32_t h_dtype, int64_t n,
+                             int32_t n_channels, const float* d_alpha, const float* d_color, float* dh_out,
+                             inpc_stream_t stream);
+
+/* ======================================================================== */
 /* (d) Octree maintenance (Sec. 3.1 "Probability Updates", "Subdivision",   */
 /*     "Pruning"; App. A.4)                                                  */
 /* ======================================================================== */

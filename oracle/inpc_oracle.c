@@ -1024,6 +1024,25 @@ void oracle_sh_basis(const double* d, double* Y) {
   Y[8] = sqrt(15.0 / (16.0 * pi)) * (x * x - y * y);
 }
 
+/* Absolute-term version of the basis for the condition-aware tolerance:
+ * every polynomial with its terms taken in absolute value (3z^2 + 1,
+ * x^2 + y^2), so that cancellation inside a basis function is covered. */
+static void sh_basis_abs(const double* d, double* Y) {
+  const double pi = acos(-1.0);
+  double x = fabs(d[0]), y = fabs(d[1]), z = fabs(d[2]);
+  Y[0] = sqrt(1.0 / (4.0 * pi));
+  double c1 = sqrt(3.0 / (4.0 * pi));
+  Y[1] = c1 * y;
+  Y[2] = c1 * z;
+  Y[3] = c1 * x;
+  double c2 = sqrt(15.0 / (4.0 * pi));
+  Y[4] = c2 * x * y;
+  Y[5] = c2 * y * z;
+  Y[6] = sqrt(5.0 / (16.0 * pi)) * (3.0 * z * z + 1.0);
+  Y[7] = c2 * x * z;
+  Y[8] = sqrt(15.0 / (16.0 * pi)) * (x * x + y * y);
+}
+
 static void view_dir(const oracle_camera* cam, const float* p, double* d) {
   /* camera center o = -R^T t */
   double o[3];
@@ -1035,20 +1054,22 @@ static void view_dir(const oracle_camera* cam, const float* p, double* d) {
 }
 
 /* Head forward (Sec. 3.3): alpha = 1 - exp(-exp(h0)); color_c = sum_k Y_k h[1 + 9c + k]
- * (c < 4); abs_out (optional) = sum_k |Y_k h[1 + 9c + k]|.  h is [n, F], F >= 37. */
+ * (c < 4); abs_out (optional) = sum_k |Y|_k |h[1 + 9c + k]| with the
+ * absolute-term basis |Y| (see sh_basis_abs).  h is [n, F], F >= 37. */
 int oracle_sh_head_fwd(const oracle_camera* cam, const float* pos, const double* h, int64_t n, int32_t F,
                        double* alpha, double* color, double* abs_out) {
   if (F < 37) return ORACLE_ERR_ARG;
   for (int64_t p = 0; p < n; ++p) {
-    double d[3], Y[9];
+    double d[3], Y[9], Ya[9];
     view_dir(cam, pos + 3 * p, d);
     oracle_sh_basis(d, Y);
+    sh_basis_abs(d, Ya);
     alpha[p] = 1.0 - exp(-exp(h[p * F]));
     for (int c = 0; c < 4; ++c) {
       double s = 0.0, a = 0.0;
       for (int k = 0; k < 9; ++k) {
         s += Y[k] * h[p * F + 1 + 9 * c + k];
-        a += fabs(Y[k] * h[p * F + 1 + 9 * c + k]);
+        a += Ya[k] * fabs(h[p * F + 1 + 9 * c + k]);
       }
       color[4 * p + c] = s;
       if (abs_out) abs_out[4 * p + c] = a;
@@ -1058,20 +1079,27 @@ int oracle_sh_head_fwd(const oracle_camera* cam, const float* pos, const double*
 }
 
 /* Head backward: dh[0] = d_alpha exp(h0) exp(-exp(h0)); dh[1 + 9c + k] =
- * Y_k d_color_c; every other channel 0.  abs_out (optional) = |terms|. */
+ * Y_k d_color_c; every other channel 0.  abs_out (optional): |dh[0]| and
+ * |Y|_k |d_color_c|. */
 int oracle_sh_head_bwd(const oracle_camera* cam, const float* pos, const double* h, int64_t n, int32_t F,
                        const double* d_alpha, const double* d_color, double* dh, double* abs_out) {
   if (F < 37) return ORACLE_ERR_ARG;
   for (int64_t p = 0; p < n; ++p) {
-    double d[3], Y[9];
+    double d[3], Y[9], Ya[9];
     view_dir(cam, pos + 3 * p, d);
     oracle_sh_basis(d, Y);
+    sh_basis_abs(d, Ya);
     for (int f = 0; f < F; ++f) dh[p * F + f] = 0.0;
     double e = exp(h[p * F]);
     dh[p * F] = d_alpha[p] * e * exp(-e);
     for (int c = 0; c < 4; ++c)
       for (int k = 0; k < 9; ++k) dh[p * F + 1 + 9 * c + k] = Y[k] * d_color[4 * p + c];
-    if (abs_out) for (int f = 0; f < F; ++f) abs_out[p * F + f] = fabs(dh[p * F + f]);
+    if (abs_out) {
+      for (int f = 0; f < F; ++f) abs_out[p * F + f] = 0.0;
+      abs_out[p * F] = fabs(dh[p * F]);
+      for (int c = 0; c < 4; ++c)
+        for (int k = 0; k < 9; ++k) abs_out[p * F + 1 + 9 * c + k] = Ya[k] * fabs(d_color[4 * p + c]);
+    }
   }
   return ORACLE_OK;
 }

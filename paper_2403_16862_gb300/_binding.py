@@ -44,6 +44,7 @@ DECLARED = [
     "inpc_octree_refine_workspace_size", "inpc_octree_subdivide", "inpc_octree_prune",
     "inpc_view_weights", "inpc_sample_octree_view",
     "inpc_level_weights", "inpc_sample_octree_halton", "inpc_accumulate_image",
+    "inpc_contract_positions", "inpc_sh_head_fwd", "inpc_sh_head_bwd",
 ]
 
 
@@ -130,6 +131,10 @@ def load(path: str = LIB_PATH):
         L.inpc_sample_octree_halton.argtypes = [C.POINTER(InpcOctree), C.c_uint64, C.c_int64, _P, _P, _P, _P,
                                                 C.c_size_t, _P]
         L.inpc_accumulate_image.argtypes = [_P, C.c_int32, C.c_int64, C.c_float, _P, _P]
+        L.inpc_contract_positions.argtypes = [_P, C.c_int64, _P, C.c_float, _P, _P]
+        L.inpc_sh_head_fwd.argtypes = [C.POINTER(InpcCamera), _P, _P, C.c_int32, C.c_int64, C.c_int32, _P, _P, _P]
+        L.inpc_sh_head_bwd.argtypes = [C.POINTER(InpcCamera), _P, _P, C.c_int32, C.c_int64, C.c_int32, _P, _P, _P,
+                                       _P]
         L.inpc_kernel_timer_enable.argtypes = [C.c_int]
         L.inpc_kernel_timer_read.argtypes = [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         for name in DECLARED:
@@ -305,3 +310,18 @@ def inpc_sample_octree_halton(tree: InpcOctree, seed: int, n_samples: int, leaf_
 
 def inpc_accumulate_image(image: int, dtype: int, n_elems: int, scale: float, acc: int, stream: int):
     check(load().inpc_accumulate_image(image, dtype, n_elems, scale, acc, stream))
+
+
+def inpc_contract_positions(pos: int, n: int, center, radius: float, out: int, stream: int):
+    c = (C.c_float * 3)(*[float(x) for x in center])
+    check(load().inpc_contract_positions(pos, n, C.cast(c, C.c_void_p), radius, out, stream))
+
+
+def inpc_sh_head_fwd(cam: InpcCamera, pos: int, h: int, h_dtype: int, n: int, n_channels: int, alpha_out: int,
+                     color_out: int, stream: int):
+    check(load().inpc_sh_head_fwd(C.byref(cam), pos, h, h_dtype, n, n_channels, alpha_out, color_out, stream))
+
+
+def inpc_sh_head_bwd(cam: InpcCamera, pos: int, h: int, h_dtype: int, n: int, n_channels: int, d_alpha: int,
+                     d_color: int, dh_out: int, stream: int):
+    check(load().inpc_sh_head_bwd(C.byref(cam), pos, h, h_dtype, n, n_channels, d_alpha, d_color, dh_out, stream))

@@ -422,3 +422,48 @@ def multisample_render(tree_t, root_size: float, desc, table, cam, seed: int, n_
         img, _, _, ws_r = rasterize_fwd(cam, opts, pos, h, ws=ws_r)
         accumulate_image(img, acc, 1.0 / k)
     return acc
+
+
+# ------------------------------------------------------ view-dependent head ---
+def contract_positions(pos, center, radius: float, out=None):
+    """Spherical contraction into [0, 1]^3 (the grid query's domain)."""
+    _need(pos, torch.float32, "pos")
+    o = out if out is not None else torch.empty_like(pos)
+    B.inpc_contract_positions(_ptr(pos), pos.shape[0], center, float(radius), _ptr(o), _stream())
+    return o
+
+
+def sh_head_fwd(cam, pos, h):
+    """(alpha_h float32 [N], color float32 [N,4]) of the degree-2 SH head."""
+    n, F = h.shape
+    dt = B.INPC_BF16 if h.dtype == torch.bfloat16 else B.INPC_F32
+    alpha = torch.empty(n, dtype=torch.float32, device=h.device)
+    color = torch.empty(n, 4, dtype=torch.float32, device=h.device)
+    B.inpc_sh_head_fwd(camera(cam), _ptr(pos), h.data_ptr(), dt, n, F, _ptr(alpha), _ptr(color), _stream())
+    return alpha, color
+
+
+def sh_head_bwd(cam, pos, h, d_alpha, d_color):
+    """dh float32 [N, F] of the SH head."""
+    n, F = h.shape
+    dt = B.INPC_BF16 if h.dtype == torch.bfloat16 else B.INPC_F32
+    dh = torch.empty(n, F, dtype=torch.float32, device=h.device)
+    B.inpc_sh_head_bwd(camera(cam), _ptr(pos), h.data_ptr(), dt, n, F, _ptr(d_alpha), _ptr(d_color), _ptr(dh),
+                       _stream())
+    return dh
+
+
+def render_view_sh(pos, desc, table, cam, center, radius: float, d_image=None, grad_table=None):
+    """The view-dependent variant of the path: contraction -> grid query ->
+    SH head -> rasterizer (4 channels, given opacities); with d_image also the
+    backward into grad_table.  Returns (image, T_final, n_contrib)."""
+    q = contract_positions(pos, center, radius)
+    h = query_hashgrid(desc, table, q)
+    alpha, color = sh_head_fwd(cam, pos, h)
+    opts = RasterOptions(n_channels=4, head_mode=False)
+    img, T, nc, ws = rasterize_fwd(cam, opts, pos, color, alpha)
+    if d_image is not None:
+        d_op, d_col = rasterize_bwd(cam, opts, pos, color, alpha, T, nc, d_image, ws)
+        dh = sh_head_bwd(cam, pos, h, d_op, d_col)
+        query_hashgrid_bwd(desc, q, dh, grad_table)
+    return img, T, nc
