@@ -1050,6 +1050,7 @@ struct HeavySmem {
   float warp_tot[kWarps];
   float prev[kThreads];
   float red[kThreads];
+  float red64[kWarps][64];  // per-warp partial colors of the 64-channel slot blend
   float carry;
   int stop;
 };
@@ -1122,10 +1123,74 @@ __device__ int cta_transmittance(const RP& P, AlphaAt alpha_at, int m, TStore t_
   return n;
 }
 
+// 64 channels on the CTA path: the 8 warps x 8 fragment slots take 64
+// fragments per pass (lane: slot f = lane / 4, part q = lane % 4, 16
+// channels), accumulate per slot, reduce-scatter within the warp and sum
+// the 8 warps' partial colors in shared memory.
+template <class FT, class KeyAt, class AlphaAt, class TLoad>
+__device__ void blend_fwd_cta_slots(const RP& P, KeyAt key_at, AlphaAt alpha_at, TLoad t_load, int n, float T,
+                                    long long pix, const FT* __restrict__ feat, FT* __restrict__ image,
+                                    float* __restrict__ T_final, int32_t* __restrict__ n_contrib, HeavySmem& H) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int q = lane & 3, f = lane >> 2;
+  float acc[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) acc[e] = 0.f;
+#pragma unroll 2
+  for (int k = 8 * wid + f; k < n; k += 64) {
+    const float wk = __fmul_rn(t_load(k), alpha_at(k));
+    float c[16];
+    Slot64<FT>::load(feat + 64ll * (long long)(key_at(k) & kIdMask), q, c);
+    if (P.head && q == 0) c[0] = 1.0f;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[e] = __fmaf_rn(wk, c[e], acc[e]);
+  }
+  const int h4 = (lane >> 4) & 1, h3 = (lane >> 3) & 1, h2 = (lane >> 2) & 1;
+  float r8[8], r4[4], r2[2];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float send = h4 ? acc[k] : acc[8 + k];
+    const float keep = h4 ? acc[8 + k] : acc[k];
+    r8[k] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, 16));
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float send = h3 ? r8[k] : r8[4 + k];
+    const float keep = h3 ? r8[4 + k] : r8[k];
+    r4[k] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, 8));
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = h2 ? r4[k] : r4[2 + k];
+    const float keep = h2 ? r4[2 + k] : r4[k];
+    r2[k] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, 4));
+  }
+  const int ch0 = Slot64<FT>::channel(q, 8 * h4 + 4 * h3 + 2 * h2);
+  __syncthreads();
+  H.red64[wid][ch0] = r2[0];
+  H.red64[wid][ch0 + 1] = r2[1];
+  __syncthreads();
+  if (threadIdx.x < 64) {  // warps 0 and 1, whole
+    float sum = 0.f;
+    for (int w = 0; w < kWarps; ++w) sum = __fadd_rn(sum, H.red64[w][threadIdx.x]);
+    const float other = __shfl_down_sync(0xffffffffu, sum, 1);
+    if (threadIdx.x % 2 == 0) Slot64<FT>::store2(image + pix * 64, threadIdx.x, sum, other);
+  }
+  if (threadIdx.x == 0) {
+    T_final[pix] = T;
+    n_contrib[pix] = n;
+  }
+  __syncthreads();
+}
+
 template <int V, int GA, class FT, class KeyAt, class AlphaAt, class TLoad>
 __device__ void blend_fwd_cta(const RP& P, KeyAt key_at, AlphaAt alpha_at, TLoad t_load, int n, float T, long long pix,
                               const FT* __restrict__ feat, FT* __restrict__ image, float* __restrict__ T_final,
                               int32_t* __restrict__ n_contrib, HeavySmem& H) {
+  if constexpr (V == 2 && GA == 32) {  // F = 64
+    blend_fwd_cta_slots<FT>(P, key_at, alpha_at, t_load, n, T, pix, feat, image, T_final, n_contrib, H);
+    return;
+  }
   constexpr int kGroups = kThreads / GA;
   const Group<GA> G;
   const int group = threadIdx.x / GA;
