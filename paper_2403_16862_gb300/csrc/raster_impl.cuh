@@ -1646,9 +1646,24 @@ unsigned point_grid(long long n) {
   return (unsigned)std::max<long long>(1, std::min<long long>(ceil_div(n, 256), cap));
 }
 
+// Raises a kernel's dynamic shared-memory limit once per device (the
+// attribute belongs to the kernel on the current device).
+struct SmemOnce {
+  std::mutex mu;
+  uint64_t done = 0;  // bit d: set on device d
+};
+
 template <class K>
-void set_smem(K kernel, size_t bytes, std::once_flag& once) {
-  std::call_once(once, [&] { cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes); });
+inpc_status set_smem(K kernel, size_t bytes, SmemOnce& once) {
+  int dev = 0;
+  INPC_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(once.mu);
+  const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+  if (bit && (once.done & bit)) return INPC_OK;
+  INPC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
+            "cudaFuncSetAttribute");
+  once.done |= bit;
+  return INPC_OK;
 }
 
 // Forward binning: per-pixel counts, offsets, buckets (keys and alphas),
@@ -1681,8 +1696,8 @@ template <int V, int GA, class FT>
 inpc_status launch_fwd(const RP& P, const float* pos, const float* opacity, const FT* feat, const RasterWs& ws,
                        FT* image, float* T_final, int32_t* n_contrib, cudaStream_t s) {
   INPC_TRY(bin_fragments(P, pos, opacity, feat, ws, 2 * GA, GA * kRegMax, s));
-  static std::once_flag f2;
-  set_smem(k_blend_fwd_heavy<V, GA, FT>, HeavyBuf::bytes(), f2);
+  static SmemOnce f2;
+  INPC_TRY(set_smem(k_blend_fwd_heavy<V, GA, FT>, HeavyBuf::bytes(), f2));
   INPC_TIMED("k_blend_fwd", s,
              k_blend_fwd<V, GA, FT><<<P.n_tiles, kThreads, 0, s>>>(P, feat, ws, image, T_final, n_contrib));
   INPC_TRY(check_launch("k_blend_fwd"));
