@@ -77,11 +77,11 @@ def algorithmic_bytes(n, n_leaves, n_entries, n_frag, n_pix):
 
 KERNELS = ["k_draw_count", "k_place", "k_hash_fwd", "k_pix_count", "k_pix_scatter", "k_blend_fwd",
            "k_blend_fwd_large", "k_blend_fwd_heavy", "k_blend_bwd", "k_blend_bwd_large", "k_blend_bwd_heavy",
-           "k_point_grad_hash", "k_fold_replicas", "k_point_grad", "k_hash_bwd"]
+           "k_point_grad_hash", "k_point_grad", "k_hash_bwd"]
 
 # DRAM bytes per launch of the dominant kernel on the full workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); see profiles/.
-TRAFFIC = {"k_point_grad_hash": 2.45e9 + 0.68856e9}
+TRAFFIC = {}
 
 
 def kernel_bytes(kernel, n, n_entries, n_frag, n_pix):

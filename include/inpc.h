@@ -284,10 +284,10 @@ inpc_status inpc_rasterize_bwd(const inpc_camera* cam, const inpc_raster_opts* o
  *   grad_table  float32 [n_entries, n_feats], accumulated (+=)
  *   d_feat      optional float32 [n, F]: also written when non-NULL
  * The workspace is the forward's, sized by
- * inpc_rasterize_bwd_hashgrid_workspace_size (the rasterizer's workspace
- * plus replicas of the coarse levels' gradient, which spread the atomic
- * additions those few rows receive; they are summed into grad_table at the
- * end of the call).  Other arguments as for inpc_rasterize_bwd. */
+ * inpc_rasterize_bwd_hashgrid_workspace_size (the same size as the
+ * rasterizer's).  Additions into grad_table are atomic, so several calls
+ * may accumulate into one table concurrently.  Other arguments as for
+ * inpc_rasterize_bwd. */
 inpc_status inpc_rasterize_bwd_hashgrid_workspace_size(const inpc_camera* cam, const inpc_raster_opts* opts,
                                                        const inpc_hashgrid_desc* grid, int64_t n, size_t* bytes);
 inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const inpc_raster_opts* opts,

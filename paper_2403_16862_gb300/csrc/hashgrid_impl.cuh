@@ -77,6 +77,12 @@ __device__ __forceinline__ void cell_frac(float x, int N, uint32_t& cell, float&
   f0 = __fsub_rn(__fsub_rn(c + 1.0f, s), e);
 }
 
+__device__ __forceinline__ void swap_f(float& a, float& b) {
+  const float t = a;
+  a = b;
+  b = t;
+}
+
 __device__ __forceinline__ uint32_t vertex_row(const GridParams& P, int l, uint32_t x, uint32_t y, uint32_t z) {
   if (P.dense[l]) return x + P.side[l] * (y + P.side[l] * z);
   return (x ^ (y * 2654435761u) ^ (z * 805459861u)) & P.hash_mask;

@@ -9,63 +9,54 @@ namespace {
 // row, gathered as in k_point_grad, then that level's eight corner
 // contributions to the table gradient straight from registers (the adjoint
 // of the query, as in k_hash_bwd), so the row never goes through memory.
-// Coarse levels have few rows and receive millions of additions each, which
-// serialise on the same L2 addresses.  Their contributions go to one of
-// kReplicas copies (chosen by CTA) and k_fold_replicas sums the copies into
-// the table gradient afterwards.
-constexpr int kReplicas = 16;
-constexpr int64_t kReplicaMaxRows = 1 << 17;  // levels up to this many rows are replicated
-
-struct Replicas {
-  int n_levels;      // leading levels that are replicated
-  long long rows;    // table rows they span (level-aligned)
-  float* base;       // [kReplicas][rows][4]
-};
-
-inline Replicas replica_plan(const GridParams& Gp, void* base) {
-  Replicas r;
-  r.n_levels = 0;
-  while (r.n_levels < Gp.n_levels && r.n_levels + 1 < kMaxLevels &&
-         (Gp.offset[r.n_levels + 1] - Gp.offset[r.n_levels]) <= kReplicaMaxRows)
-    ++r.n_levels;
-  r.rows = r.n_levels > 0 ? Gp.offset[r.n_levels] : 0;
-  r.base = static_cast<float*>(base);
-  return r;
-}
-
-inline size_t replica_bytes(const Replicas& r) { return (size_t)kReplicas * r.rows * 4 * sizeof(float); }
-
-// Sum the replicas into the table gradient.  The add is atomic, so calls
-// for several views may accumulate into one table concurrently.
-__global__ void k_fold_replicas(const float4* __restrict__ rep, long long rows, float* __restrict__ grad) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < rows; i += (long long)gridDim.x * blockDim.x) {
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < kReplicas; ++k) {
-      const float4 v = rep[k * rows + i];
-      s.x += v.x;
-      s.y += v.y;
-      s.z += v.z;
-      s.w += v.w;
-    }
-    if (s.x != 0.f || s.y != 0.f || s.z != 0.f || s.w != 0.f) red_add_v4(grad + 4 * i, s);
-  }
-}
-
+//
+// The levels are split in halves over a pair of warps that share the same
+// points: the even warp takes the coarse half, the odd warp the fine half.
+// Each point slot of a CTA walks a run of points a few apart.  Points come
+// grouped by octree leaf with the leaves in Morton order, so at the coarse
+// levels such points fall in the same or a neighbouring cell, and a coarse
+// lane keeps one float4 accumulator per cell corner (in shared memory),
+// sending a corner's sum to memory only when the next point needs a
+// different vertex in that slot.  The slot of vertex (X, Y, Z) is given by
+// the parities of X, Y and Z: every cell has exactly one corner of each
+// parity class, and a step of one cell along an axis keeps the four shared
+// vertices in their slots, so neighbouring cells share accumulators as well.
+// Coarse levels have few rows that would otherwise receive millions of
+// additions each.  Fine levels change vertex at almost every point and
+// reduce directly.
 template <int GA, class FT>
 __global__ void __launch_bounds__(kThreads) k_point_grad_hash(RP P, GridParams Gp, const float* __restrict__ pos,
                                                                const FT* __restrict__ feat,
                                                                const float* __restrict__ d_image, RasterWs ws,
                                                                float* __restrict__ grad_table,
-                                                               float* __restrict__ d_feat, Replicas rep) {
-  constexpr int kGroups = kThreads / GA;
-  const Group<GA> G;
-  const int l = G.lg;
+                                                               float* __restrict__ d_feat, long long chunk) {
+  constexpr int kGroups = kThreads / GA;  // points in flight per CTA
+  constexpr int kH = GA / 2;               // levels per half
+  constexpr int kPW = 32 / kH;             // points per warp
+  // warps come in pairs over the same kPW points: the even warp takes the
+  // coarse half of the levels, the odd warp the fine half
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool coarse = (warp & 1) == 0;
+  const int l = (coarse ? 0 : kH) + lane % kH;
   const int ch = 4 * l;
   const bool active = l < Gp.n_levels;
-  const long long g0 = (long long)blockIdx.x * kGroups + threadIdx.x / GA;
+  const int slot = (warp >> 1) * kPW + lane / kH;
+  // the CTA takes `chunk` consecutive points; its point slots interleave
+  // over them, so at any moment its warps work on neighbouring points
+  // (shared image and fragment data in L1) while each slot's own sequence,
+  // kGroups points apart, stays within a leaf or two
+  const long long first = (long long)blockIdx.x * chunk + slot;
+  const long long last = min((long long)(blockIdx.x + 1) * chunk, P.n);
   const uint64_t keep = l2_evict_last(), stream = l2_evict_first();
-  for (long long id = g0; id < P.n; id += (long long)gridDim.x * kGroups) {
+  float* gl = active ? grad_table + 4 * Gp.offset[l] : nullptr;
+  // the coarse warps' corner accumulators, [corner slot][point slot][level]
+  constexpr int kStride = kGroups * kH;
+  __shared__ float4 acc_s[8][kStride];
+  float4* acc = &acc_s[0][slot * kH + lane % kH];
+  // the cell whose corners the accumulators hold (kFar: none yet)
+  constexpr uint32_t kFar = 1u << 30;
+  uint32_t hx = kFar, hy = kFar, hz = kFar;
+  for (long long id = first; id < last; id += kGroups) {
     const uint4 sl = ld_hint_u4(reinterpret_cast<const uint4*>(ws.pslot) + id, stream);
     const uint32_t slots[4] = {sl.x, sl.y, sl.z, sl.w};
     float dc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -105,36 +96,70 @@ __global__ void __launch_bounds__(kThreads) k_point_grad_hash(RP P, GridParams G
     cell_frac(__ldg(pos + 3 * id + 0), N, cx, gx[0], gx[1]);
     cell_frac(__ldg(pos + 3 * id + 1), N, cy, gy[0], gy[1]);
     cell_frac(__ldg(pos + 3 * id + 2), N, cz, gz[0], gz[1]);
-    float* gl = l < rep.n_levels
-                    ? rep.base + 4 * ((long long)(blockIdx.x % kReplicas) * rep.rows + Gp.offset[l])
-                    : grad_table + 4 * Gp.offset[l];
+    // slot s holds the corner whose offsets are s's bits xor the cell's
+    // parities; swapping the weight pairs of odd cells makes gx[sx] that
+    // corner's weight
+    const uint32_t px = cx & 1u, py = cy & 1u, pz = cz & 1u;
+    const uint32_t qx = hx & 1u, qy = hy & 1u, qz = hz & 1u;
+    if (px) swap_f(gx[0], gx[1]);
+    if (py) swap_f(gy[0], gy[1]);
+    if (pz) swap_f(gz[0], gz[1]);
+    // per axis and parity: does the slot keep its vertex?
+    const bool kx[2] = {cx + px == hx + qx, cx + (px ^ 1u) == hx + (qx ^ 1u)};
+    const bool ky[2] = {cy + py == hy + qy, cy + (py ^ 1u) == hy + (qy ^ 1u)};
+    const bool kz[2] = {cz + pz == hz + qz, cz + (pz ^ 1u) == hz + (qz ^ 1u)};
+    if (coarse) {
+      const bool held = hx != kFar;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
-      const float w = gx[bx] * gy[by] * gz[bz];
-      const uint32_t row = vertex_row(Gp, l, cx + bx, cy + by, cz + bz);
-      red_add_v4(gl + 4ull * row, make_float4(w * dc[0], w * dc[1], w * dc[2], w * dc[3]), keep);
+      for (int s = 0; s < 8; ++s) {
+        const uint32_t sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
+        const float w = gx[sx] * gy[sy] * gz[sz];
+        const float4 v = make_float4(w * dc[0], w * dc[1], w * dc[2], w * dc[3]);
+        const float4 a = acc[s * kStride];
+        const bool same = kx[sx] && ky[sy] && kz[sz];
+        acc[s * kStride] = same ? make_float4(a.x + v.x, a.y + v.y, a.z + v.z, a.w + v.w) : v;
+        // the slot moves to another vertex: send the old vertex its sum
+        if (!same && held)
+          red_add_v4(gl + 4ull * vertex_row(Gp, l, hx + (sx ^ qx), hy + (sy ^ qy), hz + (sz ^ qz)), a, keep);
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const uint32_t sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
+        const float w = gx[sx] * gy[sy] * gz[sz];
+        red_add_v4(gl + 4ull * vertex_row(Gp, l, cx + (sx ^ px), cy + (sy ^ py), cz + (sz ^ pz)),
+                   make_float4(w * dc[0], w * dc[1], w * dc[2], w * dc[3]), keep);
+      }
     }
+    hx = cx;
+    hy = cy;
+    hz = cz;
+  }
+  if (!active || !coarse || hx == kFar) return;
+  const uint32_t qx = hx & 1u, qy = hy & 1u, qz = hz & 1u;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const uint32_t sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
+    red_add_v4(gl + 4ull * vertex_row(Gp, l, hx + (sx ^ qx), hy + (sy ^ qy), hz + (sz ^ qz)), acc[s * kStride],
+               keep);
   }
 }
 
 template <int GA, class FT>
 inpc_status launch_point_grad_hash(const RP& P, const GridParams& Gp, const float* pos, const FT* feat,
                                    const float* d_image, const RasterWs& ws, float* grad_table, float* d_feat,
-                                   const Replicas& rep, cudaStream_t s) {
+                                   cudaStream_t s) {
   constexpr int kGroups = kThreads / GA;
-  if (rep.rows > 0) INPC_CUDA(cudaMemsetAsync(rep.base, 0, replica_bytes(rep), s), "clear replicas");
-  const long long grid = std::min<long long>(ceil_div(P.n, kGroups), (long long)device_sm_count() * 32);
+  // kRun points per group and CTA chunk, as many CTAs as that needs up to
+  // 32 per SM (longer runs beyond that)
+  constexpr long long kRun = 48;
+  const long long ctas_max = (long long)device_sm_count() * 32;
+  const long long chunk = kGroups * std::max<long long>(kRun, ceil_div(P.n, ctas_max * kGroups));
+  const long long grid = ceil_div(P.n, chunk);
   INPC_TIMED("k_point_grad_hash", s,
              k_point_grad_hash<GA, FT><<<(unsigned)std::max<long long>(grid, 1), kThreads, 0, s>>>(
-                 P, Gp, pos, feat, d_image, ws, grad_table, d_feat, rep));
+                 P, Gp, pos, feat, d_image, ws, grad_table, d_feat, chunk));
   INPC_TRY(check_launch("k_point_grad_hash"));
-  if (rep.rows > 0) {
-    INPC_TIMED("k_fold_replicas", s,
-               k_fold_replicas<<<(unsigned)std::min<long long>(ceil_div(rep.rows, 256), device_sm_count() * 8), 256,
-                                 0, s>>>(reinterpret_cast<const float4*>(rep.base), rep.rows, grad_table));
-    INPC_TRY(check_launch("k_fold_replicas"));
-  }
   return INPC_OK;
 }
 
@@ -189,8 +214,7 @@ extern "C" inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const
   if (P.F != 4 * Gp.n_levels)
     return fail(INPC_ERR_INVALID_ARG, "n_channels (%d) must equal n_levels * n_feats (%d)", P.F, 4 * Gp.n_levels);
   const RasterWs need = carve(nullptr, P.n_pix, n);
-  const Replicas rep_need = replica_plan(Gp, nullptr);
-  const size_t total = need.bytes + replica_bytes(rep_need);
+  const size_t total = need.bytes;
   if (!workspace || workspace_bytes < total || !aligned(workspace, 256))
     return fail(INPC_ERR_INVALID_ARG,
                 "workspace null, unaligned or smaller than %zu bytes (inpc_rasterize_bwd_hashgrid_workspace_size)",
@@ -203,7 +227,6 @@ extern "C" inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const
     return fail(INPC_ERR_INVALID_ARG, "feat/d_image/grad_table/d_feat misaligned");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   RasterWs ws = carve(workspace, P.n_pix, n);
-  const Replicas rep = replica_plan(Gp, static_cast<char*>(workspace) + need.bytes);
   return dispatch(P.F, [&](auto Vc, auto Gc) -> inpc_status {
     constexpr int V = decltype(Vc)::value, GA = decltype(Gc)::value;
     auto run = [&](auto ftag) -> inpc_status {
@@ -211,10 +234,10 @@ extern "C" inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const
       const FT* f = static_cast<const FT*>(feat);
       INPC_TRY((launch_blend_bwd<V, GA, FT>(P, f, n_contrib, d_image, ws, s)));
       if (Gp.n_levels <= 8)
-        return launch_point_grad_hash<8, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, rep, s);
+        return launch_point_grad_hash<8, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, s);
       if (Gp.n_levels <= 16)
-        return launch_point_grad_hash<16, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, rep, s);
-      return launch_point_grad_hash<32, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, rep, s);
+        return launch_point_grad_hash<16, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, s);
+      return launch_point_grad_hash<32, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, s);
     };
     if constexpr (GA != 32) {
       if (P.bf16) return fail(INPC_ERR_UNSUPPORTED, "BF16 features need n_channels = 32, 64 or 128");
@@ -235,6 +258,6 @@ extern "C" inpc_status inpc_rasterize_bwd_hashgrid_workspace_size(const inpc_cam
   GridParams Gp;
   int64_t n_entries = 0;
   INPC_TRY(make_params(grid, Gp, &n_entries));
-  *bytes = carve(nullptr, P.n_pix, n).bytes + replica_bytes(replica_plan(Gp, nullptr));
+  *bytes = carve(nullptr, P.n_pix, n).bytes;
   return INPC_OK;
 }
