@@ -81,7 +81,10 @@ KERNELS = ["k_draw_count", "k_place", "k_hash_fwd", "k_pix_count", "k_pix_scatte
 
 # DRAM bytes per launch of the dominant kernel on the full workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); see profiles/.
-TRAFFIC = {}
+TRAFFIC = {"k_point_grad_hash": 2.52e9 + 0.63208e9}
+# L2 vector-reduction requests of one launch of the dominant kernel on the full
+# workload (lts__t_requests_op_red.sum, one ncu capture); see profiles/.
+L2_REDUCTIONS = {"k_point_grad_hash": 418_879_860}
 
 
 def kernel_bytes(kernel, n, n_entries, n_frag, n_pix):
@@ -101,12 +104,17 @@ def kernel_bytes(kernel, n, n_entries, n_frag, n_pix):
 
 
 def atomic_ceiling(kernel, n, ms):
-    """The grid adjoint issues 8 vector reductions (16 B) per point and level;
-    L2 atomic throughput bounds it, not DRAM."""
+    """The grid adjoint forms 8 corner contributions (16 B) per point and
+    level.  Coarse levels merge runs of them before they reach L2, so the L2
+    vector reductions (lts__t_requests_op_red.sum, one ncu capture) are
+    fewer; their rate, not DRAM, is what the reductions cost."""
     if kernel != "k_point_grad_hash":
         return {}
-    ops = 8 * 16 * n
-    return {"l2_vector_atomics": ops, "l2_atomic_gops": ops / (ms * 1e-3) / 1e9}
+    out = {"corner_contributions": 8 * 16 * n}
+    red = L2_REDUCTIONS.get(kernel) if SCALE == 1 else None
+    if red:
+        out.update({"l2_reductions": red, "l2_reduction_gops": red / (ms * 1e-3) / 1e9})
+    return out
 
 
 class ClockSampler:
