@@ -1,12 +1,11 @@
 // hashgrid.cu -- multi-resolution hash-grid query (Sec. 3.3, App. A.5) and
 // its adjoint (the table gradient).
 //
-// One thread per (point, level); levels go in groups of two along grid y so
-// that the rows in use at any time fit in L2, and within a group a warp
-// covers 16 points x 2 levels (32-byte output pieces, one sector each).  The 8 corner rows of a level are
-// gathered as 16-byte vectors (FP32) or 8-byte vectors (BF16); for the x
-// neighbours the hash (multiplier 1 on x) keeps rows adjacent, so a corner
-// pair usually shares one 32-byte sector.  The output is written with
+// The query runs two threads per (point, level), each gathering the four
+// corners on one side of the cell along x; levels go in groups of two along
+// grid y so that the rows in use at any time fit in L2, and within a group
+// a warp covers 8 points x 2 levels.  Corner rows are gathered as 16-byte
+// vectors (FP32) or 8-byte vectors (BF16).  The output is written with
 // streaming stores so that it does not evict the table from L2.
 //
 // The backward uses red.global.add.v4.f32 (one 16-byte vector reduction per
@@ -24,17 +23,31 @@ namespace {
 // stay resident in L2 instead of the whole table.
 constexpr int kLevelGroup = 2;
 
-template <class TT, class OT, bool kPairs>
+// Two lanes per (point, level): lane bx gathers the four corners at x + bx.
+// The x neighbours' rows differ only in their lowest bits (hashed: x is
+// multiplied by 1 before the XOR; dense: consecutive rows), so they share
+// one 128-byte line unless the carry of x + 1 reaches bit 3 (FP32) or bit 4
+// (BF16).  Loading both from one instruction then costs one L1 wavefront
+// instead of two, and the L1 wavefront rate bounds this kernel.  The pair
+// adds its partial sums with one exchange, and each lane stores half of
+// the four features.
+template <class TT, class OT>
 __global__ void __launch_bounds__(256) k_hash_fwd(GridParams P, const TT* __restrict__ table,
                                                   const float* __restrict__ pos, long long n, OT* __restrict__ h) {
   const int l0 = blockIdx.y * kLevelGroup;
   const int gl = min(kLevelGroup, P.n_levels - l0);
-  const long long total = n * gl;
+  const long long total = 2 * n * gl;
   const uint64_t keep = l2_evict_last();
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i / gl;
-    const int l = l0 + (int)(i - p * gl);
+  const int lane = threadIdx.x & 31;
+  const uint32_t bx = lane & 1u;
+  // warp-uniform trip count: the pair exchange is a warp shuffle
+  for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane); base < total;
+       base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + lane;
+    const bool valid = i < total;
+    const long long item = (valid ? i : total - 1) >> 1;  // spare lanes redo the last item
+    const long long p = item / gl;
+    const int l = l0 + (int)(item - p * gl);
     uint32_t cx, cy, cz;
     float gx[2], gy[2], gz[2];
     const int N = P.res[l];
@@ -42,40 +55,23 @@ __global__ void __launch_bounds__(256) k_hash_fwd(GridParams P, const TT* __rest
     cell_frac(__ldg(pos + 3 * p + 1), N, cy, gy[0], gy[1]);
     cell_frac(__ldg(pos + 3 * p + 2), N, cz, gz[0], gz[1]);
     const TT* tab = table + 4 * P.offset[l];
+    const float wx = bx ? gx[1] : gx[0];
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    // the 8 corners as 4 x-neighbour pairs: when the pair's rows differ
-    // only in the lowest bit (dense rows 2k, 2k+1, or hashed rows at even x)
-    // they share one aligned 32-byte (FP32) / 16-byte (BF16) chunk and are
-    // fetched with a single load
 #pragma unroll
     for (int yz = 0; yz < 4; ++yz) {
       const int by = yz & 1, bz = yz >> 1;
-      const uint32_t r0 = vertex_row(P, l, cx, cy + by, cz + bz);
-      const uint32_t r1 = vertex_row(P, l, cx + 1, cy + by, cz + bz);
-      float4 t0, t1;
-      if (kPairs && (r0 ^ r1) == 1u) {
-        load_row_pair<TT>(tab, r0 & ~1u, t0, t1, keep);
-        if (r0 & 1u) {
-          const float4 tmp = t0;
-          t0 = t1;
-          t1 = tmp;
-        }
-      } else {
-        t0 = load_row<TT>(tab, r0, keep);
-        t1 = load_row<TT>(tab, r1, keep);
-      }
-      const float wyz = gy[by] * gz[bz];
-      const float w0 = gx[0] * wyz, w1 = gx[1] * wyz;
-      acc.x = fmaf(w0, t0.x, acc.x);
-      acc.y = fmaf(w0, t0.y, acc.y);
-      acc.z = fmaf(w0, t0.z, acc.z);
-      acc.w = fmaf(w0, t0.w, acc.w);
-      acc.x = fmaf(w1, t1.x, acc.x);
-      acc.y = fmaf(w1, t1.y, acc.y);
-      acc.z = fmaf(w1, t1.z, acc.z);
-      acc.w = fmaf(w1, t1.w, acc.w);
+      const float4 t = load_row<TT>(tab, vertex_row(P, l, cx + bx, cy + by, cz + bz), keep);
+      const float w = wx * (gy[by] * gz[bz]);
+      acc.x = fmaf(w, t.x, acc.x);
+      acc.y = fmaf(w, t.y, acc.y);
+      acc.z = fmaf(w, t.z, acc.z);
+      acc.w = fmaf(w, t.w, acc.w);
     }
-    store_out<OT>(h, p * P.n_levels + l, acc);
+    // lane 0 keeps features 0-1, lane 1 features 2-3
+    const float s0 = bx ? acc.x : acc.z, s1 = bx ? acc.y : acc.w;
+    const float r0 = __shfl_xor_sync(0xffffffffu, s0, 1), r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+    const float2 mine = bx ? make_float2(acc.z + r0, acc.w + r1) : make_float2(acc.x + r0, acc.y + r1);
+    if (valid) store_half<OT>(h, p * P.n_levels + l, bx, mine);
   }
 }
 
@@ -141,27 +137,17 @@ extern "C" inpc_status inpc_query_hashgrid(const inpc_hashgrid_desc* g, const vo
   if (!aligned(table, ta) || !aligned(h_out, oa) || !aligned(pos, 4))
     return fail(INPC_ERR_INVALID_ARG, "inpc_query_hashgrid: misaligned table/output/pos");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const dim3 grid = grid_for(n, P.n_levels, 256);
-  // aligned row pairs need the table to start on a pair boundary
-  const bool pairs = aligned(table, 2 * ta);
+  const dim3 grid = grid_for(2 * n, P.n_levels, 256);
   TimedLaunch timed("k_hash_fwd", s);
-  if (g->table_dtype == INPC_F32 && g->out_dtype == INPC_F32) {
-    if (pairs) k_hash_fwd<float, float, true><<<grid, 256, 0, s>>>(P, (const float*)table, pos, n, (float*)h_out);
-    else k_hash_fwd<float, float, false><<<grid, 256, 0, s>>>(P, (const float*)table, pos, n, (float*)h_out);
-  } else if (g->table_dtype == INPC_F32) {
-    k_hash_fwd<float, __nv_bfloat16, false>
-        <<<grid, 256, 0, s>>>(P, (const float*)table, pos, n, (__nv_bfloat16*)h_out);
-  } else if (g->out_dtype == INPC_F32) {
-    k_hash_fwd<__nv_bfloat16, float, false>
-        <<<grid, 256, 0, s>>>(P, (const __nv_bfloat16*)table, pos, n, (float*)h_out);
-  } else {
-    if (pairs)
-      k_hash_fwd<__nv_bfloat16, __nv_bfloat16, true>
-          <<<grid, 256, 0, s>>>(P, (const __nv_bfloat16*)table, pos, n, (__nv_bfloat16*)h_out);
-    else
-      k_hash_fwd<__nv_bfloat16, __nv_bfloat16, false>
-          <<<grid, 256, 0, s>>>(P, (const __nv_bfloat16*)table, pos, n, (__nv_bfloat16*)h_out);
-  }
+  if (g->table_dtype == INPC_F32 && g->out_dtype == INPC_F32)
+    k_hash_fwd<float, float><<<grid, 256, 0, s>>>(P, (const float*)table, pos, n, (float*)h_out);
+  else if (g->table_dtype == INPC_F32)
+    k_hash_fwd<float, __nv_bfloat16><<<grid, 256, 0, s>>>(P, (const float*)table, pos, n, (__nv_bfloat16*)h_out);
+  else if (g->out_dtype == INPC_F32)
+    k_hash_fwd<__nv_bfloat16, float><<<grid, 256, 0, s>>>(P, (const __nv_bfloat16*)table, pos, n, (float*)h_out);
+  else
+    k_hash_fwd<__nv_bfloat16, __nv_bfloat16>
+        <<<grid, 256, 0, s>>>(P, (const __nv_bfloat16*)table, pos, n, (__nv_bfloat16*)h_out);
   return check_launch("k_hash_fwd");
 }
 

@@ -101,53 +101,7 @@ __device__ __forceinline__ uint64_t l2_evict_first() {
   asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
-template <class TT>
-__device__ __forceinline__ float4 load_row(const TT* __restrict__ table, long long row);
 
-template <>
-__device__ __forceinline__ float4 load_row<float>(const float* __restrict__ table, long long row) {
-  return __ldg(reinterpret_cast<const float4*>(table) + row);
-}
-
-template <>
-__device__ __forceinline__ float4 load_row<__nv_bfloat16>(const __nv_bfloat16* __restrict__ table, long long row) {
-  const uint2 raw = __ldg(reinterpret_cast<const uint2*>(table) + row);
-  float4 r;
-  r.x = __uint_as_float(raw.x << 16);
-  r.y = __uint_as_float(raw.x & 0xFFFF0000u);
-  r.z = __uint_as_float(raw.y << 16);
-  r.w = __uint_as_float(raw.y & 0xFFFF0000u);
-  return r;
-}
-
-// Two consecutive rows starting at an even row (one aligned vector load).
-template <class TT>
-__device__ __forceinline__ void load_row_pair(const TT* __restrict__ table, uint32_t even_row, float4& a, float4& b);
-
-template <>
-__device__ __forceinline__ void load_row_pair<float>(const float* __restrict__ table, uint32_t even_row, float4& a,
-                                                     float4& b) {
-  const float* p = table + 4ull * even_row;
-  asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
-               : "l"(p));
-}
-
-template <>
-__device__ __forceinline__ void load_row_pair<__nv_bfloat16>(const __nv_bfloat16* __restrict__ table,
-                                                             uint32_t even_row, float4& a, float4& b) {
-  const uint4 raw = __ldg(reinterpret_cast<const uint4*>(table + 4ull * even_row));
-  a.x = __uint_as_float(raw.x << 16);
-  a.y = __uint_as_float(raw.x & 0xFFFF0000u);
-  a.z = __uint_as_float(raw.y << 16);
-  a.w = __uint_as_float(raw.y & 0xFFFF0000u);
-  b.x = __uint_as_float(raw.z << 16);
-  b.y = __uint_as_float(raw.z & 0xFFFF0000u);
-  b.z = __uint_as_float(raw.w << 16);
-  b.w = __uint_as_float(raw.w & 0xFFFF0000u);
-}
-
-// The same loads with an L2 eviction-priority policy.
 template <class TT>
 __device__ __forceinline__ float4 load_row(const TT* __restrict__ table, long long row, uint64_t pol);
 
@@ -170,31 +124,6 @@ __device__ __forceinline__ float4 load_row<__nv_bfloat16>(const __nv_bfloat16* _
                      __uint_as_float(y & 0xFFFF0000u));
 }
 
-template <class TT>
-__device__ __forceinline__ void load_row_pair(const TT* __restrict__ table, uint32_t even_row, float4& a, float4& b,
-                                              uint64_t pol);
-
-template <>
-__device__ __forceinline__ void load_row_pair<float>(const float* __restrict__ table, uint32_t even_row, float4& a,
-                                                     float4& b, uint64_t pol) {
-  asm("ld.global.nc.L2::cache_hint.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
-               : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
-               : "l"(table + 4ull * even_row), "l"(pol));
-}
-
-template <>
-__device__ __forceinline__ void load_row_pair<__nv_bfloat16>(const __nv_bfloat16* __restrict__ table,
-                                                             uint32_t even_row, float4& a, float4& b, uint64_t pol) {
-  uint32_t w[4];
-  asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
-               : "l"(table + 4ull * even_row), "l"(pol));
-  a = make_float4(__uint_as_float(w[0] << 16), __uint_as_float(w[0] & 0xFFFF0000u), __uint_as_float(w[1] << 16),
-                  __uint_as_float(w[1] & 0xFFFF0000u));
-  b = make_float4(__uint_as_float(w[2] << 16), __uint_as_float(w[2] & 0xFFFF0000u), __uint_as_float(w[3] << 16),
-                  __uint_as_float(w[3] & 0xFFFF0000u));
-}
-
 template <class OT>
 __device__ __forceinline__ void store_out(OT* __restrict__ out, long long idx4, float4 v);
 
@@ -211,6 +140,22 @@ __device__ __forceinline__ void store_out<__nv_bfloat16>(__nv_bfloat16* __restri
   raw.x = *reinterpret_cast<uint32_t*>(&a);
   raw.y = *reinterpret_cast<uint32_t*>(&b);
   __stcs(reinterpret_cast<uint2*>(out) + idx4, raw);
+}
+
+// Half of a 4-feature output row: features 2 half .. 2 half + 1.
+template <class OT>
+__device__ __forceinline__ void store_half(OT* __restrict__ out, long long idx4, uint32_t half, float2 v);
+
+template <>
+__device__ __forceinline__ void store_half<float>(float* __restrict__ out, long long idx4, uint32_t half, float2 v) {
+  __stcs(reinterpret_cast<float2*>(out) + 2 * idx4 + half, v);
+}
+
+template <>
+__device__ __forceinline__ void store_half<__nv_bfloat16>(__nv_bfloat16* __restrict__ out, long long idx4,
+                                                          uint32_t half, float2 v) {
+  __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+  __stcs(reinterpret_cast<unsigned int*>(out) + 2 * idx4 + half, *reinterpret_cast<unsigned int*>(&a));
 }
 
 __device__ __forceinline__ void red_add_v4(float* addr, float4 v) {
