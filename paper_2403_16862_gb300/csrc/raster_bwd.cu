@@ -25,11 +25,11 @@ namespace {
 // additions each.  Fine levels change vertex at almost every point and
 // reduce directly.
 template <int GA, class FT>
-__global__ void __launch_bounds__(kThreads) k_point_grad_hash(RP P, GridParams Gp, const float* __restrict__ pos,
+__global__ void __launch_bounds__(kThreads, 5) k_point_grad_hash(RP P, GridParams Gp, const float* __restrict__ pos,
                                                                const FT* __restrict__ feat,
                                                                const float* __restrict__ d_image, RasterWs ws,
                                                                float* __restrict__ grad_table,
-                                                               float* __restrict__ d_feat, long long chunk) {
+                                                               float* __restrict__ d_feat, int chunk) {
   constexpr int kGroups = kThreads / GA;  // points in flight per CTA
   constexpr int kH = GA / 2;               // levels per half
   constexpr int kPW = 32 / kH;             // points per warp
@@ -45,8 +45,9 @@ __global__ void __launch_bounds__(kThreads) k_point_grad_hash(RP P, GridParams G
   // over them, so at any moment its warps work on neighbouring points
   // (shared image and fragment data in L1) while each slot's own sequence,
   // kGroups points apart, stays within a leaf or two
-  const long long first = (long long)blockIdx.x * chunk + slot;
-  const long long last = min((long long)(blockIdx.x + 1) * chunk, P.n);
+  // n <= 2^25 (the rasterizer's key packing), so 32-bit point indices
+  const int first = (int)blockIdx.x * chunk + slot;
+  const int last = (int)min((long long)(blockIdx.x + 1) * chunk, P.n);
   const uint64_t keep = l2_evict_last(), stream = l2_evict_first();
   float* gl = active ? grad_table + 4 * Gp.offset[l] : nullptr;
   // the coarse warps' corner accumulators, [corner slot][point slot][level]
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(kThreads) k_point_grad_hash(RP P, GridParams G
   // the cell whose corners the accumulators hold (kFar: none yet)
   constexpr uint32_t kFar = 1u << 30;
   uint32_t hx = kFar, hy = kFar, hz = kFar;
-  for (long long id = first; id < last; id += kGroups) {
+  for (int id = first; id < last; id += kGroups) {
     const uint4 sl = ld_hint_u4(reinterpret_cast<const uint4*>(ws.pslot) + id, stream);
     const uint32_t slots[4] = {sl.x, sl.y, sl.z, sl.w};
     float dc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(kThreads) k_point_grad_hash(RP P, GridParams G
       if (l == 0) dc[0] = dah * (e_h0 * expf(-e_h0));
     }
     if (!active) continue;
-    if (d_feat) *reinterpret_cast<float4*>(d_feat + id * P.F + ch) = make_float4(dc[0], dc[1], dc[2], dc[3]);
+    if (d_feat) *reinterpret_cast<float4*>(d_feat + (long long)id * P.F + ch) = make_float4(dc[0], dc[1], dc[2], dc[3]);
     if (dc[0] == 0.f && dc[1] == 0.f && dc[2] == 0.f && dc[3] == 0.f) continue;
     uint32_t cx, cy, cz;
     float gx[2], gy[2], gz[2];
@@ -158,7 +159,7 @@ inpc_status launch_point_grad_hash(const RP& P, const GridParams& Gp, const floa
   const long long grid = ceil_div(P.n, chunk);
   INPC_TIMED("k_point_grad_hash", s,
              k_point_grad_hash<GA, FT><<<(unsigned)std::max<long long>(grid, 1), kThreads, 0, s>>>(
-                 P, Gp, pos, feat, d_image, ws, grad_table, d_feat, chunk));
+                 P, Gp, pos, feat, d_image, ws, grad_table, d_feat, (int)chunk));
   INPC_TRY(check_launch("k_point_grad_hash"));
   return INPC_OK;
 }
