@@ -176,7 +176,7 @@ inpc_status inpc_hashgrid_n_entries(const inpc_hashgrid_desc* g, int64_t* n_entr
  * (cell = min(floor(x N_l), N_l - 1) per axis; the fraction x N_l - cell is
  * formed exactly).  pos: float32 [n, 3]; table: [n_entries, n_feats] of
  * table_dtype; h_out: [n, n_levels * n_feats] of out_dtype.  Arithmetic is
- * FP32.  n in [0, 2^31 - 1]. */
+ * FP32.  n in [0, 2^29] (INPC_ERR_CAPACITY beyond). */
 inpc_status inpc_query_hashgrid(const inpc_hashgrid_desc* g, const void* table, const float* pos, int64_t n,
                                 void* h_out, inpc_stream_t stream);
 

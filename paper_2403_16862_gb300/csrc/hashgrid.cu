@@ -36,17 +36,17 @@ __global__ void __launch_bounds__(256) k_hash_fwd(GridParams P, const TT* __rest
                                                   const float* __restrict__ pos, long long n, OT* __restrict__ h) {
   const int l0 = blockIdx.y * kLevelGroup;
   const int gl = min(kLevelGroup, P.n_levels - l0);
-  const long long total = 2 * n * gl;
+  // n <= 2^29 (checked by the caller): 32-bit indices do not overflow
+  const uint32_t total = 2u * (uint32_t)n * (uint32_t)gl;
   const uint64_t keep = l2_evict_last();
   const int lane = threadIdx.x & 31;
   const uint32_t bx = lane & 1u;
   // warp-uniform trip count: the pair exchange is a warp shuffle
-  for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x - lane); base < total;
-       base += (long long)gridDim.x * blockDim.x) {
-    const long long i = base + lane;
+  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x - lane); base < total; base += gridDim.x * blockDim.x) {
+    const uint32_t i = base + lane;
     const bool valid = i < total;
-    const long long item = (valid ? i : total - 1) >> 1;  // spare lanes redo the last item
-    const long long p = item / gl;
+    const uint32_t item = (valid ? i : total - 1) >> 1;  // spare lanes redo the last item
+    const uint32_t p = item / (uint32_t)gl;
     const int l = l0 + (int)(item - p * gl);
     uint32_t cx, cy, cz;
     float gx[2], gy[2], gz[2];
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_hash_fwd(GridParams P, const TT* __rest
     const float s0 = bx ? acc.x : acc.z, s1 = bx ? acc.y : acc.w;
     const float r0 = __shfl_xor_sync(0xffffffffu, s0, 1), r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
     const float2 mine = bx ? make_float2(acc.z + r0, acc.w + r1) : make_float2(acc.x + r0, acc.y + r1);
-    if (valid) store_half<OT>(h, p * P.n_levels + l, bx, mine);
+    if (valid) store_half<OT>(h, (long long)p * P.n_levels + l, bx, mine);
   }
 }
 
@@ -130,7 +130,7 @@ extern "C" inpc_status inpc_query_hashgrid(const inpc_hashgrid_desc* g, const vo
   GridParams P;
   int64_t total = 0;
   INPC_TRY(make_params(g, P, &total));
-  if (n < 0 || n > INT32_MAX) return fail(INPC_ERR_CAPACITY, "n out of range");
+  if (n < 0 || n > (int64_t(1) << 29)) return fail(INPC_ERR_CAPACITY, "n must be in [0, 2^29]");
   if (n == 0) return INPC_OK;
   if (!table || !pos || !h_out) return fail(INPC_ERR_INVALID_ARG, "inpc_query_hashgrid: null pointer");
   const size_t ta = g->table_dtype == INPC_F32 ? 16 : 8, oa = g->out_dtype == INPC_F32 ? 16 : 8;

@@ -117,12 +117,13 @@ __device__ __forceinline__ bool splat_point(const RP& P, const float* __restrict
   return footprint(P.cam, u, v, s.f);
 }
 
-// Pixel of corner k (= a + 2b) of a footprint, or -1 if off-image.
-__device__ __forceinline__ long long corner_pixel(const RP& P, const Footprint& f, int k) {
+// Pixel of corner k (= a + 2b) of a footprint, or -1 if off-image (images
+// are at most 32768 x 32768, so the index fits in an int).
+__device__ __forceinline__ int corner_pixel(const RP& P, const Footprint& f, int k) {
   const int px = f.i0 + (k & 1);
   const int py = f.j0 + (k >> 1);
   if (px < 0 || px >= P.cam.W || py < 0 || py >= P.cam.H) return -1;
-  return (long long)py * P.cam.W + px;
+  return py * P.cam.W + px;
 }
 
 // Feature elements are FP32 or BF16; all arithmetic is FP32.
@@ -148,11 +149,12 @@ __global__ void __launch_bounds__(256) k_pix_count(RP P, const float* __restrict
                                                    uint32_t* __restrict__ pix_count) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  for (long long base = blockIdx.x * (long long)blockDim.x; base < P.n; base += (long long)gridDim.x * blockDim.x) {
-    const long long id = base + threadIdx.x;
-    long long q[4] = {-1, -1, -1, -1};
+  const int n = (int)P.n;  // <= 2^25
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int id = base + threadIdx.x;
+    int q[4] = {-1, -1, -1, -1};
     Splat s;
-    if (id < P.n && splat_point(P, pos, id, s))
+    if (id < n && splat_point(P, pos, id, s))
       for (int k = 0; k < 4; ++k) q[k] = corner_pixel(P, s.f, k);
     for (int k = 0; k < 4; ++k) {
       // leaf-grouped points are spatially coherent: aggregate equal pixels per warp
@@ -172,12 +174,13 @@ __global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restri
                                                      float* __restrict__ alpha, uint32_t* __restrict__ pslot) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  for (long long base = blockIdx.x * (long long)blockDim.x; base < P.n; base += (long long)gridDim.x * blockDim.x) {
-    const long long id = base + threadIdx.x;
-    long long q[4] = {-1, -1, -1, -1};
+  const int n = (int)P.n;  // <= 2^25
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int id = base + threadIdx.x;
+    int q[4] = {-1, -1, -1, -1};
     Splat s;
     float ah = 0.f;
-    if (id < P.n && splat_point(P, pos, id, s)) {
+    if (id < n && splat_point(P, pos, id, s)) {
       for (int k = 0; k < 4; ++k) q[k] = corner_pixel(P, s.f, k);
       ah = point_alpha_h(P, opacity, feat, id, nullptr);
     }
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restri
         alpha[slots[k]] = fminf(__fmul_rn(ah, corner_weight(s.f, k & 1, k >> 1)), P.alpha_max);
       }
     }
-    if (id < P.n) reinterpret_cast<uint4*>(pslot)[id] = make_uint4(slots[0], slots[1], slots[2], slots[3]);
+    if (id < n) reinterpret_cast<uint4*>(pslot)[id] = make_uint4(slots[0], slots[1], slots[2], slots[3]);
   }
 }
 

@@ -183,14 +183,22 @@ __device__ __forceinline__ void load_coarse(const T* __restrict__ arr, int64_t L
   __syncthreads();
 }
 
-// Smallest i with arr[i] > key (arr non-decreasing); L when none.
+// Order key of a searched value.  The CDF holds exact non-negative integers
+// as doubles, and non-negative doubles order like their IEEE-754 bit
+// patterns read as unsigned integers, so the searches compare 64-bit
+// integers (the same decisions, without the narrow FP64 pipe).
+__device__ __forceinline__ uint64_t ord(double x) { return (uint64_t)__double_as_longlong(x); }
+__device__ __forceinline__ uint32_t ord(uint32_t x) { return x; }
+
+// Smallest i with arr[i] > key (arr non-decreasing, non-negative); L when none.
 template <class T>
 __device__ __forceinline__ int64_t upper_bound2(const T* __restrict__ arr, int64_t L, const T* coarse, int n_coarse,
-                                                int stride_log2, T key) {
+                                                int stride_log2, T key_value) {
+  const auto key = ord(key_value);
   int lo = 0, hi = n_coarse;  // first coarse block whose last element exceeds key
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (coarse[mid] > key) hi = mid; else lo = mid + 1;
+    if (ord(coarse[mid]) > key) hi = mid; else lo = mid + 1;
   }
   if (lo == n_coarse) return L;
   int64_t a = (int64_t)lo << stride_log2;
@@ -198,7 +206,7 @@ __device__ __forceinline__ int64_t upper_bound2(const T* __restrict__ arr, int64
   if (b > L - 1) b = L - 1;
   while (a < b) {  // arr[b] > key holds
     const int64_t mid = (a + b) >> 1;
-    if (arr[mid] > key) b = mid; else a = mid + 1;
+    if (ord(arr[mid]) > key) b = mid; else a = mid + 1;
   }
   return a;
 }
@@ -366,11 +374,11 @@ __global__ void k_resample_round(const double* __restrict__ cdf, int64_t L, Cam 
     const U32x4 r = philox4x32_10((uint32_t)k, (uint32_t)((uint64_t)k >> 32), view_id, 2u + 2u * round, k0, k1);
     const uint64_t b = ((uint64_t)(r.y & 0x1FFFFFu) << 32) | (uint64_t)r.x;
     const uint64_t lo = b * Qi, hi = __umul64hi(b, Qi);
-    const double key = (double)((hi << 11) | (lo >> 53));
+    const uint64_t key = ord((double)((hi << 11) | (lo >> 53)));
     int64_t a = 0, z = L - 1;  // smallest i with cdf[i] > key
     while (a < z) {
       const int64_t mid = (a + z) >> 1;
-      if (cdf[mid] > key) z = mid; else a = mid + 1;
+      if (ord(cdf[mid]) > key) z = mid; else a = mid + 1;
     }
     const int64_t leaf = a;
     const U32x4 r2 = philox4x32_10((uint32_t)k, (uint32_t)((uint64_t)k >> 32), view_id, 3u + 2u * round, k0, k1);
