@@ -185,18 +185,28 @@ __global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restri
       ah = point_alpha_h(P, opacity, feat, id, nullptr);
     }
     const unsigned long long key = ((unsigned long long)__float_as_uint(s.d) << kIdBits) | (unsigned long long)id;
-    uint32_t slots[4];
+    // the four corners' bucket offsets and atomics are all issued before
+    // any result is used, so their round trips overlap
+    unsigned peers[4];
+    uint32_t start[4], top[4];
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const unsigned peers = __match_any_sync(full, q[k]);
-      const int leader = __ffs(peers) - 1;
-      uint32_t top = 0;
+      peers[k] = __match_any_sync(full, q[k]);
+      start[k] = q[k] >= 0 ? __ldg(pix_start + q[k]) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
       // counts run down from the bucket size, so the buckets fill back to front
-      if (q[k] >= 0 && lane == leader) top = atomicSub(pix_count + q[k], (uint32_t)__popc(peers));
-      top = __shfl_sync(peers, top, leader);
+      top[k] = 0;
+      if (q[k] >= 0 && lane == __ffs(peers[k]) - 1) top[k] = atomicSub(pix_count + q[k], (uint32_t)__popc(peers[k]));
+    }
+    uint32_t slots[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t t = __shfl_sync(peers[k], top[k], __ffs(peers[k]) - 1);
       slots[k] = kNoSlot;
       if (q[k] >= 0) {
-        const uint32_t local = top - 1 - __popc(peers & ((1u << lane) - 1));
-        slots[k] = pix_start[q[k]] + local;
+        slots[k] = start[k] + t - 1 - __popc(peers[k] & ((1u << lane) - 1));
         keys[slots[k]] = key;
         alpha[slots[k]] = fminf(__fmul_rn(ah, corner_weight(s.f, k & 1, k >> 1)), P.alpha_max);
       }
