@@ -25,9 +25,9 @@ constexpr int kScanItems = 8;
 constexpr int kScanBlock = kScanThreads * kScanItems;  // 2048 items per CTA
 constexpr int kCoarse = 2048;                          // coarse search table entries (shared memory)
 constexpr int kDrawThreads = 256;
-constexpr int kDrawPerThread = 8;
+constexpr int kDrawPerThread = 16;
 constexpr int kDrawPerCta = kDrawThreads * kDrawPerThread;
-constexpr int kHashSlots = 4096;                       // per-CTA leaf histogram (open addressing)
+constexpr int kSmemLeaves = 4096;  // trees up to this many leaves count their draws in shared memory
 
 struct SampleWs {
   uint32_t* status;          // header word 0
@@ -211,27 +211,25 @@ __device__ __forceinline__ int64_t upper_bound2(const T* __restrict__ arr, int64
   return a;
 }
 
-__device__ __forceinline__ uint32_t slot_hash(uint32_t k) {
-  k *= 0x9E3779B1u;
-  return k >> (32 - 12);  // kHashSlots = 4096
-}
-
+// Draws land on leaves at random, so a CTA's draws only repeat leaves when
+// the tree is small: then they are counted in shared memory (one counter
+// per leaf) and flushed once; otherwise each warp merges its equal leaves
+// and adds to the global counts directly.
+template <bool kSmem>
 __global__ void __launch_bounds__(kDrawThreads) k_draw_count(const double* __restrict__ cdf, int64_t L,
                                                              int stride_log2, int64_t n_draws, uint32_t k0,
                                                              uint32_t k1, uint32_t view_id,
                                                              uint32_t* __restrict__ counts) {
   __shared__ double coarse[kCoarse];
-  __shared__ int keys[kHashSlots];
-  __shared__ uint32_t vals[kHashSlots];
+  __shared__ uint32_t vals[kSmem ? kSmemLeaves : 1];
   int n_coarse;
-  for (int j = threadIdx.x; j < kHashSlots; j += blockDim.x) {
-    keys[j] = -1;
-    vals[j] = 0;
-  }
-  load_coarse<double>(cdf, L, stride_log2, coarse, n_coarse);
+  if (kSmem)
+    for (int j = threadIdx.x; j < L; j += blockDim.x) vals[j] = 0;
+  load_coarse<double>(cdf, L, stride_log2, coarse, n_coarse);  // ends with a barrier
   const double Q = cdf[L - 1];
   const uint64_t Qi = (uint64_t)Q;
   const int64_t base = (int64_t)blockIdx.x * kDrawPerCta;
+  const int lane = threadIdx.x & 31;
   for (int k = 0; k < kDrawPerThread; ++k) {
     const int64_t s = base + (int64_t)k * kDrawThreads + threadIdx.x;
     int leaf = -1;
@@ -246,25 +244,17 @@ __global__ void __launch_bounds__(kDrawThreads) k_draw_count(const double* __res
       if (i >= L) i = L - 1;  // only reachable when Q == 0 (flagged as a device status)
       leaf = (int)i;
     }
-    // warp pre-aggregation of equal leaves, then the shared-memory table
     const unsigned peers = __match_any_sync(0xffffffffu, leaf);
-    const int lane = threadIdx.x & 31;
     if (leaf >= 0 && lane == __ffs(peers) - 1) {
-      const uint32_t add = __popc(peers);
-      uint32_t h = slot_hash((uint32_t)leaf);
-      for (int probe = 0; probe < kHashSlots; ++probe) {
-        const int prev = atomicCAS(&keys[h], -1, leaf);
-        if (prev == -1 || prev == leaf) {
-          atomicAdd(&vals[h], add);
-          break;
-        }
-        h = (h + 1) & (kHashSlots - 1);
-      }
+      if (kSmem) atomicAdd(&vals[leaf], (uint32_t)__popc(peers));
+      else atomicAdd(&counts[leaf], (uint32_t)__popc(peers));
     }
   }
-  __syncthreads();
-  for (int j = threadIdx.x; j < kHashSlots; j += blockDim.x)
-    if (keys[j] >= 0) atomicAdd(&counts[keys[j]], vals[j]);
+  if (kSmem) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < L; j += blockDim.x)
+      if (vals[j]) atomicAdd(&counts[j], vals[j]);
+  }
 }
 
 __global__ void __launch_bounds__(256) k_place(const uint32_t* __restrict__ starts, int64_t L, int stride_log2,
@@ -553,9 +543,14 @@ inpc_status sample_impl(const inpc_octree* tree, uint64_t seed, uint32_t view_id
   const int sl = coarse_stride_log2(L);
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   if (n_samples > 0) {
-    INPC_TIMED("k_draw_count", s,
-               k_draw_count<<<(unsigned)ceil_div(n_samples, kDrawPerCta), kDrawThreads, 0, s>>>(
-                   ws.cdf, L, sl, n_samples, k0, k1, view_id, ws.counts));
+    const unsigned grid = (unsigned)ceil_div(n_samples, kDrawPerCta);
+    if (L <= kSmemLeaves)
+      INPC_TIMED("k_draw_count", s,
+                 k_draw_count<true><<<grid, kDrawThreads, 0, s>>>(ws.cdf, L, sl, n_samples, k0, k1, view_id, ws.counts));
+    else
+      INPC_TIMED("k_draw_count", s,
+                 k_draw_count<false><<<grid, kDrawThreads, 0, s>>>(ws.cdf, L, sl, n_samples, k0, k1, view_id,
+                                                                   ws.counts));
     INPC_TRY(check_launch("k_draw_count"));
   }
   INPC_TRY((scan<uint32_t, CountLoad, false>(CountLoad{ws.counts}, L, ws.starts, ws.count_tops, s)));
