@@ -24,8 +24,18 @@ namespace {
 // Coarse levels have few rows that would otherwise receive millions of
 // additions each.  Fine levels change vertex at almost every point and
 // reduce directly.
+// A point's values shared by its level lanes.
+struct __align__(16) PointRec {
+  int pix0;        // pixel of footprint corner 0 (j0 W + i0)
+  uint32_t mask;   // bit k: corner k has a fragment
+  float h0term;    // level-0 channel-0 gradient: the opacity path into h0
+  float x;
+  float4 sc;       // T_k alpha_k of the four fragments (0 without one)
+  float y, z, pad0, pad1;
+};
+
 template <int GA, class FT>
-__global__ void __launch_bounds__(kThreads, 5) k_point_grad_hash(RP P, GridParams Gp, const float* __restrict__ pos,
+__global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParams Gp, const float* __restrict__ pos,
                                                                const FT* __restrict__ feat,
                                                                const float* __restrict__ d_image, RasterWs ws,
                                                                float* __restrict__ grad_table,
@@ -33,6 +43,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_point_grad_hash(RP P, GridParam
   constexpr int kGroups = kThreads / GA;  // points in flight per CTA
   constexpr int kH = GA / 2;               // levels per half
   constexpr int kPW = 32 / kH;             // points per warp
+  constexpr int kBatch = 32 / kPW;         // iterations covered by one round of point records
   // warps come in pairs over the same kPW points: the even warp takes the
   // coarse half of the levels, the odd warp the fine half
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -57,84 +68,126 @@ __global__ void __launch_bounds__(kThreads, 5) k_point_grad_hash(RP P, GridParam
   // the cell whose corners the accumulators hold (kFar: none yet)
   constexpr uint32_t kFar = 1u << 30;
   uint32_t hx = kFar, hy = kFar, hz = kFar;
-  for (int id = first; id < last; id += kGroups) {
-    const uint4 sl = ld_hint_u4(reinterpret_cast<const uint4*>(ws.pslot) + id, stream);
-    const uint32_t slots[4] = {sl.x, sl.y, sl.z, sl.w};
-    float dc[4] = {0.f, 0.f, 0.f, 0.f};
-    if ((sl.x & sl.y & sl.z & sl.w) != kNoSlot) {
-      Splat s;
-      splat_point(P, pos, id, s);
-      float e_h0 = 0.f;
-      const float ah = point_alpha_h(P, nullptr, feat, id, &e_h0);
-      float2 sc[4];
+  __shared__ PointRec rec_s[kThreads / 32][32];
+  // Per-point values (fragment scalars, pixel, position, the h0 term) are
+  // formed once per point: each lane of a warp computes them for one of the
+  // next kBatch x kPW points into a record, and the level lanes then read
+  // the records, instead of every level lane repeating the projection and
+  // the fragment gathers.
+  PointRec* rec = rec_s[warp];
+  const int base = (int)blockIdx.x * chunk + (warp >> 1) * kPW;  // the warp's first point slot
+  for (int t0 = 0; base + t0 * kGroups < last; t0 += kBatch) {
+    {
+      const int pid = base + lane % kPW + (t0 + lane / kPW) * kGroups;
+      PointRec R;
+      R.mask = 0;
+      R.pix0 = 0;
+      R.h0term = 0.f;
+      R.sc = make_float4(0.f, 0.f, 0.f, 0.f);
+      R.x = R.y = R.z = 0.f;
+      if (pid < last) {
+        const uint4 sl = ld_hint_u4(reinterpret_cast<const uint4*>(ws.pslot) + pid, stream);
+        const uint32_t slots[4] = {sl.x, sl.y, sl.z, sl.w};
+        R.x = __ldg(pos + 3 * pid + 0);
+        R.y = __ldg(pos + 3 * pid + 1);
+        R.z = __ldg(pos + 3 * pid + 2);
+        if ((sl.x & sl.y & sl.z & sl.w) != kNoSlot) {
+          Splat sp;
+          splat_xyz(P, R.x, R.y, R.z, sp);
+          float e_h0 = 0.f;
+          const float ah = point_alpha_h(P, nullptr, feat, pid, &e_h0);
+          float2 sc[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) sc[k] = slots[k] == kNoSlot ? make_float2(0.f, 0.f) : ld_hint_f2(ws.fscal + slots[k], stream);
-      float dah = 0.f;
+          for (int k = 0; k < 4; ++k)
+            sc[k] = slots[k] == kNoSlot ? make_float2(0.f, 0.f) : ld_hint_f2(ws.fscal + slots[k], stream);
+          float dah = 0.f;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (slots[k] == kNoSlot) continue;
-        const float w = corner_weight(s.f, k & 1, k >> 1);
-        if (__fmul_rn(ah, w) <= P.alpha_max) dah = __fmaf_rn(w, sc[k].y, dah);
-        if (active) {
-          const long long pix = (long long)(s.f.j0 + (k >> 1)) * P.cam.W + (s.f.i0 + (k & 1));
-          const float4 g = __ldg(reinterpret_cast<const float4*>(d_image + pix * P.F + ch));
-          dc[0] = __fmaf_rn(sc[k].x, g.x, dc[0]);
-          dc[1] = __fmaf_rn(sc[k].x, g.y, dc[1]);
-          dc[2] = __fmaf_rn(sc[k].x, g.z, dc[2]);
-          dc[3] = __fmaf_rn(sc[k].x, g.w, dc[3]);
+          for (int k = 0; k < 4; ++k) {
+            if (slots[k] == kNoSlot) continue;
+            R.mask |= 1u << k;
+            const float w = corner_weight(sp.f, k & 1, k >> 1);
+            if (__fmul_rn(ah, w) <= P.alpha_max) dah = __fmaf_rn(w, sc[k].y, dah);
+          }
+          // channel 0 of the blended color is the constant 1; the opacity
+          // gradient reaches h0 through alpha_h = 1 - exp(-exp(h0))
+          R.h0term = dah * (e_h0 * expf(-e_h0));
+          R.pix0 = sp.f.j0 * P.cam.W + sp.f.i0;
+          R.sc = make_float4(sc[0].x, sc[1].x, sc[2].x, sc[3].x);
         }
       }
-      // channel 0 of the blended color is the constant 1; the opacity
-      // gradient reaches h0 through alpha_h = 1 - exp(-exp(h0))
-      if (l == 0) dc[0] = dah * (e_h0 * expf(-e_h0));
+      rec[lane] = R;
     }
-    if (!active) continue;
-    if (d_feat) *reinterpret_cast<float4*>(d_feat + (long long)id * P.F + ch) = make_float4(dc[0], dc[1], dc[2], dc[3]);
-    if (dc[0] == 0.f && dc[1] == 0.f && dc[2] == 0.f && dc[3] == 0.f) continue;
-    uint32_t cx, cy, cz;
-    float gx[2], gy[2], gz[2];
-    const int N = Gp.res[l];
-    cell_frac(__ldg(pos + 3 * id + 0), N, cx, gx[0], gx[1]);
-    cell_frac(__ldg(pos + 3 * id + 1), N, cy, gy[0], gy[1]);
-    cell_frac(__ldg(pos + 3 * id + 2), N, cz, gz[0], gz[1]);
-    // slot s holds the corner whose offsets are s's bits xor the cell's
-    // parities; swapping the weight pairs of odd cells makes gx[sx] that
-    // corner's weight
-    const uint32_t px = cx & 1u, py = cy & 1u, pz = cz & 1u;
-    const uint32_t qx = hx & 1u, qy = hy & 1u, qz = hz & 1u;
-    if (px) swap_f(gx[0], gx[1]);
-    if (py) swap_f(gy[0], gy[1]);
-    if (pz) swap_f(gz[0], gz[1]);
-    // per axis and parity: does the slot keep its vertex?
-    const bool kx[2] = {cx + px == hx + qx, cx + (px ^ 1u) == hx + (qx ^ 1u)};
-    const bool ky[2] = {cy + py == hy + qy, cy + (py ^ 1u) == hy + (qy ^ 1u)};
-    const bool kz[2] = {cz + pz == hz + qz, cz + (pz ^ 1u) == hz + (qz ^ 1u)};
-    if (coarse) {
-      const bool held = hx != kFar;
+    __syncwarp();
+    for (int t = 0; t < kBatch; ++t) {
+      const int id = first + (t0 + t) * kGroups;
+      if (id >= last) break;
+      const PointRec R = rec[t * kPW + lane / kH];
+      float dc[4] = {0.f, 0.f, 0.f, 0.f};
+      if (R.mask) {
+        const float scx[4] = {R.sc.x, R.sc.y, R.sc.z, R.sc.w};
+        if (active) {
 #pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        const uint32_t sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
-        const float w = gx[sx] * gy[sy] * gz[sz];
-        const float4 v = make_float4(w * dc[0], w * dc[1], w * dc[2], w * dc[3]);
-        const float4 a = acc[s * kStride];
-        const bool same = kx[sx] && ky[sy] && kz[sz];
-        acc[s * kStride] = same ? make_float4(a.x + v.x, a.y + v.y, a.z + v.z, a.w + v.w) : v;
-        // the slot moves to another vertex: send the old vertex its sum
-        if (!same && held)
-          red_add_v4(gl + 4ull * vertex_row(Gp, l, hx + (sx ^ qx), hy + (sy ^ qy), hz + (sz ^ qz)), a, keep);
+          for (int k = 0; k < 4; ++k) {
+            if (!(R.mask & (1u << k))) continue;
+            const int pix = R.pix0 + (k >> 1) * P.cam.W + (k & 1);
+            const float4 g = __ldg(reinterpret_cast<const float4*>(d_image + (long long)pix * P.F + ch));
+            dc[0] = __fmaf_rn(scx[k], g.x, dc[0]);
+            dc[1] = __fmaf_rn(scx[k], g.y, dc[1]);
+            dc[2] = __fmaf_rn(scx[k], g.z, dc[2]);
+            dc[3] = __fmaf_rn(scx[k], g.w, dc[3]);
+          }
+        }
+        if (l == 0) dc[0] = R.h0term;
       }
-    } else {
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        const uint32_t sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
-        const float w = gx[sx] * gy[sy] * gz[sz];
-        red_add_v4(gl + 4ull * vertex_row(Gp, l, cx + (sx ^ px), cy + (sy ^ py), cz + (sz ^ pz)),
-                   make_float4(w * dc[0], w * dc[1], w * dc[2], w * dc[3]), keep);
+      if (!active) continue;
+      if (d_feat) *reinterpret_cast<float4*>(d_feat + (long long)id * P.F + ch) = make_float4(dc[0], dc[1], dc[2], dc[3]);
+      if (dc[0] == 0.f && dc[1] == 0.f && dc[2] == 0.f && dc[3] == 0.f) continue;
+      uint32_t cx, cy, cz;
+      float gx[2], gy[2], gz[2];
+      const int N = Gp.res[l];
+      cell_frac(R.x, N, cx, gx[0], gx[1]);
+      cell_frac(R.y, N, cy, gy[0], gy[1]);
+      cell_frac(R.z, N, cz, gz[0], gz[1]);
+      // slot s holds the corner whose offsets are s's bits xor the cell's
+      // parities; swapping the weight pairs of odd cells makes gx[sx] that
+      // corner's weight
+      const uint32_t px = cx & 1u, py = cy & 1u, pz = cz & 1u;
+      const uint32_t qx = hx & 1u, qy = hy & 1u, qz = hz & 1u;
+      if (px) swap_f(gx[0], gx[1]);
+      if (py) swap_f(gy[0], gy[1]);
+      if (pz) swap_f(gz[0], gz[1]);
+      // per axis and parity: does the slot keep its vertex?
+      const bool kx[2] = {cx + px == hx + qx, cx + (px ^ 1u) == hx + (qx ^ 1u)};
+      const bool ky[2] = {cy + py == hy + qy, cy + (py ^ 1u) == hy + (qy ^ 1u)};
+      const bool kz[2] = {cz + pz == hz + qz, cz + (pz ^ 1u) == hz + (qz ^ 1u)};
+      if (coarse) {
+        const bool held = hx != kFar;
+  #pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const uint32_t sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
+          const float w = gx[sx] * gy[sy] * gz[sz];
+          const float4 v = make_float4(w * dc[0], w * dc[1], w * dc[2], w * dc[3]);
+          const float4 a = acc[s * kStride];
+          const bool same = kx[sx] && ky[sy] && kz[sz];
+          acc[s * kStride] = same ? make_float4(a.x + v.x, a.y + v.y, a.z + v.z, a.w + v.w) : v;
+          // the slot moves to another vertex: send the old vertex its sum
+          if (!same && held)
+            red_add_v4(gl + 4ull * vertex_row(Gp, l, hx + (sx ^ qx), hy + (sy ^ qy), hz + (sz ^ qz)), a, keep);
+        }
+      } else {
+  #pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const uint32_t sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
+          const float w = gx[sx] * gy[sy] * gz[sz];
+          red_add_v4(gl + 4ull * vertex_row(Gp, l, cx + (sx ^ px), cy + (sy ^ py), cz + (sz ^ pz)),
+                     make_float4(w * dc[0], w * dc[1], w * dc[2], w * dc[3]), keep);
+        }
       }
+      hx = cx;
+      hy = cy;
+      hz = cz;
     }
-    hx = cx;
-    hy = cy;
-    hz = cz;
+    __syncwarp();
   }
   if (!active || !coarse || hx == kFar) return;
   const uint32_t qx = hx & 1u, qy = hy & 1u, qz = hz & 1u;

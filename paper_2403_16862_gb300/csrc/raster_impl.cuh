@@ -110,11 +110,14 @@ struct Splat {
   float d;
 };
 
-__device__ __forceinline__ bool splat_point(const RP& P, const float* __restrict__ pos, long long id, Splat& s) {
+__device__ __forceinline__ bool splat_xyz(const RP& P, float x, float y, float z, Splat& s) {
   float u, v;
-  const float x = __ldg(pos + 3 * id), y = __ldg(pos + 3 * id + 1), z = __ldg(pos + 3 * id + 2);
   if (!project_point(P.cam, x, y, z, u, v, s.d)) return false;
   return footprint(P.cam, u, v, s.f);
+}
+
+__device__ __forceinline__ bool splat_point(const RP& P, const float* __restrict__ pos, long long id, Splat& s) {
+  return splat_xyz(P, __ldg(pos + 3 * id), __ldg(pos + 3 * id + 1), __ldg(pos + 3 * id + 2), s);
 }
 
 // Pixel of corner k (= a + 2b) of a footprint, or -1 if off-image (images
