@@ -61,6 +61,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
   const int last = (int)min((long long)(blockIdx.x + 1) * chunk, P.n);
   const uint64_t keep = l2_evict_last(), stream = l2_evict_first();
   float* gl = active ? grad_table + 4 * Gp.offset[l] : nullptr;
+  // this lane's level, hoisted: a row is x + y my + z mz (dense) or
+  // (x ^ y my ^ z mz) & mask (hashed), as in vertex_row
+  const bool dense = active && Gp.dense[active ? l : 0];
+  const uint32_t side = active ? Gp.side[l] : 1u;
+  const uint32_t my = dense ? side : 2654435761u, mz = dense ? side * side : 805459861u;
+  const uint32_t rmask = dense ? 0xffffffffu : Gp.hash_mask;
+  const int N = active ? Gp.res[l] : 1;
   // the coarse warps' corner accumulators, [corner slot][point slot][level]
   constexpr int kStride = kGroups * kH;
   __shared__ float4 acc_s[8][kStride];
@@ -144,7 +151,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
       if (dc[0] == 0.f && dc[1] == 0.f && dc[2] == 0.f && dc[3] == 0.f) continue;
       uint32_t cx, cy, cz;
       float gx[2], gy[2], gz[2];
-      const int N = Gp.res[l];
       cell_frac(R.x, N, cx, gx[0], gx[1]);
       cell_frac(R.y, N, cy, gy[0], gy[1]);
       cell_frac(R.z, N, cz, gz[0], gz[1]);
@@ -162,25 +168,36 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
       const bool kz[2] = {cz + pz == hz + qz, cz + (pz ^ 1u) == hz + (qz ^ 1u)};
       if (coarse) {
         const bool held = hx != kFar;
-  #pragma unroll
+        // the y and z terms of the held cell's rows of slots sy, sz
+        const uint32_t hyb[2] = {(hy + qy) * my, (hy + (qy ^ 1u)) * my};
+        const uint32_t hzb[2] = {(hz + qz) * mz, (hz + (qz ^ 1u)) * mz};
+#pragma unroll
         for (int s = 0; s < 8; ++s) {
           const uint32_t sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
           const float w = gx[sx] * gy[sy] * gz[sz];
-          const float4 v = make_float4(w * dc[0], w * dc[1], w * dc[2], w * dc[3]);
           const float4 a = acc[s * kStride];
           const bool same = kx[sx] && ky[sy] && kz[sz];
-          acc[s * kStride] = same ? make_float4(a.x + v.x, a.y + v.y, a.z + v.z, a.w + v.w) : v;
+          // same vertex: add to the sum; otherwise start a new sum (fma onto 0)
+          acc[s * kStride] = make_float4(__fmaf_rn(w, dc[0], same ? a.x : 0.f), __fmaf_rn(w, dc[1], same ? a.y : 0.f),
+                                         __fmaf_rn(w, dc[2], same ? a.z : 0.f), __fmaf_rn(w, dc[3], same ? a.w : 0.f));
           // the slot moves to another vertex: send the old vertex its sum
-          if (!same && held)
-            red_add_v4(gl + 4ull * vertex_row(Gp, l, hx + (sx ^ qx), hy + (sy ^ qy), hz + (sz ^ qz)), a, keep);
+          if (!same && held) {
+            const uint32_t X = hx + (sx ^ qx);
+            const uint32_t row = dense ? X + hyb[sy] + hzb[sz] : ((X ^ hyb[sy] ^ hzb[sz]) & rmask);
+            red_add_v4(gl + 4ull * row, a, keep);
+          }
         }
       } else {
-  #pragma unroll
+        // the y and z terms of this cell's rows of slots sy, sz
+        const uint32_t yb[2] = {(cy + py) * my, (cy + (py ^ 1u)) * my};
+        const uint32_t zb[2] = {(cz + pz) * mz, (cz + (pz ^ 1u)) * mz};
+#pragma unroll
         for (int s = 0; s < 8; ++s) {
           const uint32_t sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
           const float w = gx[sx] * gy[sy] * gz[sz];
-          red_add_v4(gl + 4ull * vertex_row(Gp, l, cx + (sx ^ px), cy + (sy ^ py), cz + (sz ^ pz)),
-                     make_float4(w * dc[0], w * dc[1], w * dc[2], w * dc[3]), keep);
+          const uint32_t X = cx + (sx ^ px);
+          const uint32_t row = dense ? X + yb[sy] + zb[sz] : ((X ^ yb[sy] ^ zb[sz]) & rmask);
+          red_add_v4(gl + 4ull * row, make_float4(w * dc[0], w * dc[1], w * dc[2], w * dc[3]), keep);
         }
       }
       hx = cx;
