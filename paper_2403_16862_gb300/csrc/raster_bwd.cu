@@ -5,10 +5,16 @@
 namespace inpc {
 namespace {
 
-// Per point, one lane per grid level (its 4 features): the point's gradient
-// row, gathered as in k_point_grad, then that level's eight corner
+// Per point and grid level (its 4 features), two lanes: the point's gradient
+// row for that level, gathered as in k_point_grad, then the level's corner
 // contributions to the table gradient straight from registers (the adjoint
 // of the query, as in k_hash_bwd), so the row never goes through memory.
+// The two lanes own the cell's two x vertices, so each issues four of the
+// eight corner reductions, and a pair's two reductions (x and x + 1 with
+// the same y, z: rows differing in their low bits) usually share a 128-byte
+// line, one L1 wavefront.  Values that depend on the point only (fragment
+// scalars, footprint, position, the h0 term) are formed once per point, one
+// lane per point, into shared-memory records that the level lanes read.
 //
 // The levels are split in halves over a pair of warps that share the same
 // points: the even warp takes the coarse half, the odd warp the fine half.
@@ -40,18 +46,24 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
                                                                const float* __restrict__ d_image, RasterWs ws,
                                                                float* __restrict__ grad_table,
                                                                float* __restrict__ d_feat, int chunk) {
-  constexpr int kGroups = kThreads / GA;  // points in flight per CTA
-  constexpr int kH = GA / 2;               // levels per half
-  constexpr int kPW = 32 / kH;             // points per warp
-  constexpr int kBatch = 32 / kPW;         // iterations covered by one round of point records
+  constexpr int kH = GA / 2;                      // levels per half
+  constexpr int kPW = 16 / kH;                    // points per warp (two lanes per level)
+  constexpr int kGroups = (kThreads / 64) * kPW;  // points in flight per CTA
+  constexpr int kBatch = 32 / kPW;                // iterations covered by one round of point records
   // warps come in pairs over the same kPW points: the even warp takes the
-  // coarse half of the levels, the odd warp the fine half
+  // coarse half of the levels, the odd warp the fine half.  Each level has
+  // two adjacent lanes, one per x vertex of the cell (bx = the vertex's x
+  // parity): the pair's reductions usually fall in one 128-byte line and
+  // cost one L1 wavefront instead of two.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool coarse = (warp & 1) == 0;
-  const int l = (coarse ? 0 : kH) + lane % kH;
+  const uint32_t bx = lane & 1u;
+  const int lvl = (lane >> 1) % kH;
+  const int l = (coarse ? 0 : kH) + lvl;
   const int ch = 4 * l;
   const bool active = l < Gp.n_levels;
-  const int slot = (warp >> 1) * kPW + lane / kH;
+  const int pw = lane / (2 * kH);
+  const int slot = (warp >> 1) * kPW + pw;
   // the CTA takes `chunk` consecutive points; its point slots interleave
   // over them, so at any moment its warps work on neighbouring points
   // (shared image and fragment data in L1) while each slot's own sequence,
@@ -68,10 +80,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
   const uint32_t my = dense ? side : 2654435761u, mz = dense ? side * side : 805459861u;
   const uint32_t rmask = dense ? 0xffffffffu : Gp.hash_mask;
   const int N = active ? Gp.res[l] : 1;
-  // the coarse warps' corner accumulators, [corner slot][point slot][level]
-  constexpr int kStride = kGroups * kH;
-  __shared__ float4 acc_s[8][kStride];
-  float4* acc = &acc_s[0][slot * kH + lane % kH];
+  // the coarse warps' corner accumulators, [y-z corner][point slot][level][x side]
+  constexpr int kStride = kGroups * kH * 2;
+  __shared__ float4 acc_s[4][kStride];
+  float4* acc = &acc_s[0][(slot * kH + lvl) * 2 + bx];
   // the cell whose corners the accumulators hold (kFar: none yet)
   constexpr uint32_t kFar = 1u << 30;
   uint32_t hx = kFar, hy = kFar, hz = kFar;
@@ -128,7 +140,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
     for (int t = 0; t < kBatch; ++t) {
       const int id = first + (t0 + t) * kGroups;
       if (id >= last) break;
-      const PointRec R = rec[t * kPW + lane / kH];
+      const PointRec R = rec[t * kPW + pw];
       float dc[4] = {0.f, 0.f, 0.f, 0.f};
       if (R.mask) {
         const float scx[4] = {R.sc.x, R.sc.y, R.sc.z, R.sc.w};
@@ -147,7 +159,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
         if (l == 0) dc[0] = R.h0term;
       }
       if (!active) continue;
-      if (d_feat) *reinterpret_cast<float4*>(d_feat + (long long)id * P.F + ch) = make_float4(dc[0], dc[1], dc[2], dc[3]);
+      if (d_feat && bx == 0)
+        *reinterpret_cast<float4*>(d_feat + (long long)id * P.F + ch) = make_float4(dc[0], dc[1], dc[2], dc[3]);
       if (dc[0] == 0.f && dc[1] == 0.f && dc[2] == 0.f && dc[3] == 0.f) continue;
       uint32_t cx, cy, cz;
       float gx[2], gy[2], gz[2];
@@ -155,35 +168,36 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
       cell_frac(R.y, N, cy, gy[0], gy[1]);
       cell_frac(R.z, N, cz, gz[0], gz[1]);
       // slot s holds the corner whose offsets are s's bits xor the cell's
-      // parities; swapping the weight pairs of odd cells makes gx[sx] that
-      // corner's weight
+      // parities; swapping the weight pairs of odd cells makes gy[sy] that
+      // corner's weight.  Along x this lane owns the vertex of parity bx.
       const uint32_t px = cx & 1u, py = cy & 1u, pz = cz & 1u;
       const uint32_t qx = hx & 1u, qy = hy & 1u, qz = hz & 1u;
-      if (px) swap_f(gx[0], gx[1]);
+      const uint32_t X = cx + (bx ^ px);
+      const float wx = (bx ^ px) ? gx[1] : gx[0];
       if (py) swap_f(gy[0], gy[1]);
       if (pz) swap_f(gz[0], gz[1]);
-      // per axis and parity: does the slot keep its vertex?
-      const bool kx[2] = {cx + px == hx + qx, cx + (px ^ 1u) == hx + (qx ^ 1u)};
-      const bool ky[2] = {cy + py == hy + qy, cy + (py ^ 1u) == hy + (qy ^ 1u)};
-      const bool kz[2] = {cz + pz == hz + qz, cz + (pz ^ 1u) == hz + (qz ^ 1u)};
       if (coarse) {
+        // does the slot keep its vertex?
+        const uint32_t HX = hx + (bx ^ qx);
+        const bool kx = X == HX;
+        const bool ky[2] = {cy + py == hy + qy, cy + (py ^ 1u) == hy + (qy ^ 1u)};
+        const bool kz[2] = {cz + pz == hz + qz, cz + (pz ^ 1u) == hz + (qz ^ 1u)};
         const bool held = hx != kFar;
         // the y and z terms of the held cell's rows of slots sy, sz
         const uint32_t hyb[2] = {(hy + qy) * my, (hy + (qy ^ 1u)) * my};
         const uint32_t hzb[2] = {(hz + qz) * mz, (hz + (qz ^ 1u)) * mz};
 #pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          const uint32_t sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
-          const float w = gx[sx] * gy[sy] * gz[sz];
+        for (int s = 0; s < 4; ++s) {
+          const uint32_t sy = s & 1, sz = s >> 1;
+          const float w = wx * gy[sy] * gz[sz];
           const float4 a = acc[s * kStride];
-          const bool same = kx[sx] && ky[sy] && kz[sz];
+          const bool same = kx && ky[sy] && kz[sz];
           // same vertex: add to the sum; otherwise start a new sum (fma onto 0)
           acc[s * kStride] = make_float4(__fmaf_rn(w, dc[0], same ? a.x : 0.f), __fmaf_rn(w, dc[1], same ? a.y : 0.f),
                                          __fmaf_rn(w, dc[2], same ? a.z : 0.f), __fmaf_rn(w, dc[3], same ? a.w : 0.f));
           // the slot moves to another vertex: send the old vertex its sum
           if (!same && held) {
-            const uint32_t X = hx + (sx ^ qx);
-            const uint32_t row = dense ? X + hyb[sy] + hzb[sz] : ((X ^ hyb[sy] ^ hzb[sz]) & rmask);
+            const uint32_t row = dense ? HX + hyb[sy] + hzb[sz] : ((HX ^ hyb[sy] ^ hzb[sz]) & rmask);
             red_add_v4(gl + 4ull * row, a, keep);
           }
         }
@@ -192,10 +206,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
         const uint32_t yb[2] = {(cy + py) * my, (cy + (py ^ 1u)) * my};
         const uint32_t zb[2] = {(cz + pz) * mz, (cz + (pz ^ 1u)) * mz};
 #pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          const uint32_t sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
-          const float w = gx[sx] * gy[sy] * gz[sz];
-          const uint32_t X = cx + (sx ^ px);
+        for (int s = 0; s < 4; ++s) {
+          const uint32_t sy = s & 1, sz = s >> 1;
+          const float w = wx * gy[sy] * gz[sz];
           const uint32_t row = dense ? X + yb[sy] + zb[sz] : ((X ^ yb[sy] ^ zb[sz]) & rmask);
           red_add_v4(gl + 4ull * row, make_float4(w * dc[0], w * dc[1], w * dc[2], w * dc[3]), keep);
         }
@@ -209,10 +222,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
   if (!active || !coarse || hx == kFar) return;
   const uint32_t qx = hx & 1u, qy = hy & 1u, qz = hz & 1u;
 #pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    const uint32_t sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
-    red_add_v4(gl + 4ull * vertex_row(Gp, l, hx + (sx ^ qx), hy + (sy ^ qy), hz + (sz ^ qz)), acc[s * kStride],
-               keep);
+  for (int s = 0; s < 4; ++s) {
+    const uint32_t sy = s & 1, sz = s >> 1;
+    red_add_v4(gl + 4ull * vertex_row(Gp, l, hx + (bx ^ qx), hy + (sy ^ qy), hz + (sz ^ qz)), acc[s * kStride], keep);
   }
 }
 
@@ -220,7 +232,7 @@ template <int GA, class FT>
 inpc_status launch_point_grad_hash(const RP& P, const GridParams& Gp, const float* pos, const FT* feat,
                                    const float* d_image, const RasterWs& ws, float* grad_table, float* d_feat,
                                    cudaStream_t s) {
-  constexpr int kGroups = kThreads / GA;
+  constexpr int kGroups = (kThreads / 64) * (32 / GA);  // points in flight per CTA
   // kRun points per group and CTA chunk, as many CTAs as that needs up to
   // 32 per SM (longer runs beyond that)
   constexpr long long kRun = 48;

@@ -34,6 +34,16 @@ def test_small_trees(gpu, oracle):
         _check(t, seed=7 + seed, view=seed, n=100_000 + 37 * seed, dev=gpu, oracle=oracle)
 
 
+def test_count_paths(gpu, oracle):
+    """Trees up to 4,096 leaves count their draws per CTA in shared memory,
+    larger ones with warp-merged global additions: both sides of the
+    threshold, and a 64-leaf tree whose counters take many draws each."""
+    for n_leaves, start in ((64, 2), (4096, 4), (4096 + 7, 4)):
+        t = scenes.make_octree(11, n_leaves, start_level=start)
+        assert t.n_leaves == n_leaves
+        _check(t, seed=13, view=2, n=300_001, dev=gpu, oracle=oracle)
+
+
 def test_full_size_octree_4m_samples(gpu, oracle):
     """65,536-leaf octree, 4,194,304 samples: the sampling step of the
     full-size workload, in the launch configuration the benchmark times."""
