@@ -81,10 +81,10 @@ KERNELS = ["k_draw_count", "k_place", "k_hash_fwd", "k_pix_count", "k_pix_scatte
 
 # DRAM bytes per launch of the dominant kernel on the full workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); see profiles/.
-TRAFFIC = {"k_point_grad_hash": 2.52e9 + 0.63208e9}
+TRAFFIC = {"k_point_grad_hash": 2.74e9 + 0.71932e9}
 # L2 vector-reduction requests of one launch of the dominant kernel on the full
 # workload (lts__t_requests_op_red.sum, one ncu capture); see profiles/.
-L2_REDUCTIONS = {"k_point_grad_hash": 418_879_860}
+L2_REDUCTIONS = {"k_point_grad_hash": 243_135_594}
 
 
 def kernel_bytes(kernel, n, n_entries, n_frag, n_pix):
