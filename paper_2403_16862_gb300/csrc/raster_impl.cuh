@@ -582,11 +582,15 @@ __device__ __forceinline__ ChunkT<GA> chunk_transmittance(const Group<GA>& G, co
 // position in the low 8 bits (key << 8 | position), which locates its alpha.
 constexpr int kRegMax = 8;
 
+// Stages up to block size k leave the lowest k elements sorted ascending;
+// elements at or above m are the maximum key, so a bucket of m <= k needs
+// no later stage (m is uniform over the group).
 template <int GA, int R>
-__device__ __forceinline__ void reg_sort(const Group<GA>& G, unsigned long long (&key)[R]) {
+__device__ __forceinline__ void reg_sort(const Group<GA>& G, unsigned long long (&key)[R], int m = GA * R) {
   constexpr int P2 = GA * R;
 #pragma unroll
   for (int k = 2; k <= P2; k <<= 1) {
+    if ((k >> 1) >= m) break;
 #pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
       if (j >= GA) {
@@ -624,7 +628,7 @@ __device__ __forceinline__ void load_sorted(const Group<GA>& G, const unsigned l
     const int e = r * GA + G.lg;
     key[r] = e < m ? (keys[s0 + e] << 8) | (unsigned long long)e : ~0ull;
   }
-  reg_sort<GA, R>(G, key);
+  reg_sort<GA, R>(G, key, m);
 }
 
 __device__ __forceinline__ long long reg_id(unsigned long long k) { return (long long)((k >> 8) & kIdMask); }
@@ -699,8 +703,38 @@ template <class FT, int R>
 __device__ void blend_fwd_slots(const Group<32>& G, const RP& P, const RasterWs& ws, uint32_t s0, int m,
                                 long long pix, const FT* __restrict__ feat, FT* __restrict__ image,
                                 float* __restrict__ T_final, int32_t* __restrict__ n_contrib) {
+  if (m == 0) {  // no fragment: the background
+    Slot64<FT>::store2(image + pix * 64, 2 * G.lg, 0.f, 0.f);
+    if (G.lg == 0) {
+      T_final[pix] = 1.0f;
+      n_contrib[pix] = 0;
+    }
+    return;
+  }
   unsigned long long key[R];
+  // Small buckets (R <= 2): the alphas are loaded in bucket order beside the
+  // keys, and after the sort each lane takes its fragment's alpha from the
+  // lane that loaded that bucket position, instead of gathering it after
+  // the sort (one dependent round trip less per pixel).
+  float a_in[R];
+  if constexpr (R <= 2) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int e = r * 32 + G.lg;
+      a_in[r] = e < m ? ws.alpha[s0 + e] : 0.f;
+    }
+  }
   load_sorted<32, R>(G, ws.keys, s0, m, key);
+  float a_sorted[R];
+  if constexpr (R <= 2) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t pos = reg_pos(key[r]);
+      const float v0 = __shfl_sync(0xffffffffu, a_in[0], pos & 31);
+      const float v1 = R == 2 ? __shfl_sync(0xffffffffu, a_in[R - 1], pos & 31) : 0.f;
+      a_sorted[r] = (R == 2 && (pos >> 5) == 1) ? v1 : v0;
+    }
+  }
   const int q = G.lg & 3, f = G.lg >> 2;
   float acc[16];
 #pragma unroll
@@ -712,7 +746,9 @@ __device__ void blend_fwd_slots(const Group<32>& G, const RP& P, const RasterWs&
     const int b = r * 32;
     if (b >= m) break;
     const bool valid = b + G.lg < m;
-    const float a = valid ? ws.alpha[s0 + reg_pos(key[r])] : 0.f;
+    float a = 0.f;
+    if constexpr (R <= 2) a = valid ? a_sorted[r] : 0.f;
+    else a = valid ? ws.alpha[s0 + reg_pos(key[r])] : 0.f;
     const uint32_t id = valid ? (uint32_t)reg_id(key[r]) : 0u;
     const ChunkT<32> ct = chunk_transmittance<32>(G, P, a, valid, min(32, m - b), T);
     const float wk = __fmul_rn(ct.Tk, a);
