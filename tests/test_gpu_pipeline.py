@@ -102,3 +102,43 @@ def test_pipeline_full_size(gpu, oracle):
     """65,536 leaves, 4,194,304 samples, 2^19 grid, 1280x832, fwd + bwd."""
     cam = scenes.make_camera((0.5, 0.5, -1.2), 900, 900, 640, 416, 1280, 832)
     _pipeline(gpu, oracle, 65536, 4_194_304, 19, cam, seed=0)
+
+
+@pytest.mark.parametrize("n_levels", [6, 8, 24, 32])
+def test_fused_backward_level_counts(gpu, oracle, n_levels):
+    """The fused rasterizer backward + grid adjoint for level counts other
+    than 16 (its 8-, 16- and 32-lane layouts; levels past the count idle),
+    on a 2^14 grid so that coarse levels are dense and the rest hashed."""
+    res = scenes.geometric_resolutions(n_levels, 16, 1024)
+    log2_T, F, n_samples = 14, 4 * n_levels, 60_000
+    tree = scenes.make_octree(4, 4096 + 7 * 200)
+    grid = scenes.make_hashgrid(5, oracle.hash_entries(res, log2_T), res, log2_T)
+    cam = scenes.make_camera((0.5, 0.5, -1.2), 900 * 0.125, 900 * 0.125, 80, 52, 160, 104)
+    g_img = scenes.upstream_grad(6, (cam.height, cam.width, F))
+    c, l, w = (torch.from_numpy(x).to(gpu) for x in (tree.centers, tree.levels, tree.weights))
+    table = torch.from_numpy(grid.table).to(gpu)
+    desc = api.hashgrid_desc(res, log2_T)
+    opts = api.RasterOptions(n_channels=F, head_mode=True)
+    _, pos = api.sample_octree(c, l, w, tree.root_size, 4, 0, n_samples)
+    h = api.query_hashgrid(desc, table, pos)
+    ws = api.workspace(api.rasterize_bwd_hashgrid_workspace_size(cam, opts, desc, n_samples), gpu)
+    img, T, n, ws = api.rasterize_fwd(cam, opts, pos, h, ws=ws)
+    gt = torch.zeros_like(table)
+    dh = torch.empty(n_samples, F, dtype=torch.float32, device=gpu)
+    api.rasterize_bwd_hashgrid(cam, opts, desc, pos, h, T, n, torch.from_numpy(g_img).to(gpu), ws, gt, d_feat=dh)
+    torch.cuda.synchronize()
+
+    _, o_pos64, _ = oracle.sample_octree(tree, 4, 0, n_samples)
+    o_pos = o_pos64.astype(np.float32)
+    o_h, o_hab = oracle.hash_fwd(res, log2_T, grid.table, o_pos, with_abs=True)
+    ref = oracle.raster_fwd(cam, o_pos, o_h, head_mode=True, with_abs=True, feat_abs=o_hab)
+    rb = oracle.raster_bwd(cam, o_pos, o_h, g_img, head_mode=True, with_abs=True, feat_abs=o_hab)
+    o_gt, o_gab = oracle.hash_bwd(res, log2_T, 4, o_pos, rb["d_feat"], with_abs=True, dh_abs=rb["abs_feat"])
+    ok = ref["flags"] == 0
+    assert (~ok).sum() <= max(2, 1e-4 * ok.size)
+    assert_cond_close(img.cpu().numpy(), ref["image"], ref["abs"], mask=ok[..., None], what="image")
+    keep = ~_excluded_points(oracle, cam, o_pos, ref["flags"])
+    assert_cond_close(dh.cpu().numpy(), rb["d_feat"], rb["abs_feat"], mask=keep[:, None], what="dh")
+    reach = oracle.hash_bwd(res, log2_T, 4, o_pos, np.repeat((~keep)[:, None], F, 1).astype(np.float64))
+    assert_cond_close(gt.cpu().numpy(), o_gt, o_gab, mask=reach == 0, what="grad_table (fused)")
+    assert np.abs(o_gt).max() > 0
