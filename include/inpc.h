@@ -125,7 +125,7 @@ inpc_status inpc_sample_octree(const inpc_octree* tree, uint64_t seed, uint32_t 
  * cudaMalloc, or a plugin that is handed buffers but no allocation rights.
  * They still pass the octree and the output arrays; the sampler's scratch
  * lives in a file-scope device array of INPC_SAMPLE_STATIC_SCRATCH_BYTES
- * (4 MiB + 64 KiB: about 262,000 leaves), which every GPU that loads this
+ * (4 MiB + 576 KiB: about 266,000 leaves), which every GPU that loads this
  * library holds until the process exits.
  *   - Same definition, outputs and device status bits as inpc_sample_octree
  *     (the status word sits at the start of the static array).
@@ -138,7 +138,7 @@ inpc_status inpc_sample_octree(const inpc_octree* tree, uint64_t seed, uint32_t 
  *     a device shares the one array, each call clears what must start at
  *     zero, and calls whose GPU work overlaps (other streams, other host
  *     threads) race on it. */
-#define INPC_SAMPLE_STATIC_SCRATCH_BYTES ((4u << 20) + (64u << 10))
+#define INPC_SAMPLE_STATIC_SCRATCH_BYTES ((4u << 20) + (576u << 10))
 inpc_status inpc_sample_octree_noalloc(const inpc_octree* tree, uint64_t seed, uint32_t view_id, int64_t n_samples,
                                        int32_t* leaf_idx_out, float* pos_out, int32_t* leaf_counts_out,
                                        inpc_stream_t stream);

@@ -37,8 +37,17 @@ struct SampleWs {
   uint32_t* counts;          // [L]
   uint32_t* starts;          // [L]
   uint32_t* count_tops;      // [nb]
+  uint32_t* guide;           // [2^guide_log2(L) + 1]
   size_t bytes;
 };
+
+// Draw buckets: the top guide_log2(L) bits of a draw's 53-bit random number
+// (about two leaves per bucket).
+int guide_log2(int64_t L) {
+  int f = 0;
+  while ((int64_t(1) << (f + 1)) <= L) ++f;  // floor(log2 L)
+  return f > 0 ? f - 1 : 0;
+}
 
 SampleWs carve(void* base, int64_t L) {
   Carver c(base);
@@ -51,6 +60,7 @@ SampleWs carve(void* base, int64_t L) {
   w.counts = c.take<uint32_t>(L);
   w.starts = c.take<uint32_t>(L);
   w.count_tops = c.take<uint32_t>(nb);
+  w.guide = c.take<uint32_t>((int64_t(1) << guide_log2(L)) + 1);
   w.bytes = c.bytes();
   return w;
 }
@@ -211,21 +221,56 @@ __device__ __forceinline__ int64_t upper_bound2(const T* __restrict__ arr, int64
   return a;
 }
 
+// Guide table (an indexed search): a draw's value r = floor(b Q / 2^53)
+// from the 53-bit random b lies, for b in bucket j = b >> (53 - G_l), in
+// [floor(j Q / 2^G_l), floor((j + 1) Q / 2^G_l)], and the leaf of r (the
+// smallest i with cdf[i] > r) is monotone in r, so guide[j] = the leaf of
+// floor(j Q / 2^G_l) and guide[j + 1] bound it.  The bucket bounds are
+// formed exactly from the 128-bit product j Q.
+__global__ void k_guide(const double* __restrict__ cdf, int64_t L, int Gl, uint32_t* __restrict__ guide) {
+  const uint64_t Q = (uint64_t)cdf[L - 1];
+  const int64_t G = int64_t(1) << Gl;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= G; j += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t pl = (uint64_t)j * Q, ph = __umul64hi((uint64_t)j, Q);
+    const uint64_t lo = Gl == 0 ? pl : ((ph << (64 - Gl)) | (pl >> Gl));
+    const uint64_t key = ord((double)lo);  // lo <= Q <= 2^53: exact
+    int64_t a = 0, z = L;                  // smallest i with cdf[i] > lo; L when none
+    while (a < z) {
+      const int64_t mid = (a + z) >> 1;
+      if (ord(cdf[mid]) > key) z = mid; else a = mid + 1;
+    }
+    guide[j] = (uint32_t)a;
+  }
+}
+
+// Leaf of a draw: the smallest i with cdf[i] > r (key = the bits of r as a
+// double), searched between the guide entries of the draw's bucket j.
+// Returns L only when Q == 0 (flagged as a device status).
+__device__ __forceinline__ int64_t guided_leaf(const double* __restrict__ cdf, int64_t L,
+                                               const uint32_t* __restrict__ guide, uint32_t j, uint64_t key) {
+  int64_t a = guide[j], z = guide[j + 1];
+  if (z > L - 1) z = L - 1;
+  while (a < z) {  // cdf[z] > r holds
+    const int64_t mid = (a + z) >> 1;
+    if (ord(cdf[mid]) > key) z = mid; else a = mid + 1;
+  }
+  return a;
+}
+
 // Draws land on leaves at random, so a CTA's draws only repeat leaves when
 // the tree is small: then they are counted in shared memory (one counter
 // per leaf) and flushed once; otherwise each warp merges its equal leaves
 // and adds to the global counts directly.
 template <bool kSmem>
 __global__ void __launch_bounds__(kDrawThreads) k_draw_count(const double* __restrict__ cdf, int64_t L,
-                                                             int stride_log2, int64_t n_draws, uint32_t k0,
-                                                             uint32_t k1, uint32_t view_id,
-                                                             uint32_t* __restrict__ counts) {
-  __shared__ double coarse[kCoarse];
+                                                             const uint32_t* __restrict__ guide, int Gl,
+                                                             int64_t n_draws, uint32_t k0, uint32_t k1,
+                                                             uint32_t view_id, uint32_t* __restrict__ counts) {
   __shared__ uint32_t vals[kSmem ? kSmemLeaves : 1];
-  int n_coarse;
-  if (kSmem)
+  if (kSmem) {
     for (int j = threadIdx.x; j < L; j += blockDim.x) vals[j] = 0;
-  load_coarse<double>(cdf, L, stride_log2, coarse, n_coarse);  // ends with a barrier
+    __syncthreads();
+  }
   const double Q = cdf[L - 1];
   const uint64_t Qi = (uint64_t)Q;
   const int64_t base = (int64_t)blockIdx.x * kDrawPerCta;
@@ -240,7 +285,7 @@ __global__ void __launch_bounds__(kDrawThreads) k_draw_count(const double* __res
       const uint64_t lo = b * Qi;
       const uint64_t hi = __umul64hi(b, Qi);
       const uint64_t rr = (hi << 11) | (lo >> 53);
-      int64_t i = upper_bound2<double>(cdf, L, coarse, n_coarse, stride_log2, (double)rr);
+      int64_t i = guided_leaf(cdf, L, guide, (uint32_t)(b >> (53 - Gl)), ord((double)rr));
       if (i >= L) i = L - 1;  // only reachable when Q == 0 (flagged as a device status)
       leaf = (int)i;
     }
@@ -354,7 +399,8 @@ __device__ __forceinline__ bool in_view(const Cam& c, const float* p) {
 
 // One re-sampling round: every sample not in view draws a new leaf from the
 // CDF (Philox purpose 2 + 2 round) and a new position in it (3 + 2 round).
-__global__ void k_resample_round(const double* __restrict__ cdf, int64_t L, Cam cam, int64_t n, uint32_t k0,
+__global__ void k_resample_round(const double* __restrict__ cdf, int64_t L, const uint32_t* __restrict__ guide,
+                                 int Gl, Cam cam, int64_t n, uint32_t k0,
                                  uint32_t k1, uint32_t view_id, uint32_t round, const float* __restrict__ centers,
                                  const int32_t* __restrict__ levels, float root_size, int32_t* __restrict__ leaf_out,
                                  float* __restrict__ pos_out) {
@@ -364,13 +410,8 @@ __global__ void k_resample_round(const double* __restrict__ cdf, int64_t L, Cam 
     const U32x4 r = philox4x32_10((uint32_t)k, (uint32_t)((uint64_t)k >> 32), view_id, 2u + 2u * round, k0, k1);
     const uint64_t b = ((uint64_t)(r.y & 0x1FFFFFu) << 32) | (uint64_t)r.x;
     const uint64_t lo = b * Qi, hi = __umul64hi(b, Qi);
-    const uint64_t key = ord((double)((hi << 11) | (lo >> 53)));
-    int64_t a = 0, z = L - 1;  // smallest i with cdf[i] > key
-    while (a < z) {
-      const int64_t mid = (a + z) >> 1;
-      if (ord(cdf[mid]) > key) z = mid; else a = mid + 1;
-    }
-    const int64_t leaf = a;
+    int64_t leaf = guided_leaf(cdf, L, guide, (uint32_t)(b >> (53 - Gl)), ord((double)((hi << 11) | (lo >> 53))));
+    if (leaf >= L) leaf = L - 1;
     const U32x4 r2 = philox4x32_10((uint32_t)k, (uint32_t)((uint64_t)k >> 32), view_id, 3u + 2u * round, k0, k1);
     const float edge = ldexpf(root_size, -levels[leaf]);
     leaf_out[k] = (int32_t)leaf;
@@ -540,17 +581,22 @@ inpc_status sample_impl(const inpc_octree* tree, uint64_t seed, uint32_t view_id
   INPC_TRY((scan<double, QuantLoad, true>(QuantLoad{tree->weights, ws.wmax}, L, ws.cdf, ws.cdf_tops, s)));
   k_check_total<<<1, 32, 0, s>>>(ws.cdf, L, ws.status);
   INPC_TRY(check_launch("k_check_total"));
+  const int Gl = guide_log2(L);
+  k_guide<<<(unsigned)std::min<int64_t>(ceil_div((int64_t(1) << Gl) + 1, 256), sms * 8), 256, 0, s>>>(ws.cdf, L, Gl,
+                                                                                                     ws.guide);
+  INPC_TRY(check_launch("k_guide"));
   const int sl = coarse_stride_log2(L);
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   if (n_samples > 0) {
     const unsigned grid = (unsigned)ceil_div(n_samples, kDrawPerCta);
     if (L <= kSmemLeaves)
       INPC_TIMED("k_draw_count", s,
-                 k_draw_count<true><<<grid, kDrawThreads, 0, s>>>(ws.cdf, L, sl, n_samples, k0, k1, view_id, ws.counts));
+                 k_draw_count<true><<<grid, kDrawThreads, 0, s>>>(ws.cdf, L, ws.guide, Gl, n_samples, k0, k1, view_id,
+                                                                  ws.counts));
     else
       INPC_TIMED("k_draw_count", s,
-                 k_draw_count<false><<<grid, kDrawThreads, 0, s>>>(ws.cdf, L, sl, n_samples, k0, k1, view_id,
-                                                                   ws.counts));
+                 k_draw_count<false><<<grid, kDrawThreads, 0, s>>>(ws.cdf, L, ws.guide, Gl, n_samples, k0, k1,
+                                                                   view_id, ws.counts));
     INPC_TRY(check_launch("k_draw_count"));
   }
   INPC_TRY((scan<uint32_t, CountLoad, false>(CountLoad{ws.counts}, L, ws.starts, ws.count_tops, s)));
@@ -615,7 +661,8 @@ extern "C" inpc_status inpc_sample_octree_view(const inpc_octree* tree, const in
   if (n_samples > 0)
     for (int32_t r = 0; r < max_rounds; ++r) {
       INPC_TIMED("k_resample_round", s,
-                 k_resample_round<<<(unsigned)grid, 256, 0, s>>>(ws.cdf, tree->n_leaves, c, n_samples, k0, k1, view_id,
+                 k_resample_round<<<(unsigned)grid, 256, 0, s>>>(ws.cdf, tree->n_leaves, ws.guide,
+                                                                guide_log2(tree->n_leaves), c, n_samples, k0, k1, view_id,
                                                                 (uint32_t)r, tree->centers, tree->levels,
                                                                 tree->root_size, leaf_idx_out, pos_out));
       INPC_TRY(check_launch("k_resample_round"));
