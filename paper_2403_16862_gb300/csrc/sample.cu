@@ -1,5 +1,5 @@
 // sample.cu -- octree point sampling (Sec. 3.2): exact quantised FP64 CDF,
-// Philox4x32-10 draws with a two-level CDF search, per-leaf counts, and
+// Philox4x32-10 draws with a guide-table CDF search, per-leaf counts, and
 // leaf-grouped output slots with uniform in-leaf positions.
 //
 // Kernel sequence per call (one stream, no host synchronisation):
@@ -7,7 +7,8 @@
 //   k_scan_local  per-block inclusive scan of q_i = rint(w_i / wmax * 2^29)
 //   k_scan_tops   exclusive scan of the block totals (one CTA)
 //   k_scan_add    add block offsets -> cdf (exact integers in FP64)
-//   k_draw_count  draws -> leaf, per-CTA shared-memory histogram -> counts
+//   k_guide       first leaf of every bucket of draw values
+//   k_draw_count  draws -> leaf (search between two guide entries) -> counts
 //   k_scan_*      exclusive scan of counts -> first output slot of each leaf
 //   k_place       slot -> leaf (two-level search), Philox position
 #include <algorithm>
