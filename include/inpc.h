@@ -458,6 +458,63 @@ inpc_status inpc_octree_prune(const inpc_octree* tree, const double* q, double t
                               int32_t* levels_out, double* p_out, double* q_out, int64_t out_capacity,
                               int64_t* n_out, void* workspace, size_t workspace_bytes, inpc_stream_t stream);
 
+/* ======================================================================== */
+/* (f) Batches of views                                                     */
+/* ======================================================================== */
+/* One view of a batch (all pointers are device memory owned by the caller;
+ * nothing in a job is read after inpc_render_batch's work completes).
+ *   cam, opts   the view's camera and rasterizer options (head mode,
+ *               n_channels = 4 * grid levels; tile sizes may differ per view)
+ *   view_id     the view's Philox stream of the batch's seed (Sec. 3.2)
+ *   n_samples   points drawn for this view
+ *   leaf_idx, pos, h   [n] int32, [n, 3] float32, [n, n_channels] of
+ *               opts.feat_dtype (= the grid's out_dtype): sampled points and
+ *               their features
+ *   image, T_final, n_contrib   the forward's outputs, as for
+ *               inpc_rasterize_fwd
+ *   d_image     float32 [H, W, n_channels] upstream image gradient, or NULL
+ *               for a forward-only view
+ *   sample_ws   inpc_sample_workspace_size(n_leaves, n_samples) bytes
+ *   raster_ws   inpc_rasterize_bwd_hashgrid_workspace_size(...) bytes */
+typedef struct {
+  inpc_camera cam;
+  inpc_raster_opts opts;
+  uint32_t view_id;
+  int64_t n_samples;
+  int32_t* leaf_idx;
+  float* pos;
+  void* h;
+  void* image;
+  float* T_final;
+  int32_t* n_contrib;
+  const float* d_image;
+  void* sample_ws;
+  size_t sample_ws_bytes;
+  void* raster_ws;
+  size_t raster_ws_bytes;
+} inpc_view_job;
+
+/* A batch of views of one scene (the paper renders one viewpoint per
+ * training iteration, Sec. 4.1; a batch of independent views is this
+ * library's throughput form and has no counterpart in the paper): every
+ * view samples the shared octree, queries the
+ * shared grid `table`, rasterizes, and, when its d_image is given, runs the
+ * fused backward, adding into the shared FP32 `grad_table` (atomic, so
+ * views may run concurrently; the caller zeroes it).  Each view is exactly
+ * the sequence inpc_sample_octree -> inpc_query_hashgrid ->
+ * inpc_rasterize_fwd -> inpc_rasterize_bwd_hashgrid.
+ * Views are spread round-robin over `streams` (n_streams >= 1, distinct):
+ * the call forks them from streams[0] and joins them back into it, so all
+ * of the batch is ordered after earlier work on streams[0] and before later
+ * work there, and one stream capture on streams[0] records the whole batch
+ * as one CUDA graph (replayed as one launch per step).
+ * Errors: INPC_ERR_INVALID_ARG (null or bad arguments, repeated streams),
+ * or the first error of a view's call (the remaining views are not
+ * enqueued; the streams are still joined). */
+inpc_status inpc_render_batch(const inpc_octree* tree, uint64_t seed, const inpc_hashgrid_desc* grid,
+                              const void* table, const inpc_view_job* views, int32_t n_views, float* grad_table,
+                              const inpc_stream_t* streams, int32_t n_streams);
+
 #ifdef __cplusplus
 }
 #endif

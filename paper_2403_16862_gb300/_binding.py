@@ -45,6 +45,7 @@ DECLARED = [
     "inpc_view_weights", "inpc_sample_octree_view",
     "inpc_level_weights", "inpc_sample_octree_halton", "inpc_accumulate_image",
     "inpc_contract_positions", "inpc_sh_head_fwd", "inpc_sh_head_bwd",
+    "inpc_render_batch",
 ]
 
 
@@ -74,6 +75,14 @@ class InpcRasterOpts(C.Structure):
     _fields_ = [("opacity_mode", C.c_int32), ("n_channels", C.c_int32), ("feat_dtype", C.c_int32),
                 ("image_dtype", C.c_int32), ("t_min", C.c_float), ("alpha_max", C.c_float),
                 ("tile_w", C.c_int32), ("tile_h", C.c_int32)]
+
+
+class InpcViewJob(C.Structure):
+    _fields_ = [("cam", InpcCamera), ("opts", InpcRasterOpts), ("view_id", C.c_uint32), ("n_samples", C.c_int64),
+                ("leaf_idx", C.c_void_p), ("pos", C.c_void_p), ("h", C.c_void_p), ("image", C.c_void_p),
+                ("T_final", C.c_void_p), ("n_contrib", C.c_void_p), ("d_image", C.c_void_p),
+                ("sample_ws", C.c_void_p), ("sample_ws_bytes", C.c_size_t), ("raster_ws", C.c_void_p),
+                ("raster_ws_bytes", C.c_size_t)]
 
 
 _P = C.c_void_p
@@ -135,6 +144,8 @@ def load(path: str = LIB_PATH):
         L.inpc_sh_head_fwd.argtypes = [C.POINTER(InpcCamera), _P, _P, C.c_int32, C.c_int64, C.c_int32, _P, _P, _P]
         L.inpc_sh_head_bwd.argtypes = [C.POINTER(InpcCamera), _P, _P, C.c_int32, C.c_int64, C.c_int32, _P, _P, _P,
                                        _P]
+        L.inpc_render_batch.argtypes = [C.POINTER(InpcOctree), C.c_uint64, C.POINTER(InpcHashgridDesc), _P,
+                                        C.POINTER(InpcViewJob), C.c_int32, _P, C.POINTER(_P), C.c_int32]
         L.inpc_kernel_timer_enable.argtypes = [C.c_int]
         L.inpc_kernel_timer_read.argtypes = [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         for name in DECLARED:
@@ -325,3 +336,13 @@ def inpc_sh_head_fwd(cam: InpcCamera, pos: int, h: int, h_dtype: int, n: int, n_
 def inpc_sh_head_bwd(cam: InpcCamera, pos: int, h: int, h_dtype: int, n: int, n_channels: int, d_alpha: int,
                      d_color: int, dh_out: int, stream: int):
     check(load().inpc_sh_head_bwd(C.byref(cam), pos, h, h_dtype, n, n_channels, d_alpha, d_color, dh_out, stream))
+
+
+def inpc_render_batch(tree: InpcOctree, seed: int, desc: InpcHashgridDesc, table: int, jobs, grad_table,
+                      streams):
+    """jobs: a sequence of InpcViewJob (or a ctypes array of them); streams:
+    raw cudaStream_t handles, streams[0] the origin."""
+    arr = jobs if isinstance(jobs, C.Array) else (InpcViewJob * len(jobs))(*jobs)
+    st = (_P * len(streams))(*streams)
+    check(load().inpc_render_batch(C.byref(tree), seed, C.byref(desc), table, arr, len(arr), grad_table, st,
+                                   len(streams)))

@@ -51,6 +51,7 @@ class ViewBatch:
             d["ws_r"] = api.workspace(api.rasterize_bwd_hashgrid_workspace_size(d["cam"], d["opts"], desc, self.n),
                                       self.dev)
         self.graph = None
+        self._job_array = None
 
     def _tune(self):
         # one eager pass per view provides realistic inputs for the tile search
@@ -61,24 +62,31 @@ class ViewBatch:
             tw, th = tuned_tiles(d["cam"], d["opts"], self.desc, d["pos"], d["h"], d["d_image"])
             d["opts"].tile_w, d["opts"].tile_h = tw, th
 
+    def _jobs(self):
+        jobs = []
+        for d in self.views:
+            for k in ("d_image", "leaf", "pos", "h", "img", "T", "nc", "ws_s", "ws_r"):
+                assert d[k].is_contiguous()
+            jobs.append(B.InpcViewJob(
+                cam=api.camera(d["cam"]), opts=d["opts"].c(), view_id=d["view_id"], n_samples=self.n,
+                leaf_idx=d["leaf"].data_ptr(), pos=d["pos"].data_ptr(), h=d["h"].data_ptr(),
+                image=d["img"].data_ptr(), T_final=d["T"].data_ptr(), n_contrib=d["nc"].data_ptr(),
+                d_image=d["d_image"].data_ptr(), sample_ws=d["ws_s"].data_ptr(), sample_ws_bytes=d["ws_s"].numel(),
+                raster_ws=d["ws_r"].data_ptr(), raster_ws_bytes=d["ws_r"].numel()))
+        return (B.InpcViewJob * len(jobs))(*jobs)
+
     def _enqueue(self):
+        """All views through inpc_render_batch: the current stream is the
+        origin, the batch's own streams carry the other views."""
         c, l, w, rs = self.tree
         main = torch.cuda.current_stream()
         self.grad_table.zero_()
-        start = torch.cuda.Event()
-        start.record(main)
-        for v, d in enumerate(self.views):
-            s = self.streams[v % len(self.streams)]
-            s.wait_event(start)
-            with torch.cuda.stream(s):
-                api.sample_octree(c, l, w, rs, self.seed, d["view_id"], self.n, ws=d["ws_s"], out=(d["leaf"], d["pos"]))
-                api.query_hashgrid(self.desc, self.table, d["pos"], out=d["h"])
-                api.rasterize_fwd(d["cam"], d["opts"], d["pos"], d["h"], None, ws=d["ws_r"],
-                                  out=(d["img"], d["T"], d["nc"]))
-                api.rasterize_bwd_hashgrid(d["cam"], d["opts"], self.desc, d["pos"], d["h"], d["T"], d["nc"],
-                                           d["d_image"], d["ws_r"], self.grad_table)
-        for s in self.streams:
-            main.wait_stream(s)
+        if self._job_array is None:
+            self._job_array = self._jobs()
+        tree = B.InpcOctree(c.data_ptr(), l.data_ptr(), w.data_ptr(), rs, l.shape[0])
+        streams = [main.cuda_stream] + [s.cuda_stream for s in self.streams]
+        B.inpc_render_batch(tree, self.seed, self.desc, self.table.data_ptr(), self._job_array,
+                            self.grad_table.data_ptr(), streams)
 
     def run_eager(self):
         """One pass without the graph (also creates the library's side streams)."""

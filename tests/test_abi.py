@@ -92,3 +92,28 @@ def test_argument_errors_are_reported(B):
                              None, 0, None)
     assert e.value.status == B.INPC_ERR_INVALID_ARG
     assert "workspace" in str(e.value)
+
+
+def test_render_batch_argument_errors(B):
+    """inpc_render_batch validates its arguments before any stream work."""
+    from paper_2403_16862_gb300 import api
+    cam = scenes.make_camera((0, 0, -3), 10, 10, 5, 5, 10, 10)
+    desc = api.hashgrid_desc(scenes.geometric_resolutions(16, 16, 4096), 14)
+    tree = B.InpcOctree(1, 1, 1, 1.0, 8)  # never dereferenced: validation fails first
+    job = B.InpcViewJob(cam=api.camera(cam), opts=api.RasterOptions(n_channels=64, head_mode=True).c(), view_id=0,
+                        n_samples=10, d_image=1)
+    cases = [
+        (dict(table=0, jobs=[job], grad_table=1, streams=[1]), "null pointer"),
+        (dict(table=1, jobs=[job], grad_table=1, streams=[]), "n_streams"),
+        (dict(table=1, jobs=[job], grad_table=1, streams=[7, 7]), "repeats"),
+        (dict(table=1, jobs=[job], grad_table=None, streams=[1]), "grad_table is null"),
+    ]
+    for kw, msg in cases:
+        with pytest.raises(B.InpcError) as e:
+            B.inpc_render_batch(tree, 0, desc, kw["table"], kw["jobs"], kw["grad_table"], kw["streams"])
+        assert e.value.status == B.INPC_ERR_INVALID_ARG and msg in str(e.value), (msg, str(e.value))
+    given = B.InpcViewJob(cam=api.camera(cam), opts=api.RasterOptions(n_channels=64).c(), n_samples=10)
+    with pytest.raises(B.InpcError) as e:
+        B.inpc_render_batch(tree, 0, desc, 1, [given], 1, [1])
+    assert e.value.status == B.INPC_ERR_INVALID_ARG and "head mode" in str(e.value)
+    B.inpc_render_batch(tree, 0, desc, 1, [], 1, [1])  # an empty batch is a no-op
