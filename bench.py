@@ -81,10 +81,10 @@ KERNELS = ["k_draw_count", "k_place", "k_hash_fwd", "k_pix_count", "k_pix_scatte
 
 # DRAM bytes per launch of the dominant kernel on the full workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); see profiles/.
-TRAFFIC = {"k_point_grad_hash": 2.74e9 + 0.71932e9}
+TRAFFIC = {"k_point_grad_hash": 2_750_635_008 + 720_782_592}
 # L2 vector-reduction requests of one launch of the dominant kernel on the full
 # workload (lts__t_requests_op_red.sum, one ncu capture); see profiles/.
-L2_REDUCTIONS = {"k_point_grad_hash": 243_135_594}
+L2_REDUCTIONS = {"k_point_grad_hash": 243_178_151}
 
 
 def kernel_bytes(kernel, n, n_entries, n_frag, n_pix):
@@ -561,7 +561,7 @@ def run_forms(args, api, B, dev, world, rank):
     torch.cuda.empty_cache()
 
     # ---- inference: a pre-extracted cloud rendered from several views
-    n_pre = 1 << 25  # the rasterizer's point-index range
+    n_pre = 1 << 26
     lw = api.level_weights(l, w.clone(), 0.5)
     _, pos_pre = api.sample_octree_halton(c, l, lw, tree.root_size, 5, n_pre)
     h_pre = api.query_hashgrid(d16, t16, pos_pre)
@@ -571,7 +571,7 @@ def run_forms(args, api, B, dev, world, rank):
     bufs = api.rasterize_fwd(cams_r[0], opts_pre, pos_pre, h_pre, ws=ws_pre)[:3]
     ms_render = timed(lambda k: api.rasterize_fwd(cams_r[k % 4], opts_pre, pos_pre, h_pre, ws=ws_pre, out=bufs), steps)
     out["bf16_preextracted_render"] = {
-        "workload": "33,554,432 points pre-extracted once (level weights, Halton positions) from the 1,048,576-leaf "
+        "workload": "67,108,864 points pre-extracted once (level weights, Halton positions) from the 1,048,576-leaf "
                     "octree, BF16 features queried once, rendered (rasterizer forward only) at 1280x832 per view",
         "ms_per_view": ms_render, "views_per_s": 1e3 / ms_render}
     del h_pre, pos_pre, ws_pre, bufs

@@ -250,7 +250,13 @@ inpc_status inpc_rasterize_workspace_size(const inpc_camera* cam, const inpc_ras
  *   image    [H, W, F] of image_dtype;  T_final float32 [H, W];
  *   n_contrib int32 [H, W] (fragments blended per pixel)
  * The workspace must stay untouched until the matching inpc_rasterize_bwd.
- * n in [0, 2^25] (point indices are packed into 25 bits of the sort key). */
+ * n in [0, 2^28] (4n fragment slots are 32-bit).  The sort key holds the
+ * point index beside the depth: up to 2^25 points the depth's raw FP32 bits,
+ * beyond that its bits above those of near_plane, which must then span at
+ * fewer than 2^(56 - b) values up to far_plane for b-bit point indices
+ * (INPC_ERR_CAPACITY otherwise; near = 0.01, far = 100 allow 2^28 points).
+ * The calls that continue from this one (inpc_rasterize_bwd,
+ * inpc_rasterize_bwd_hashgrid, inpc_rasterize_point_weights) take n <= 2^25. */
 inpc_status inpc_rasterize_fwd(const inpc_camera* cam, const inpc_raster_opts* opts, const float* pos,
                                const float* opacity, const void* feat, int64_t n, void* image, float* T_final,
                                int32_t* n_contrib, void* workspace, size_t workspace_bytes, inpc_stream_t stream);

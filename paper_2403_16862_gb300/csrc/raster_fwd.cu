@@ -7,7 +7,7 @@ extern "C" inpc_status inpc_rasterize_workspace_size(const inpc_camera* cam, con
                                                      size_t* bytes) {
   if (!bytes) return fail(INPC_ERR_INVALID_ARG, "bytes is null");
   RP P;
-  INPC_TRY(make_rp(cam, opts, n, P));
+  INPC_TRY(make_rp(cam, opts, n, P, kMaxFwdPoints));
   *bytes = carve(nullptr, P.n_pix, n).bytes;
   return INPC_OK;
 }
@@ -17,7 +17,7 @@ extern "C" inpc_status inpc_rasterize_fwd(const inpc_camera* cam, const inpc_ras
                                           float* T_final, int32_t* n_contrib, void* workspace,
                                           size_t workspace_bytes, inpc_stream_t stream) {
   RP P;
-  INPC_TRY(make_rp(cam, opts, n, P));
+  INPC_TRY(make_rp(cam, opts, n, P, kMaxFwdPoints));
   const RasterWs need = carve(nullptr, P.n_pix, n);
   if (!workspace || workspace_bytes < need.bytes || !aligned(workspace, 256))
     return fail(INPC_ERR_INVALID_ARG, "workspace null, unaligned or smaller than %zu bytes", need.bytes);

@@ -5,7 +5,7 @@
 // the pixel is the most significant radix digit and is handled by a
 // counting sort into per-pixel buckets (k_pix_count, prefix sum,
 // k_pix_scatter); each bucket is then ordered by the remaining key
-// (FP32 depth bits << 25 | point index) in shared memory by the threads that
+// (depth field << idb | point index) in shared memory by the threads that
 // blend it: a group of GA lanes per pixel for buckets of at most CG
 // fragments, a whole CTA (bitonic network) for larger ones, and a stable LSD
 // radix sort in global memory beyond the shared-memory capacity.  Every path
@@ -32,6 +32,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstring>
 #include <mutex>
 
 #include "common.cuh"
@@ -42,8 +43,15 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+// Sort keys: (FP32 depth bits - dbase) << idb | point index.  Up to 2^25
+// points the depth field is the raw bits of the positive depth (31 bits) and
+// idb = 25; beyond that idb is the bit width of n - 1 and the depth field the
+// bits above those of the near plane (every kept depth lies strictly between
+// near and far, so the field is positive and monotone in depth).  Either way
+// a key fits in 56 bits: the register sorts append an 8-bit bucket position.
 constexpr int kIdBits = 25;
-constexpr unsigned long long kIdMask = (1ull << kIdBits) - 1;
+constexpr int kKeyBits = 56;
+constexpr int64_t kMaxFwdPoints = int64_t(1) << 28;  // 4n fragment slots stay below 2^32
 constexpr int kHeavyKeys = 2048;  // shared-memory bucket entries on the CTA path (larger buckets sort in global memory)
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 
@@ -56,6 +64,9 @@ struct RP {
   float t_min, alpha_max;
   long long n;
   long long n_pix;
+  int idb;                  // point-index bits of the sort key
+  uint32_t dbase;           // subtracted from the FP32 depth bits in the key
+  unsigned long long idm;   // (1 << idb) - 1
 };
 
 struct RasterWs {
@@ -152,7 +163,7 @@ __global__ void __launch_bounds__(256) k_pix_count(RP P, const float* __restrict
                                                    uint32_t* __restrict__ pix_count) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int n = (int)P.n;  // <= 2^25
+  const int n = (int)P.n;  // <= 2^28
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const int id = base + threadIdx.x;
     int q[4] = {-1, -1, -1, -1};
@@ -177,7 +188,7 @@ __global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restri
                                                      float* __restrict__ alpha, uint32_t* __restrict__ pslot) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int n = (int)P.n;  // <= 2^25
+  const int n = (int)P.n;  // <= 2^28
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const int id = base + threadIdx.x;
     int q[4] = {-1, -1, -1, -1};
@@ -187,7 +198,7 @@ __global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restri
       for (int k = 0; k < 4; ++k) q[k] = corner_pixel(P, s.f, k);
       ah = point_alpha_h(P, opacity, feat, id, nullptr);
     }
-    const unsigned long long key = ((unsigned long long)__float_as_uint(s.d) << kIdBits) | (unsigned long long)id;
+    const unsigned long long key = ((unsigned long long)(__float_as_uint(s.d) - P.dbase) << P.idb) | (unsigned long long)id;
     // the four corners' bucket offsets and atomics are all issued before
     // any result is used, so their round trips overlap
     unsigned peers[4];
@@ -631,7 +642,7 @@ __device__ __forceinline__ void load_sorted(const Group<GA>& G, const unsigned l
   reg_sort<GA, R>(G, key, m);
 }
 
-__device__ __forceinline__ long long reg_id(unsigned long long k) { return (long long)((k >> 8) & kIdMask); }
+__device__ __forceinline__ long long reg_id(const RP& P, unsigned long long k) { return (long long)((k >> 8) & P.idm); }
 __device__ __forceinline__ uint32_t reg_pos(unsigned long long k) { return (uint32_t)(k & 0xFF); }
 
 // ------------------------------------------- 64 channels: fragment slots ---
@@ -749,7 +760,7 @@ __device__ void blend_fwd_slots(const Group<32>& G, const RP& P, const RasterWs&
     float a = 0.f;
     if constexpr (R <= 2) a = valid ? a_sorted[r] : 0.f;
     else a = valid ? ws.alpha[s0 + reg_pos(key[r])] : 0.f;
-    const uint32_t id = valid ? (uint32_t)reg_id(key[r]) : 0u;
+    const uint32_t id = valid ? (uint32_t)reg_id(P, key[r]) : 0u;
     const ChunkT<32> ct = chunk_transmittance<32>(G, P, a, valid, min(32, m - b), T);
     const float wk = __fmul_rn(ct.Tk, a);
     if (G.lg < ct.take) ws.order[s0 + b + G.lg] = make_uint2(reg_pos(key[r]), id);
@@ -888,7 +899,7 @@ __device__ void blend_fwd_reg(const Group<GA>& G, const RP& P, const RasterWs& w
     if (b >= m) break;
     const bool valid = b + G.lg < m;
     const float a = valid ? ws.alpha[s0 + reg_pos(key[r])] : 0.f;
-    const long long id = valid ? reg_id(key[r]) : 0;
+    const long long id = valid ? reg_id(P, key[r]) : 0;
     const ChunkT<GA> ct = chunk_transmittance<GA>(G, P, a, valid, min(GA, m - b), T);
     const float wk = __fmul_rn(ct.Tk, a);
     if (G.lg < ct.take) ws.order[s0 + b + G.lg] = make_uint2(reg_pos(key[r]), (uint32_t)id);
@@ -1192,7 +1203,7 @@ __device__ void blend_fwd_cta_slots(const RP& P, KeyAt key_at, AlphaAt alpha_at,
   for (int k = 8 * wid + f; k < n; k += 64) {
     const float wk = __fmul_rn(t_load(k), alpha_at(k));
     float c[16];
-    Slot64<FT>::load(feat + 64ll * (long long)(key_at(k) & kIdMask), q, c);
+    Slot64<FT>::load(feat + 64ll * (long long)(key_at(k) & P.idm), q, c);
     if (P.head && q == 0) c[0] = 1.0f;
 #pragma unroll
     for (int e = 0; e < 16; ++e) acc[e] = __fmaf_rn(wk, c[e], acc[e]);
@@ -1254,7 +1265,7 @@ __device__ void blend_fwd_cta(const RP& P, KeyAt key_at, AlphaAt alpha_at, TLoad
     for (int k = group; k < n; k += kGroups) {
       const float w = __fmul_rn(t_load(k), alpha_at(k));
       float c[V];
-      load_color<V, FT>(P, feat, (long long)(key_at(k) & kIdMask), ch, c);
+      load_color<V, FT>(P, feat, (long long)(key_at(k) & P.idm), ch, c);
 #pragma unroll
       for (int v = 0; v < V; ++v) C[v] = __fmaf_rn(w, c[v], C[v]);
     }
@@ -1297,7 +1308,7 @@ __device__ void blend_bwd_cta(const RP& P, KeyAt key_at, AlphaAt alpha_at, SlotA
     float part = 0.f;
     if (ch < P.F) {
       float c[V];
-      load_color<V, FT>(P, feat, (long long)(key_at(k) & kIdMask), ch, c);
+      load_color<V, FT>(P, feat, (long long)(key_at(k) & P.idm), ch, c);
 #pragma unroll
       for (int v = 0; v < V; ++v) part = __fmaf_rn(c[v], g[v], part);
     }
@@ -1361,7 +1372,7 @@ struct SelSmem {
   int bstar, count, fill;
 };
 
-__device__ int cta_select_front(const RasterWs& ws, uint32_t s0, int m, const HeavyBuf& B, SortSmem& S,
+__device__ int cta_select_front(const RP& P, const RasterWs& ws, uint32_t s0, int m, const HeavyBuf& B, SortSmem& S,
                                 SelSmem& X) {
   const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -1378,7 +1389,7 @@ __device__ int cta_select_front(const RasterWs& ws, uint32_t s0, int m, const He
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int i = i0 + u * kThreads;
-      d[u] = i < m ? (uint32_t)(__ldg(ws.keys + s0 + i) >> kIdBits) : 0u;
+      d[u] = i < m ? (uint32_t)(__ldg(ws.keys + s0 + i) >> P.idb) : 0u;
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u)
@@ -1404,7 +1415,7 @@ __device__ int cta_select_front(const RasterWs& ws, uint32_t s0, int m, const He
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int i = i0 + u * kThreads;
-      d[u] = i < m ? (uint32_t)(__ldg(ws.keys + s0 + i) >> kIdBits) : 0u;
+      d[u] = i < m ? (uint32_t)(__ldg(ws.keys + s0 + i) >> P.idb) : 0u;
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u)
@@ -1431,7 +1442,7 @@ __device__ int cta_select_front(const RasterWs& ws, uint32_t s0, int m, const He
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int i = i0 + u * kThreads;
-      if (i < m && (((uint32_t)(key[u] >> kIdBits) - dmin) >> shift) <= bstar) {
+      if (i < m && (((uint32_t)(key[u] >> P.idb) - dmin) >> shift) <= bstar) {
         const int slot = atomicAdd(&X.fill, 1);
         B.K[slot] = key[u];
         B.A[slot] = ws.alpha[s0 + i];
@@ -1478,14 +1489,14 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const FT* __
     const int m = (int)(ws.pix_start[q + 1] - s0);
     float T;
     if (m > 2 * kSelectWant) {
-      const int C = cta_select_front(ws, s0, m, B, S, X);
+      const int C = cta_select_front(P, ws, s0, m, B, S, X);
       if (C > 0) {
         auto key_at = [&](int k) { return B.K[B.idx[k]]; };
         auto alpha_at = [&](int k) { return B.A[B.idx[k]]; };
         const int n = cta_transmittance(P, alpha_at, C, [&](int k, float v) { B.Tk[k] = v; }, H, &T);
         if (T < P.t_min || C == m) {  // the candidates reach the stop: the prefix is all that blends
           for (int k = threadIdx.x; k < n; k += kThreads)
-            ws.order[s0 + k] = make_uint2(B.pos[B.idx[k]], (uint32_t)(B.K[B.idx[k]] & kIdMask));
+            ws.order[s0 + k] = make_uint2(B.pos[B.idx[k]], (uint32_t)(B.K[B.idx[k]] & P.idm));
           __syncthreads();
           blend_fwd_cta<V, GA, FT>(P, key_at, alpha_at, [&](int k) { return B.Tk[k]; }, n, T, q, feat, image,
                                T_final, n_contrib, H);
@@ -1501,7 +1512,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const FT* __
       auto alpha_at = [&](int k) { return B.A[B.idx[k]]; };
       const int n = cta_transmittance(P, alpha_at, m, [&](int k, float v) { B.Tk[k] = v; }, H, &T);
       for (int k = threadIdx.x; k < n; k += kThreads)
-        ws.order[s0 + k] = make_uint2(B.pos[B.idx[k]], (uint32_t)(B.K[B.idx[k]] & kIdMask));
+        ws.order[s0 + k] = make_uint2(B.pos[B.idx[k]], (uint32_t)(B.K[B.idx[k]] & P.idm));
       __syncthreads();
       blend_fwd_cta<V, GA, FT>(P, key_at, alpha_at, [&](int k) { return B.Tk[k]; }, n, T, q, feat, image, T_final,
                            n_contrib, H);
@@ -1512,7 +1523,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const FT* __
       auto key_at = [&](int k) { return ka[k]; };
       auto alpha_at = [&](int k) { return ws.alpha[s0 + va[k]]; };
       const int n = cta_transmittance(P, alpha_at, m, [&](int k, float v) { tmp[k].x = v; }, H, &T);
-      for (int k = threadIdx.x; k < n; k += kThreads) ws.order[s0 + k] = make_uint2(va[k], (uint32_t)(ka[k] & kIdMask));
+      for (int k = threadIdx.x; k < n; k += kThreads) ws.order[s0 + k] = make_uint2(va[k], (uint32_t)(ka[k] & P.idm));
       __syncthreads();
       blend_fwd_cta<V, GA, FT>(P, key_at, alpha_at, [&](int k) { return tmp[k].x; }, n, T, q, feat, image, T_final,
                            n_contrib, H);
@@ -1629,13 +1640,31 @@ __global__ void __launch_bounds__(kThreads) k_point_grad(RP P, const float* __re
 }
 
 // ---------------------------------------------------------------- host ---
-inpc_status make_rp(const inpc_camera* cam, const inpc_raster_opts* o, int64_t n, RP& P) {
+// max_n: 2^28 for the forward alone (and its workspace), 2^25 for the calls
+// that continue from it (backward, per-point blending weights).
+inpc_status make_rp(const inpc_camera* cam, const inpc_raster_opts* o, int64_t n, RP& P,
+                    int64_t max_n = int64_t(1) << kIdBits) {
   if (!cam || !o) return fail(INPC_ERR_INVALID_ARG, "camera or options is null");
   if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
     return fail(INPC_ERR_INVALID_ARG, "image size %dx%d out of range", cam->width, cam->height);
   if (!(cam->near_plane > 0.0f) || !(cam->far_plane > cam->near_plane))
     return fail(INPC_ERR_INVALID_ARG, "need 0 < near < far");
-  if (n < 0 || n > (int64_t(1) << kIdBits)) return fail(INPC_ERR_CAPACITY, "n must be in [0, 2^25]");
+  if (n < 0 || n > max_n) return fail(INPC_ERR_CAPACITY, "n must be in [0, 2^%d]", max_n > (int64_t(1) << kIdBits) ? 28 : 25);
+  if (n <= (int64_t(1) << kIdBits)) {
+    P.idb = kIdBits;
+    P.dbase = 0u;
+  } else {
+    P.idb = 64 - __builtin_clzll((unsigned long long)(n - 1));
+    uint32_t nb, fb;
+    std::memcpy(&nb, &cam->near_plane, 4);
+    std::memcpy(&fb, &cam->far_plane, 4);
+    P.dbase = nb;
+    // kept depths lie strictly inside (near, far): their field is below fb - nb
+    if ((unsigned long long)(fb - nb) >= (1ull << (kKeyBits - P.idb)))
+      return fail(INPC_ERR_CAPACITY, "far/near = %g/%g leaves too few depth bits beside %d-bit point indices",
+                  (double)cam->far_plane, (double)cam->near_plane, P.idb);
+  }
+  P.idm = (1ull << P.idb) - 1;
   if (o->opacity_mode != INPC_OPACITY_GIVEN && o->opacity_mode != INPC_OPACITY_FROM_CH0)
     return fail(INPC_ERR_INVALID_ARG, "bad opacity_mode");
   if ((o->feat_dtype != INPC_F32 && o->feat_dtype != INPC_BF16) || o->image_dtype != o->feat_dtype)

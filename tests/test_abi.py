@@ -84,8 +84,22 @@ def test_argument_errors_are_reported(B):
     with pytest.raises(B.InpcError) as e:
         B.inpc_rasterize_workspace_size(cc, api.RasterOptions(n_channels=4, tile_w=32, tile_h=16).c(), 10)
     assert e.value.status == B.INPC_ERR_INVALID_ARG
+    # the forward takes up to 2^28 points; beyond 2^25 the near plane's bits
+    # are the depth field's base and the far plane must stay within 2^(56 - 26)
+    # of them for 26-bit point indices
+    o4 = api.RasterOptions(n_channels=4).c()
+    assert B.inpc_rasterize_workspace_size(cc, o4, 1 << 28) > B.inpc_rasterize_workspace_size(cc, o4, 1 << 25)
     with pytest.raises(B.InpcError) as e:
-        B.inpc_rasterize_workspace_size(cc, api.RasterOptions(n_channels=4).c(), (1 << 25) + 1)
+        B.inpc_rasterize_workspace_size(cc, o4, (1 << 28) + 1)
+    assert e.value.status == B.INPC_ERR_CAPACITY
+    wide = api.camera(scenes.make_camera((0, 0, -3), 10, 10, 5, 5, 10, 10, near=1e-6, far=1e6))
+    assert B.inpc_rasterize_workspace_size(wide, o4, 1 << 25) > 0
+    with pytest.raises(B.InpcError) as e:
+        B.inpc_rasterize_workspace_size(wide, o4, 1 << 28)
+    assert e.value.status == B.INPC_ERR_CAPACITY
+    # the calls that continue from the forward keep 25-bit point indices
+    with pytest.raises(B.InpcError) as e:
+        B.inpc_rasterize_bwd(cc, o4, None, None, None, (1 << 25) + 1, None, None, None, None, None, None, 0, None)
     assert e.value.status == B.INPC_ERR_CAPACITY
     with pytest.raises(B.InpcError) as e:
         B.inpc_rasterize_fwd(cc, api.RasterOptions(n_channels=4).c(), None, None, None, 10, None, None, None,

@@ -171,3 +171,39 @@ def test_autograd_wrapper(gpu):
     d_op, d_feat = api.rasterize_bwd(cam, opts, P, Fe.detach(), O.detach(), T2, n2, g, ws)
     assert torch.equal(img, img2)
     assert torch.allclose(Fe.grad, d_feat, atol=1e-6) and torch.allclose(O.grad, d_op, atol=1e-6)
+
+
+@pytest.mark.parametrize("near_far", [(0.01, 100.0), (1.9, 4.1)])
+def test_more_than_2_25_points(gpu, oracle, near_far):
+    """n = 2^25 + 8192 points: the forward's sort key carries 26-bit point
+    indices and stores the depth as its FP32 bits above those of the near
+    plane.  All but 16,384 points sit behind the camera (culled); the visible
+    ones are 8,192 indices spread over [0, 2^25) and the 8,192 from 2^25 on,
+    of which 2,048 duplicate a low-index point exactly (same depth and pixel:
+    ties broken by the point index across the 2^25 boundary).  Culled points
+    contribute nothing, so the oracle renders the visible points alone, in
+    their original order, which keeps the (depth, index) order."""
+    n_vis = 8192
+    n = (1 << 25) + n_vis
+    rng = np.random.default_rng(11)
+    pts, cam = scenes.raster_points_scene(seed=11, n=2 * n_vis, n_feat=4, size=64, focal=64.0)
+    cam.near, cam.far = near_far
+    low = np.sort(rng.choice(1 << 25, size=n_vis, replace=False))
+    vis = np.concatenate([low, (1 << 25) + np.arange(n_vis)])
+    pos = np.empty((n, 3), np.float32)
+    pos[:] = (0.0, 0.0, -10.0)  # behind the camera at z = -3
+    pos[vis] = pts.pos
+    pos[vis[n_vis:n_vis + 2048]] = pos[low[:2048]]
+    feat = np.zeros((n, 4), np.float32)
+    feat[vis] = pts.feat
+    opacity = np.full(n, 0.5, np.float32)
+    opacity[vis] = pts.opacity
+    got = _run(gpu, cam, pos, feat, opacity, head=False)
+    ref = oracle.raster_fwd(cam, pos[vis], feat[vis], opacity=opacity[vis], head_mode=False, with_abs=True)
+    ok = ref["flags"] == 0
+    assert int((~ok).sum()) <= 2
+    assert np.array_equal(got["n_contrib"][ok], ref["n_contrib"][ok]), "blended counts"
+    assert_cond_close(got["image"], ref["image"], ref["abs"], mask=ok[..., None], what="image")
+    assert_cond_close(got["T_final"], ref["T_final"], ref["T_final"], mask=ok, what="T_final")
+    assert ref["n_contrib"].max() > 1
+
