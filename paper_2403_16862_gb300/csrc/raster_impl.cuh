@@ -631,13 +631,122 @@ __device__ __forceinline__ void reg_sort(const Group<GA>& G, unsigned long long 
   }
 }
 
+// The same network on 32-bit keys: one shuffle and a min/max per element
+// and stage instead of two shuffles and a 64-bit compare and select.
 template <int GA, int R>
-__device__ __forceinline__ void load_sorted(const Group<GA>& G, const unsigned long long* __restrict__ keys,
+__device__ __forceinline__ void reg_sort32(const Group<GA>& G, uint32_t (&key)[R], int m) {
+  constexpr int P2 = GA * R;
+#pragma unroll
+  for (int k = 2; k <= P2; k <<= 1) {
+    if ((k >> 1) >= m) break;
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= GA) {
+        const int jr = j / GA;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int r2 = r ^ jr;
+          if (r2 > r) {
+            const bool up = (((r * GA + G.lg) & k) == 0);
+            const uint32_t lo = min(key[r], key[r2]), hi = max(key[r], key[r2]);
+            key[r] = up ? lo : hi;
+            key[r2] = up ? hi : lo;
+          }
+        }
+      } else {
+        const bool lower = (G.lg & j) == 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const bool up = (((r * GA + G.lg) & k) == 0);
+          const uint32_t o = __shfl_xor_sync(G.mask, key[r], j, GA);
+          key[r] = (lower == up) ? min(key[r], o) : max(key[r], o);
+        }
+      }
+    }
+  }
+}
+
+template <int GA>
+__device__ __forceinline__ uint32_t group_umin(const Group<GA>& G, uint32_t v) {
+  if constexpr (GA == 32) return __reduce_min_sync(0xffffffffu, v);
+#pragma unroll
+  for (int o = GA / 2; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(G.mask, v, o, GA));
+  return v;
+}
+
+template <int GA>
+__device__ __forceinline__ uint32_t group_umax(const Group<GA>& G, uint32_t v) {
+  if constexpr (GA == 32) return __reduce_max_sync(0xffffffffu, v);
+#pragma unroll
+  for (int o = GA / 2; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(G.mask, v, o, GA));
+  return v;
+}
+
+// Loads a bucket of m <= GA * R fragments and sorts it by (depth, point),
+// each element returned as key << 8 | bucket position.  Within one pixel
+// the depths usually span far fewer than 2^24 FP32 values, so the sort runs
+// on 32-bit keys (depth field - the bucket's minimum) << 8 | position,
+// which order the bucket exactly as the full keys do unless two fragments
+// have the same depth (then the point index decides).  Such ties show up as
+// equal neighbours after the sort; a bucket with one, or with a wider depth
+// span, is sorted again on the full 64-bit keys.  The full key of each
+// sorted element is then fetched by its position: from the lane that loaded
+// it (R <= 2) or from the bucket again (an L1 hit).
+template <int GA, int R>
+__device__ __forceinline__ void load_sorted(const Group<GA>& G, const RP& P, const unsigned long long* __restrict__ keys,
                                             uint32_t s0, int m, unsigned long long (&key)[R]) {
+  unsigned long long raw[R];
+  uint32_t k[R];
+  uint32_t lo = 0xFFFFFFFFu, hi = 0u;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int e = r * GA + G.lg;
-    key[r] = e < m ? (keys[s0 + e] << 8) | (unsigned long long)e : ~0ull;
+    raw[r] = e < m ? keys[s0 + e] : 0ull;
+    k[r] = (uint32_t)(raw[r] >> P.idb);
+    if (e < m) {
+      lo = min(lo, k[r]);
+      hi = max(hi, k[r]);
+    }
+  }
+  lo = group_umin<GA>(G, lo);
+  hi = group_umax<GA>(G, hi);
+  // valid keys stay below the 0xFFFFFFFF of the empty places
+  if (hi - lo < 0xFFFFFFu) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int e = r * GA + G.lg;
+      k[r] = e < m ? ((k[r] - lo) << 8) | (uint32_t)e : 0xFFFFFFFFu;
+    }
+    reg_sort32<GA, R>(G, k, m);
+    bool tie = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      uint32_t nx = __shfl_down_sync(G.mask, k[r], 1, GA);
+      const uint32_t n0 = r + 1 < R ? __shfl_sync(G.mask, k[r + 1 < R ? r + 1 : r], 0, GA) : 0xFFFFFFFFu;
+      if (G.lg == GA - 1) nx = n0;
+      if (r * GA + G.lg + 1 < m && (nx >> 8) == (k[r] >> 8)) tie = true;
+    }
+    if (G.ballot(tie) == 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const uint32_t e = k[r] & 0xFFu;
+        unsigned long long full;
+        if constexpr (R <= 2) {
+          const unsigned long long v0 = __shfl_sync(G.mask, raw[0], (int)(e % GA), GA);
+          const unsigned long long v1 = __shfl_sync(G.mask, raw[R - 1], (int)(e % GA), GA);
+          full = (R == 2 && e >= (uint32_t)GA) ? v1 : v0;
+        } else {
+          full = k[r] != 0xFFFFFFFFu ? keys[s0 + e] : 0ull;
+        }
+        key[r] = k[r] != 0xFFFFFFFFu ? (full << 8) | e : ~0ull;
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int e = r * GA + G.lg;
+    key[r] = e < m ? (raw[r] << 8) | (unsigned long long)e : ~0ull;
   }
   reg_sort<GA, R>(G, key, m);
 }
@@ -735,7 +844,7 @@ __device__ void blend_fwd_slots(const Group<32>& G, const RP& P, const RasterWs&
       a_in[r] = e < m ? ws.alpha[s0 + e] : 0.f;
     }
   }
-  load_sorted<32, R>(G, ws.keys, s0, m, key);
+  load_sorted<32, R>(G, P, ws.keys, s0, m, key);
   float a_sorted[R];
   if constexpr (R <= 2) {
 #pragma unroll
@@ -886,7 +995,7 @@ __device__ void blend_fwd_reg(const Group<GA>& G, const RP& P, const RasterWs& w
     return;
   }
   unsigned long long key[R];
-  load_sorted<GA, R>(G, ws.keys, s0, m, key);
+  load_sorted<GA, R>(G, P, ws.keys, s0, m, key);
   const int ch = G.lg * V;
   float C[V];
 #pragma unroll

@@ -207,3 +207,30 @@ def test_more_than_2_25_points(gpu, oracle, near_far):
     assert_cond_close(got["T_final"], ref["T_final"], ref["T_final"], mask=ok, what="T_final")
     assert ref["n_contrib"].max() > 1
 
+
+
+@pytest.mark.parametrize("F", [8, 64])
+def test_wide_depth_spans_and_exact_ties(gpu, oracle, F):
+    """The register sorts order a bucket on 32-bit keys (depth relative to
+    the bucket's nearest fragment) when the depths span fewer than 2^24 FP32
+    values and no two are equal, and on the full keys otherwise.  Left half
+    of the image: depths log-uniform in [0.05, 50] (spans of ~2^26 values);
+    right half: depths in [2, 3], 3,000 exact duplicates (equal depth and
+    pixel, ordered by point index) and a dense cluster for the CTA path."""
+    rng = np.random.default_rng(21)
+    W = H = 32
+    cam = scenes.make_camera((0.0, 0.0, 0.0), 32.0, 32.0, 16.0, 16.0, W, H)
+    n = 24000
+    u = rng.uniform(0.0, W, n)
+    v = rng.uniform(0.0, H, n)
+    d = np.where(u < W / 2, np.exp(rng.uniform(np.log(0.05), np.log(50.0), n)), rng.uniform(2.0, 3.0, n))
+    pos = np.stack([(u - 16.0) / 32.0 * d, (v - 16.0) / 32.0 * d, d], 1)
+    cl = np.stack([np.full(1500, 0.1), np.full(1500, -0.05), rng.uniform(2.0, 2.5, 1500)], 1)
+    pos = np.concatenate([pos, cl]).astype(np.float32)
+    dup = rng.choice(np.flatnonzero(pos[:, 0] > 0), 3000, replace=False)
+    pos = np.concatenate([pos, pos[dup]])
+    n = pos.shape[0]
+    opacity = rng.uniform(0.005, 0.05, n).astype(np.float32)
+    feat = rng.normal(size=(n, F)).astype(np.float32)
+    got, ref = _compare(gpu, oracle, cam, pos, feat, opacity, head=False, seed=F)
+    assert ref["n_frags"].max() > 256 and ref["n_contrib"].max() > 64
