@@ -73,6 +73,8 @@ struct RasterWs {
   uint32_t* status;
   uint32_t* heavy_count;     // header word 1
   uint32_t* large_count;     // header word 2
+  uint32_t* large_next;      // header word 3: the forward list kernel's next list entry
+  uint32_t* heavy_next;      // header word 4: the forward CTA kernel's next list entry
   uint32_t* pix_count;       // [n_pix]
   uint32_t* pix_start;       // [n_pix + 1]
   uint32_t* tops;            // prefix-sum block totals
@@ -96,6 +98,8 @@ RasterWs carve(void* base, long long n_pix, long long n) {
   w.status = reinterpret_cast<uint32_t*>(base);
   w.heavy_count = base ? reinterpret_cast<uint32_t*>(base) + 1 : nullptr;
   w.large_count = base ? reinterpret_cast<uint32_t*>(base) + 2 : nullptr;
+  w.large_next = base ? reinterpret_cast<uint32_t*>(base) + 3 : nullptr;
+  w.heavy_next = base ? reinterpret_cast<uint32_t*>(base) + 4 : nullptr;
   const long long nf = std::max<long long>(4 * n, 1);
   w.pix_count = c.take<uint32_t>(n_pix);
   w.pix_start = c.take<uint32_t>(n_pix + 1);
@@ -682,8 +686,8 @@ __device__ __forceinline__ uint32_t group_umax(const Group<GA>& G, uint32_t v) {
   return v;
 }
 
-// Loads a bucket of m <= GA * R fragments and sorts it by (depth, point),
-// each element returned as key << 8 | bucket position.  Within one pixel
+// Sorts m <= GA * R fragment keys, load(e) giving the key at position e,
+// by (depth, point), each element returned as key << 8 | position.  Within one pixel
 // the depths usually span far fewer than 2^24 FP32 values, so the sort runs
 // on 32-bit keys (depth field - the bucket's minimum) << 8 | position,
 // which order the bucket exactly as the full keys do unless two fragments
@@ -691,17 +695,17 @@ __device__ __forceinline__ uint32_t group_umax(const Group<GA>& G, uint32_t v) {
 // equal neighbours after the sort; a bucket with one, or with a wider depth
 // span, is sorted again on the full 64-bit keys.  The full key of each
 // sorted element is then fetched by its position: from the lane that loaded
-// it (R <= 2) or from the bucket again (an L1 hit).
-template <int GA, int R>
-__device__ __forceinline__ void load_sorted(const Group<GA>& G, const RP& P, const unsigned long long* __restrict__ keys,
-                                            uint32_t s0, int m, unsigned long long (&key)[R]) {
+// it (R <= 2) or through load again (an L1 or shared-memory hit).
+template <int GA, int R, class Load>
+__device__ __forceinline__ void sort_loaded(const Group<GA>& G, const RP& P, Load load, int m,
+                                            unsigned long long (&key)[R]) {
   unsigned long long raw[R];
   uint32_t k[R];
   uint32_t lo = 0xFFFFFFFFu, hi = 0u;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int e = r * GA + G.lg;
-    raw[r] = e < m ? keys[s0 + e] : 0ull;
+    raw[r] = e < m ? load(e) : 0ull;
     k[r] = (uint32_t)(raw[r] >> P.idb);
     if (e < m) {
       lo = min(lo, k[r]);
@@ -736,7 +740,7 @@ __device__ __forceinline__ void load_sorted(const Group<GA>& G, const RP& P, con
           const unsigned long long v1 = __shfl_sync(G.mask, raw[R - 1], (int)(e % GA), GA);
           full = (R == 2 && e >= (uint32_t)GA) ? v1 : v0;
         } else {
-          full = k[r] != 0xFFFFFFFFu ? keys[s0 + e] : 0ull;
+          full = k[r] != 0xFFFFFFFFu ? load((int)e) : 0ull;
         }
         key[r] = k[r] != 0xFFFFFFFFu ? (full << 8) | e : ~0ull;
       }
@@ -749,6 +753,13 @@ __device__ __forceinline__ void load_sorted(const Group<GA>& G, const RP& P, con
     key[r] = e < m ? (raw[r] << 8) | (unsigned long long)e : ~0ull;
   }
   reg_sort<GA, R>(G, key, m);
+}
+
+// A bucket of m <= GA * R fragments at keys[s0 ..], sorted as above.
+template <int GA, int R>
+__device__ __forceinline__ void load_sorted(const Group<GA>& G, const RP& P, const unsigned long long* __restrict__ keys,
+                                            uint32_t s0, int m, unsigned long long (&key)[R]) {
+  sort_loaded<GA, R>(G, P, [&](int e) { return keys[s0 + e]; }, m, key);
 }
 
 __device__ __forceinline__ long long reg_id(const RP& P, unsigned long long k) { return (long long)((k >> 8) & P.idm); }
@@ -1085,10 +1096,15 @@ template <int V, int GA, class FT>
 __global__ void __launch_bounds__(kThreads, 3) k_blend_fwd_large(RP P, const FT* __restrict__ feat, RasterWs ws,
                                                                FT* __restrict__ image, float* __restrict__ T_final,
                                                                int32_t* __restrict__ n_contrib) {
-  constexpr int kGroups = kThreads / GA;
   const Group<GA> G;
   const uint32_t n_large = *ws.large_count;
-  for (uint32_t h = blockIdx.x * kGroups + threadIdx.x / GA; h < n_large; h += gridDim.x * kGroups) {
+  // each group takes the next pixel of the list when it is done with one
+  // (bucket sizes differ by up to 4x, so a fixed stride leaves tails)
+  for (;;) {
+    uint32_t h = 0;
+    if (G.lg == 0) h = atomicAdd(ws.large_next, 1u);
+    h = G.bcast(h, 0);
+    if (h >= n_large) break;
     const long long q = ws.large[h];
     const uint32_t s0 = ws.pix_start[q];
     const int m = (int)(ws.pix_start[q + 1] - s0);
@@ -1469,7 +1485,9 @@ struct HeavyBuf {
 // bins of 2^shift, monotone in depth) gives the smallest bin b* whose
 // cumulative count reaches kSelectWant; every key in bins <= b* is nearer
 // than every key above, so those C candidates are an exact prefix of the
-// order.  They are sorted in shared memory.  Returns C, or 0 when the
+// order.  Up to 256 candidates are sorted by one warp in registers (no
+// barrier between the network's stages), more by the CTA in shared memory
+// (bitonic_sort_idx).  Returns C, or 0 when the
 // prefix does not fit (C > kHeavyKeys); the caller blends the candidates
 // and falls back to the full sort when they do not reach t_min.  (On the
 // benchmark scene 99 % of the pixels blend at most 66 fragments; targets of
@@ -1480,6 +1498,20 @@ struct SelSmem {
   uint32_t dmin, dmax;
   int bstar, count, fill;
 };
+
+// One warp sorts the C <= 32 R candidates B.K[0 .. C) and writes the
+// blending order to B.idx.
+template <int R>
+__device__ __forceinline__ void warp_sort_candidates(const RP& P, const HeavyBuf& B, int C) {
+  const Group<32> G;
+  unsigned long long key[R];
+  sort_loaded<32, R>(G, P, [&](int e) { return B.K[e]; }, C, key);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int k = r * 32 + G.lg;
+    if (k < C) B.idx[k] = (uint16_t)reg_pos(key[r]);
+  }
+}
 
 __device__ int cta_select_front(const RP& P, const RasterWs& ws, uint32_t s0, int m, const HeavyBuf& B, SortSmem& S,
                                 SelSmem& X) {
@@ -1561,7 +1593,15 @@ __device__ int cta_select_front(const RP& P, const RasterWs& ws, uint32_t s0, in
     }
   }
   __syncthreads();
-  bitonic_sort_idx(B.K, B.idx, C, threadIdx.x, kThreads, [] { __syncthreads(); });
+  if (C <= 256) {
+    if (threadIdx.x < 32) {
+      if (C <= 128) warp_sort_candidates<4>(P, B, C);
+      else warp_sort_candidates<8>(P, B, C);
+    }
+    __syncthreads();
+  } else {
+    bitonic_sort_idx(B.K, B.idx, C, threadIdx.x, kThreads, [] { __syncthreads(); });
+  }
   return C;
 }
 
@@ -1591,8 +1631,15 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const FT* __
   __shared__ HeavySmem H;
   __shared__ SelSmem X;
   const HeavyBuf B(dyn);
+  __shared__ uint32_t next;
   const uint32_t n_heavy = *ws.heavy_count;
-  for (uint32_t h = blockIdx.x; h < n_heavy; h += gridDim.x) {
+  // the CTA takes the next pixel of the list when it is done with one; every
+  // iteration ends with a barrier, so `next` is read before it is rewritten
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(ws.heavy_next, 1u);
+    __syncthreads();
+    const uint32_t h = next;
+    if (h >= n_heavy) break;
     const long long q = ws.heavy[h];
     const uint32_t s0 = ws.pix_start[q];
     const int m = (int)(ws.pix_start[q + 1] - s0);
