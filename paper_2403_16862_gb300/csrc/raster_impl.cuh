@@ -1045,49 +1045,106 @@ __device__ void blend_fwd_reg(const Group<GA>& G, const RP& P, const RasterWs& w
   }
 }
 
-// Bucket offsets of a group's pixels, GA at a time: lane j holds pixel
-// `first + j * stride` of the tile (or m = -1 outside the image).
-template <int GA>
-__device__ __forceinline__ void pixel_batch(const Group<GA>& G, const RP& P, const RasterWs& ws, int tx, int ty,
-                                            int p, uint32_t& s0, int& m, long long& q) {
-  m = -1;
-  s0 = 0;
-  q = 0;
-  if (p < P.TW * P.TH) {
-    const int px = tx * P.TW + p % P.TW, py = ty * P.TH + p / P.TW;
+// A tile's pixels in shared memory: bucket start, size (-1 outside the
+// image) and blended count of tile pixel i, loaded by thread i
+// (TW * TH <= kThreads), and the list of the pixels this kernel works on.
+// The CTA's groups take pixels from the list through a cursor, so a group
+// done with small buckets takes more and no warp waits on another's share.
+struct TileSmem {
+  uint32_t s0[kThreads];
+  int m[kThreads];
+  int nb[kThreads];
+  uint16_t list[kThreads];
+  int count, next;
+};
+
+// kBwd: the work pixels are those with 0 < blended count <= cap (else
+// 0 < bucket size <= cap).
+template <bool kBwd>
+__device__ __forceinline__ void load_tile(const RP& P, const RasterWs& ws, int tx, int ty,
+                                          const int32_t* __restrict__ n_contrib, int cap, TileSmem& S) {
+  const int i = threadIdx.x;
+  if (i == 0) {
+    S.count = 0;
+    S.next = 0;
+  }
+  __syncthreads();
+  if (i < P.TW * P.TH) {
+    int m = -1, nb = 0;
+    uint32_t s0 = 0;
+    const int px = tx * P.TW + i % P.TW, py = ty * P.TH + i / P.TW;
     if (px < P.cam.W && py < P.cam.H) {
-      q = (long long)py * P.cam.W + px;
+      const long long q = (long long)py * P.cam.W + px;
       s0 = ws.pix_start[q];
       m = (int)(ws.pix_start[q + 1] - s0);
+      if (kBwd && m > 0) nb = blended_count(n_contrib, q, m);
+    }
+    S.s0[i] = s0;
+    S.m[i] = m;
+    S.nb[i] = nb;
+    const int w = kBwd ? nb : m;
+    if (w > 0 && w <= cap) S.list[atomicAdd(&S.count, 1)] = (uint16_t)i;
+  }
+  __syncthreads();
+}
+
+// The next work pixel of the tile for this group, or -1.
+template <int GA>
+__device__ __forceinline__ int next_tile_pixel(const Group<GA>& G, TileSmem& S) {
+  int k = 0;
+  if (G.lg == 0) k = atomicAdd(&S.next, 1);
+  k = G.bcast(k, 0);
+  return k < S.count ? (int)S.list[k] : -1;
+}
+
+__device__ __forceinline__ long long tile_pixel_index(const RP& P, int tx, int ty, int j) {
+  return (long long)(ty * P.TH + j / P.TW) * P.cam.W + tx * P.TW + j % P.TW;
+}
+
+// The background (zero color, T = 1, no fragment) of the tile's empty
+// pixels, one warp per pixel.
+template <class FT>
+__device__ __forceinline__ void fill_empty(const RP& P, int tx, int ty, const TileSmem& S, FT* __restrict__ image,
+                                           float* __restrict__ T_final, int32_t* __restrict__ n_contrib) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int bytes = P.F * (int)sizeof(FT);
+  for (int j = warp; j < P.TW * P.TH; j += kWarps) {
+    if (S.m[j] != 0) continue;
+    const long long q = tile_pixel_index(P, tx, ty, j);
+    char* row = reinterpret_cast<char*>(image + q * P.F);
+    if (bytes % 8 == 0) {
+      for (int u = lane; u < bytes / 8; u += 32) reinterpret_cast<uint2*>(row)[u] = make_uint2(0u, 0u);
+    } else {
+      for (int u = lane; u < bytes / 4; u += 32) reinterpret_cast<uint32_t*>(row)[u] = 0u;
+    }
+    if (lane == 0) {
+      T_final[q] = 1.0f;
+      n_contrib[q] = 0;
     }
   }
 }
 
 // Tile-order kernel for small buckets (at most 2 registers per lane): high
-// occupancy, the offsets of GA pixels fetched with one load per lane.
+// occupancy; the groups take the tile's pixels from a shared cursor.
 template <int V, int GA, class FT>
 __global__ void __launch_bounds__(kThreads, 4) k_blend_fwd(RP P, const FT* __restrict__ feat, RasterWs ws,
                                                          FT* __restrict__ image, float* __restrict__ T_final,
                                                          int32_t* __restrict__ n_contrib) {
-  constexpr int kGroups = kThreads / GA;
+  __shared__ TileSmem S;
   const Group<GA> G;
-  const int group = threadIdx.x / GA;
   const int t = blockIdx.x;
   const int tx = t % P.tiles_x, ty = t / P.tiles_x;
-  const int npix = P.TW * P.TH;
-  for (int b = group; b < npix; b += kGroups * GA) {
-    uint32_t s0l;
-    int ml;
-    long long ql;
-    pixel_batch<GA>(G, P, ws, tx, ty, b + G.lg * kGroups, s0l, ml, ql);
-    for (int j = 0; j < GA && b + j * kGroups < npix; ++j) {
-      const int m = G.bcast(ml, j);
-      if (m < 0 || m > 2 * GA) continue;  // outside the image, or another class
-      const uint32_t s0 = G.bcast(s0l, j);
-      const long long q = G.bcast(ql, j);
-      if (m <= GA) blend_fwd_reg<V, GA, FT, 1>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
-      else blend_fwd_reg<V, GA, FT, 2>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
-    }
+  load_tile<false>(P, ws, tx, ty, nullptr, 2 * GA, S);
+  fill_empty<FT>(P, tx, ty, S, image, T_final, n_contrib);
+  // the next pixel is taken before the current one is blended
+  for (int j = next_tile_pixel(G, S); j >= 0;) {
+    const int jn = next_tile_pixel(G, S);
+    const int m = S.m[j];
+    const uint32_t s0 = S.s0[j];
+    const long long q = tile_pixel_index(P, tx, ty, j);
+    if (m <= GA) blend_fwd_reg<V, GA, FT, 1>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
+    else blend_fwd_reg<V, GA, FT, 2>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
+    j = jn;
   }
 }
 
@@ -1191,27 +1248,21 @@ template <int V, int GA, class FT>
 __global__ void __launch_bounds__(kThreads, 4) k_blend_bwd(RP P, const FT* __restrict__ feat,
                                                          const int32_t* __restrict__ n_contrib,
                                                          const float* __restrict__ d_image, RasterWs ws) {
-  constexpr int kGroups = kThreads / GA;
+  __shared__ TileSmem S;
   const Group<GA> G;
-  const int group = threadIdx.x / GA;
   const int t = blockIdx.x;
   const int tx = t % P.tiles_x, ty = t / P.tiles_x;
-  const int npix = P.TW * P.TH;
-  for (int b = group; b < npix; b += kGroups * GA) {
-    uint32_t s0l;
-    int ml;
-    long long ql;
-    pixel_batch<GA>(G, P, ws, tx, ty, b + G.lg * kGroups, s0l, ml, ql);
-    const int nbl = ml > 0 ? blended_count(n_contrib, ql, ml) : 0;
-    for (int j = 0; j < GA && b + j * kGroups < npix; ++j) {
-      const int nb = G.bcast(nbl, j);
-      if (nb <= 0 || nb > 2 * GA) continue;  // nothing blended, or another class
-      const int m = G.bcast(ml, j);
-      const uint32_t s0 = G.bcast(s0l, j);
-      const long long q = G.bcast(ql, j);
-      if (nb <= GA) blend_bwd_reg<V, GA, FT, 1>(G, P, ws, s0, m, nb, q, feat, d_image);
-      else blend_bwd_reg<V, GA, FT, 2>(G, P, ws, s0, m, nb, q, feat, d_image);
-    }
+  load_tile<true>(P, ws, tx, ty, n_contrib, 2 * GA, S);
+  // the next pixel is taken before the current one is revisited
+  for (int j = next_tile_pixel(G, S); j >= 0;) {
+    const int jn = next_tile_pixel(G, S);
+    const int nb = S.nb[j];
+    const int m = S.m[j];
+    const uint32_t s0 = S.s0[j];
+    const long long q = tile_pixel_index(P, tx, ty, j);
+    if (nb <= GA) blend_bwd_reg<V, GA, FT, 1>(G, P, ws, s0, m, nb, q, feat, d_image);
+    else blend_bwd_reg<V, GA, FT, 2>(G, P, ws, s0, m, nb, q, feat, d_image);
+    j = jn;
   }
 }
 
