@@ -81,10 +81,10 @@ KERNELS = ["k_draw_count", "k_place", "k_hash_fwd", "k_pix_count", "k_pix_scatte
 
 # DRAM bytes per launch of the dominant kernel on the full workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); see profiles/.
-TRAFFIC = {"k_point_grad_hash": 2_750_635_008 + 720_782_592}
+TRAFFIC = {"k_point_grad_hash": 2_748_142_592 + 720_322_560}
 # L2 vector-reduction requests of one launch of the dominant kernel on the full
 # workload (lts__t_requests_op_red.sum, one ncu capture); see profiles/.
-L2_REDUCTIONS = {"k_point_grad_hash": 243_178_151}
+L2_REDUCTIONS = {"k_point_grad_hash": 243_221_479}
 
 
 def kernel_bytes(kernel, n, n_entries, n_frag, n_pix):
