@@ -73,7 +73,7 @@ struct RasterWs {
   uint32_t* status;
   uint32_t* heavy_count;     // header word 1
   uint32_t* large_count;     // header word 2
-  uint32_t* large_next;      // header word 3: the forward list kernel's next list entry
+  uint32_t* large_next;      // header word 3: the list kernel's next list entry (forward, then backward)
   uint32_t* heavy_next;      // header word 4: the forward CTA kernel's next list entry
   uint32_t* pix_count;       // [n_pix]
   uint32_t* pix_start;       // [n_pix + 1]
@@ -1270,10 +1270,14 @@ template <int V, int GA, class FT>
 __global__ void __launch_bounds__(kThreads, 3) k_blend_bwd_large(RP P, const FT* __restrict__ feat,
                                                                const int32_t* __restrict__ n_contrib,
                                                                const float* __restrict__ d_image, RasterWs ws) {
-  constexpr int kGroups = kThreads / GA;
   const Group<GA> G;
   const uint32_t n_large = *ws.large_count;
-  for (uint32_t h = blockIdx.x * kGroups + threadIdx.x / GA; h < n_large; h += gridDim.x * kGroups) {
+  // as in the forward list kernel, each group takes the next pixel when done
+  for (;;) {
+    uint32_t h = 0;
+    if (G.lg == 0) h = atomicAdd(ws.large_next, 1u);
+    h = G.bcast(h, 0);
+    if (h >= n_large) break;
     const long long q = ws.large[h];
     const uint32_t s0 = ws.pix_start[q];
     const int m = (int)(ws.pix_start[q + 1] - s0);
@@ -2006,7 +2010,9 @@ inpc_status launch_blend_bwd(const RP& P, const FT* feat, const int32_t* n_contr
                              const RasterWs& ws, cudaStream_t s) {
   // fragments that were not blended keep zero scalars
   INPC_CUDA(cudaMemsetAsync(ws.fscal, 0, sizeof(float2) * std::max<long long>(4 * P.n, 1), s), "clear fscal");
-  INPC_CUDA(cudaMemsetAsync(ws.heavy_count, 0, 2 * sizeof(uint32_t), s), "clear class counts");
+  // the class counts and the list cursors (header words 1-4; the forward's
+  // kernels are done with them)
+  INPC_CUDA(cudaMemsetAsync(ws.heavy_count, 0, 4 * sizeof(uint32_t), s), "clear class counts");
   INPC_TIMED("k_classify_bwd", s,
              k_classify_bwd<<<(unsigned)ceil_div(P.n_pix, 256), 256, 0, s>>>(
                  n_contrib, ws.pix_start, P.n_pix, 2 * GA, GA * kRegMax, ws.heavy, ws.heavy_count, ws.large,
