@@ -5,11 +5,16 @@
 // the pixel is the most significant radix digit and is handled by a
 // counting sort into per-pixel buckets (k_pix_count, prefix sum,
 // k_pix_scatter); each bucket is then ordered by the remaining key
-// (depth field << idb | point index) in shared memory by the threads that
-// blend it: a group of GA lanes per pixel for buckets of at most CG
-// fragments, a whole CTA (bitonic network) for larger ones, and a stable LSD
-// radix sort in global memory beyond the shared-memory capacity.  Every path
-// yields the exact (depth, point) order.
+// (depth field << idb | point index) by the threads that blend it: in
+// registers by a group of GA lanes per pixel for buckets of at most
+// GA * kRegMax fragments (on 32-bit keys relative to the bucket's nearest
+// depth whenever those order it exactly); by a CTA for larger ones, which
+// first selects the nearest fragments by a depth histogram and has one warp
+// sort them in registers, and falls back to a shared-memory bitonic network
+// or, beyond the shared-memory capacity, a stable LSD radix sort in global
+// memory.  Every path yields the exact (depth, point) order.  Tiles of
+// small buckets, and the lists of larger ones, are worked through cursors so
+// that uneven bucket sizes leave no warp idle.
 //
 // Blending.  The scatter pass stores each fragment's alpha (Eq. 6 with the
 // clamp) beside its key, so blending gathers nothing but the feature rows of
