@@ -168,6 +168,27 @@ __device__ __forceinline__ float point_alpha_h(const RP& P, const float* __restr
 }
 
 // ---------------------------------------------------------------- binning ---
+// Warp aggregation of the per-pixel counters: points come grouped by leaf,
+// so consecutive lanes often hit the same pixel.  A run of equal pixels over
+// consecutive lanes is found with one shuffle and one ballot (its start is a
+// lane whose pixel differs from the previous lane's), and its first lane
+// updates the counter for the whole run.
+struct LaneRun {
+  int start;  // first lane of this lane's run
+  int len;    // lanes in the run (valid in the first lane)
+};
+
+__device__ __forceinline__ LaneRun lane_run(int q, int lane) {
+  const int prev = __shfl_up_sync(0xffffffffu, q, 1);
+  const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || prev != q);
+  const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+  const unsigned later = starts & ~upto;
+  LaneRun r;
+  r.start = 31 - __clz(starts & upto);
+  r.len = (later ? __ffs(later) - 1 : 32) - lane;
+  return r;
+}
+
 __global__ void __launch_bounds__(256) k_pix_count(RP P, const float* __restrict__ pos,
                                                    uint32_t* __restrict__ pix_count) {
   const unsigned full = 0xffffffffu;
@@ -180,9 +201,8 @@ __global__ void __launch_bounds__(256) k_pix_count(RP P, const float* __restrict
     if (id < n && splat_point(P, pos, id, s))
       for (int k = 0; k < 4; ++k) q[k] = corner_pixel(P, s.f, k);
     for (int k = 0; k < 4; ++k) {
-      // leaf-grouped points are spatially coherent: aggregate equal pixels per warp
-      const unsigned peers = __match_any_sync(full, q[k]);
-      if (q[k] >= 0 && lane == __ffs(peers) - 1) atomicAdd(pix_count + q[k], (uint32_t)__popc(peers));
+      const LaneRun run = lane_run(q[k], lane);
+      if (q[k] >= 0 && run.start == lane) atomicAdd(pix_count + q[k], (uint32_t)run.len);
     }
   }
 }
@@ -210,26 +230,26 @@ __global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restri
     const unsigned long long key = ((unsigned long long)(__float_as_uint(s.d) - P.dbase) << P.idb) | (unsigned long long)id;
     // the four corners' bucket offsets and atomics are all issued before
     // any result is used, so their round trips overlap
-    unsigned peers[4];
+    LaneRun run[4];
     uint32_t start[4], top[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      peers[k] = __match_any_sync(full, q[k]);
+      run[k] = lane_run(q[k], lane);
       start[k] = q[k] >= 0 ? __ldg(pix_start + q[k]) : 0u;
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       // counts run down from the bucket size, so the buckets fill back to front
       top[k] = 0;
-      if (q[k] >= 0 && lane == __ffs(peers[k]) - 1) top[k] = atomicSub(pix_count + q[k], (uint32_t)__popc(peers[k]));
+      if (q[k] >= 0 && run[k].start == lane) top[k] = atomicSub(pix_count + q[k], (uint32_t)run[k].len);
     }
     uint32_t slots[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const uint32_t t = __shfl_sync(peers[k], top[k], __ffs(peers[k]) - 1);
+      const uint32_t t = __shfl_sync(full, top[k], run[k].start);
       slots[k] = kNoSlot;
       if (q[k] >= 0) {
-        slots[k] = start[k] + t - 1 - __popc(peers[k] & ((1u << lane) - 1));
+        slots[k] = start[k] + t - 1 - (uint32_t)(lane - run[k].start);
         keys[slots[k]] = key;
         alpha[slots[k]] = fminf(__fmul_rn(ah, corner_weight(s.f, k & 1, k >> 1)), P.alpha_max);
       }
