@@ -168,6 +168,15 @@ __device__ __forceinline__ float point_alpha_h(const RP& P, const float* __restr
 }
 
 // ---------------------------------------------------------------- binning ---
+// The input of a point's alpha_h (h0 in head mode, else the given opacity)
+// and alpha_h from it, the same operations as point_alpha_h.
+template <class FT>
+__device__ __forceinline__ float alpha_input(const RP& P, const float* __restrict__ opacity,
+                                             const FT* __restrict__ feat, long long id) {
+  return P.head ? ld1(feat + (long long)P.F * id) : __ldg(opacity + id);
+}
+__device__ __forceinline__ float alpha_from_input(const RP& P, float v) { return P.head ? -expm1f(-expf(v)) : v; }
+
 // Warp aggregation of the per-pixel counters: points come grouped by leaf,
 // so consecutive lanes often hit the same pixel.  A run of equal pixels over
 // consecutive lanes is found with one shuffle and one ballot (its start is a
@@ -194,12 +203,25 @@ __global__ void __launch_bounds__(256) k_pix_count(RP P, const float* __restrict
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int n = (int)P.n;  // <= 2^28
-  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+  const int stride = gridDim.x * blockDim.x;
+  // each iteration loads the next point's position while it bins this one
+  float x = 0.f, y = 0.f, z = 0.f;
+  if (blockIdx.x * blockDim.x + threadIdx.x < n) {
+    const long long id = blockIdx.x * blockDim.x + threadIdx.x;
+    x = __ldg(pos + 3 * id); y = __ldg(pos + 3 * id + 1); z = __ldg(pos + 3 * id + 2);
+  }
+  for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
     const int id = base + threadIdx.x;
+    const long long nid = (long long)id + stride;
+    float nx = 0.f, ny = 0.f, nz = 0.f;
+    if (nid < n) {
+      nx = __ldg(pos + 3 * nid); ny = __ldg(pos + 3 * nid + 1); nz = __ldg(pos + 3 * nid + 2);
+    }
     int q[4] = {-1, -1, -1, -1};
     Splat s;
-    if (id < n && splat_point(P, pos, id, s))
+    if (id < n && splat_xyz(P, x, y, z, s))
       for (int k = 0; k < 4; ++k) q[k] = corner_pixel(P, s.f, k);
+    x = nx; y = ny; z = nz;
     for (int k = 0; k < 4; ++k) {
       const LaneRun run = lane_run(q[k], lane);
       if (q[k] >= 0 && run.start == lane) atomicAdd(pix_count + q[k], (uint32_t)run.len);
@@ -218,15 +240,31 @@ __global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restri
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int n = (int)P.n;  // <= 2^28
-  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+  const int stride = gridDim.x * blockDim.x;
+  // each iteration loads the next point's position and alpha input while it
+  // bins this one, so those round trips overlap this point's atomics
+  float x = 0.f, y = 0.f, z = 0.f, av = 0.f;
+  if (blockIdx.x * blockDim.x + threadIdx.x < n) {
+    const long long id = blockIdx.x * blockDim.x + threadIdx.x;
+    x = __ldg(pos + 3 * id); y = __ldg(pos + 3 * id + 1); z = __ldg(pos + 3 * id + 2);
+    av = alpha_input(P, opacity, feat, id);
+  }
+  for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
     const int id = base + threadIdx.x;
+    const long long nid = (long long)id + stride;
+    float nx = 0.f, ny = 0.f, nz = 0.f, na = 0.f;
+    if (nid < n) {
+      nx = __ldg(pos + 3 * nid); ny = __ldg(pos + 3 * nid + 1); nz = __ldg(pos + 3 * nid + 2);
+      na = alpha_input(P, opacity, feat, nid);
+    }
     int q[4] = {-1, -1, -1, -1};
     Splat s;
     float ah = 0.f;
-    if (id < n && splat_point(P, pos, id, s)) {
+    if (id < n && splat_xyz(P, x, y, z, s)) {
       for (int k = 0; k < 4; ++k) q[k] = corner_pixel(P, s.f, k);
-      ah = point_alpha_h(P, opacity, feat, id, nullptr);
+      ah = alpha_from_input(P, av);
     }
+    x = nx; y = ny; z = nz; av = na;
     const unsigned long long key = ((unsigned long long)(__float_as_uint(s.d) - P.dbase) << P.idb) | (unsigned long long)id;
     // the four corners' bucket offsets and atomics are all issued before
     // any result is used, so their round trips overlap
