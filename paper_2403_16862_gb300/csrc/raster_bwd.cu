@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
   // over them, so at any moment its warps work on neighbouring points
   // (shared image and fragment data in L1) while each slot's own sequence,
   // kGroups points apart, stays within a leaf or two
-  // n <= 2^25 (the rasterizer's key packing), so 32-bit point indices
+  // n <= 2^25 (the limit of the backward calls), so 32-bit point indices
   const int first = (int)blockIdx.x * chunk + slot;
   const int last = (int)min((long long)(blockIdx.x + 1) * chunk, P.n);
   const uint64_t keep = l2_evict_last(), stream = l2_evict_first();
