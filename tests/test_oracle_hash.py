@@ -156,3 +156,12 @@ def test_finite_difference_table_gradient(oracle):
         tm = tab.copy(); tm[r, f] -= e
         fd = (np.sum(oracle.hash_fwd(res, log2_T, tp, pos) * dh) - np.sum(oracle.hash_fwd(res, log2_T, tm, pos) * dh)) / (2 * e)
         assert abs(fd - grad[r, f]) < 1e-6 * (1 + abs(fd))
+
+
+def test_hashed_index_golden(oracle):
+    # hand-derived spatial-hash indices (uint32 products, XOR, mod T) on a
+    # hashed level: a wrong prime or + in place of XOR fails one of them
+    g = json.load(open(os.path.join(GOLDEN, "hash_index.json")))
+    assert (g["res"] + 1) ** 3 > 2 ** g["log2_T"], "the level must be hashed"
+    for case in g["cases"]:
+        assert oracle.hash_vertex_index(g["res"], g["log2_T"], *case["v"]) == case["index"], case
