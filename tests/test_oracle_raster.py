@@ -233,3 +233,113 @@ def test_pipeline_table_gradient_finite_differences(oracle):
         tm = tab.copy(); tm[r, f] -= e
         fd = (loss(tp) - loss(tm)) / (2 * e)
         assert abs(fd - dtab[r, f]) <= 1e-6 * (1 + abs(fd)), (r, f, fd, dtab[r, f])
+
+
+def test_differentiation_subcase_finite_differences(oracle):
+    """FP64 central differences on the differentiation workload's small case:
+    the first 4,096 samples of the 65,536-leaf octree scene (seed 0, view
+    0), the 16-level 2^19 grid, a 64x64 view from the benchmark camera with
+    the focal length scaled to 45 (the full view's 900 / 20), upstream
+    gradient ~ N(0, 1).  Checked: d h (the opacity path through h0 and the
+    color channels, head mode), d alpha and d F in given-opacity mode
+    (alpha = the head's alpha of the same points, F = the color channels),
+    and d table through the whole pipeline.  Perturbations that change a
+    pixel's blended count (the early stop) are rejected and not counted."""
+    res = scenes.geometric_resolutions(16, 16, 4096)
+    tree = scenes.make_octree(0, 65536)
+    grid = scenes.make_hashgrid(1, oracle.hash_entries(res, 19), res, 19)
+    _, pos64, _ = oracle.sample_octree(tree, 0, 0, 4096)
+    pos = pos64.astype(np.float32)
+    cam = scenes.make_camera((0.5, 0.5, -1.2), 45.0, 45.0, 32.0, 32.0, 64, 64)
+    g = scenes.upstream_grad(2, (64, 64, 64)).astype(np.float64)
+    tab = grid.table.astype(np.float64)
+    h = oracle.hash_fwd(res, 19, tab, pos)
+    base = oracle.raster_fwd(cam, pos, h, head_mode=True)
+    assert base["n_contrib"].max() > 8 and (base["n_contrib"] > 0).mean() > 0.2, "a blended scene"
+    rng = np.random.default_rng(20)
+    eps = 1e-6
+
+    def central(loss, perturb, n_want, draw):
+        done = tried = 0
+        while done < n_want:
+            tried += 1
+            assert tried < 4 * n_want, "too many perturbations crossed the stop threshold"
+            k = draw()
+            lp, lm = loss(perturb(k, eps)), loss(perturb(k, -eps))
+            if lp is None or lm is None:
+                continue
+            yield k, (lp - lm) / (2 * eps)
+            done += 1
+
+    # head mode: d h (channel 0 carries the opacity path)
+    bh = oracle.raster_bwd(cam, pos, h, g, head_mode=True)["d_feat"]
+
+    def loss_h(hh):
+        out = oracle.raster_fwd(cam, pos, hh, head_mode=True)
+        return None if not np.array_equal(out["n_contrib"], base["n_contrib"]) else float(np.sum(out["image"] * g))
+
+    def pert_h(k, e):
+        hh = h.copy()
+        hh[k] += e
+        return hh
+
+    vis = np.flatnonzero(np.abs(bh).sum(axis=1) > 0)
+    draws = iter([(int(rng.choice(vis)), 0) for _ in range(40)] + [(int(rng.choice(vis)), int(rng.integers(1, 64)))
+                                                                   for _ in range(40)])
+    for k, fd in central(lambda x: loss_h(x), pert_h, 30, lambda: next(draws)):
+        assert abs(fd - bh[k]) <= 1e-6 * (1 + abs(fd)), ("dh", k, fd, bh[k])
+
+    # given-opacity mode on the same points: d alpha and d F
+    alpha = 1.0 - np.exp(-np.exp(h[:, 0]))
+    F = h[:, 1:].copy()
+    base_g = oracle.raster_fwd(cam, pos, F, opacity=alpha)
+    bg = oracle.raster_bwd(cam, pos, F, g[..., 1:], opacity=alpha)
+
+    def loss_g(f, o):
+        out = oracle.raster_fwd(cam, pos, f, opacity=o)
+        return None if not np.array_equal(out["n_contrib"], base_g["n_contrib"]) else \
+            float(np.sum(out["image"] * g[..., 1:]))
+
+    def pert_a(k, e):
+        o = alpha.copy()
+        o[k] += e
+        return o
+
+    def pert_f(k, e):
+        f = F.copy()
+        f[k] += e
+        return f
+
+    da = iter([int(rng.choice(vis)) for _ in range(40)])
+    for k, fd in central(lambda o: loss_g(F, o), pert_a, 20, lambda: next(da)):
+        assert abs(fd - bg["d_opacity"][k]) <= 1e-6 * (1 + abs(fd)), ("d alpha", k, fd, bg["d_opacity"][k])
+    df = iter([(int(rng.choice(vis)), int(rng.integers(0, 63))) for _ in range(40)])
+    for k, fd in central(lambda f: loss_g(f, alpha), pert_f, 20, lambda: next(df)):
+        assert abs(fd - bg["d_feat"][k]) <= 1e-6 * (1 + abs(fd)), ("dF", k, fd, bg["d_feat"][k])
+
+    # d table through query -> rasterizer, on rows the points reach
+    dtab = oracle.hash_bwd(res, 19, 4, pos, bh)
+    rows = np.flatnonzero(np.abs(dtab).sum(axis=1) > 0)
+
+    def loss_t(k, e):
+        r, f = k
+        old = tab[r, f]
+        tab[r, f] = old + e
+        try:
+            return loss_h(oracle.hash_fwd(res, 19, tab, pos))
+        finally:
+            tab[r, f] = old
+
+    dt = iter([(int(rng.choice(rows)), int(rng.integers(0, 4))) for _ in range(40)])
+    done = 0
+    for _ in range(40):
+        k = next(dt)
+        lp, lm = loss_t(k, eps), loss_t(k, -eps)
+        if lp is None or lm is None:
+            continue
+        fd = (lp - lm) / (2 * eps)
+        assert abs(fd - dtab[k]) <= 1e-6 * (1 + abs(fd)), ("d table", k, fd, dtab[k])
+        done += 1
+        if done == 20:
+            break
+    assert done == 20
