@@ -49,12 +49,17 @@ def workload_config(extra=None):
     return cfg
 
 
-def make_scene():
+def make_scene(n_entries_fn=None):
+    """The seeded scene.  ``n_entries_fn(res, log2_T)`` sizes the table: the
+    library's layout query on the GPU arm, the oracle's on the reference arm
+    (which loads nothing but the oracle)."""
     from paper_2403_16862_gb300 import scenes
-    from paper_2403_16862_gb300 import api
+    if n_entries_fn is None:
+        from paper_2403_16862_gb300 import api
+        n_entries_fn = api.hashgrid_n_entries
     tree = scenes.make_octree(0, N_LEAVES)
     res = scenes.geometric_resolutions(16, 16, 4096)
-    grid = scenes.make_hashgrid(1, api.hashgrid_n_entries(res, LOG2_T), res, LOG2_T)
+    grid = scenes.make_hashgrid(1, n_entries_fn(res, LOG2_T), res, LOG2_T)
     f = 900.0 / SCALE
     cam = scenes.make_camera((0.5, 0.5, -1.2), f, f, W / 2.0, H / 2.0, W, H)
     g = scenes.upstream_grad(2, (H, W, C))
@@ -79,12 +84,39 @@ KERNELS = ["k_draw_count", "k_place", "k_hash_fwd", "k_pix_count", "k_pix_scatte
            "k_blend_fwd_large", "k_blend_fwd_heavy", "k_blend_bwd", "k_blend_bwd_large", "k_blend_bwd_heavy",
            "k_point_grad_hash", "k_point_grad", "k_hash_bwd"]
 
-# DRAM bytes per launch of the dominant kernel on the full workload, from one
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); see profiles/.
-TRAFFIC = {"k_point_grad_hash": 2_748_142_592 + 720_322_560}
-# L2 vector-reduction requests of one launch of the dominant kernel on the full
-# workload (lts__t_requests_op_red.sum, one ncu capture); see profiles/.
-L2_REDUCTIONS = {"k_point_grad_hash": 243_221_479}
+# Counters of one launch of the dominant kernel on the full workload, from one
+# ncu capture each (profiles/ holds the command and the summary):
+#   traffic        dram__bytes_read.sum + dram__bytes_write.sum
+#   l2_reductions  lts__t_requests_op_red.sum
+# with the stamp of the kernel's sources at the time of the capture.  A
+# different stamp means the kernel changed since: the counters are then
+# reported as null rather than as figures of another kernel.
+CAPTURED = {"k_point_grad_hash": {"traffic": 2_769_795_072 + 724_850_944, "l2_reductions": 243_212_179,
+                                  "stamp": "62c2bd64da4be2de"}}
+# the sources each kernel's code comes from (stamped for CAPTURED)
+KERNEL_SOURCES = {"k_point_grad_hash": ["raster_bwd.cu", "raster_impl.cuh", "hashgrid_impl.cuh", "common.cuh"],
+                  "k_hash_fwd": ["hashgrid.cu", "hashgrid_impl.cuh", "common.cuh"]}
+
+
+def source_stamp(kernel):
+    import hashlib
+    files = KERNEL_SOURCES.get(kernel)
+    if not files:
+        return None
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2403_16862_gb300", "csrc", f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured(kernel, key):
+    """A counter of CAPTURED, or None when the kernel's sources changed since
+    the capture (or the run is not the full workload)."""
+    c = CAPTURED.get(kernel)
+    if not c or SCALE != 1 or c.get("stamp") != source_stamp(kernel):
+        return None
+    return c.get(key)
 
 
 def kernel_bytes(kernel, n, n_entries, n_frag, n_pix):
@@ -111,9 +143,8 @@ def atomic_ceiling(kernel, n, ms):
     if kernel != "k_point_grad_hash":
         return {}
     out = {"corner_contributions": 8 * 16 * n}
-    red = L2_REDUCTIONS.get(kernel) if SCALE == 1 else None
-    if red:
-        out.update({"l2_reductions": red, "l2_reduction_gops": red / (ms * 1e-3) / 1e9})
+    red = captured(kernel, "l2_reductions")
+    out.update({"l2_reductions": red, "l2_reduction_gops": red / (ms * 1e-3) / 1e9 if red else None})
     return out
 
 
@@ -204,7 +235,7 @@ def run_reference(args, rank):
         return 0
     from oracle import oracle as O
     O.build()
-    tree, res, grid, cam, g = make_scene()
+    tree, res, grid, cam, g = make_scene(O.hash_entries)
     n_ref = 1 << 20  # bounded sample: a quarter of the view's samples per step
     for i in range(args.warmup):
         oracle_view(tree, res, grid, cam, g, n_ref, view=100 + i)
@@ -267,6 +298,8 @@ def main():
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     if world > 1:
+        # NVLS off: the exchange is a plain ring/tree all-reduce
+        os.environ.setdefault("NCCL_NVLS_ENABLE", "0")
         dist.init_process_group("nccl", init_method="env://")
 
     tree, res, grid, cam, g_np = make_scene()
@@ -291,6 +324,10 @@ def main():
     ncon = torch.empty(H, W, dtype=torch.int32, device=dev)
     dh = torch.empty(N, C, dtype=torch.float32, device=dev) if args.unfused else None
     gtab = torch.zeros(n_entries, 4, dtype=torch.float32, device=dev)
+    # N > 1: the table gradient's sum over ranks (the one exchange of the
+    # step) runs asynchronously after each backward, overlapped with the next
+    # view's forward, on two alternating gradient tables
+    gx = shard.GradExchange((n_entries, 4), dev) if world > 1 else None
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -305,14 +342,20 @@ def main():
         mark(2)
         api.rasterize_fwd(cam, opts, pos, h, None, ws=ws_r, out=(img, T, ncon))
         mark(3)
-        gtab.zero_()
+        if gx is not None:
+            gt = gx.begin()  # waits for the sum of two steps ago on this table
+        else:
+            gt = gtab
+            gt.zero_()
         if args.unfused:
             api.rasterize_bwd(cam, opts, pos, h, None, T, ncon, g_img, ws_r, out=(None, dh))
             mark(4)
-            api.query_hashgrid_bwd(desc, pos, dh, gtab)
+            api.query_hashgrid_bwd(desc, pos, dh, gt)
         else:
             mark(4)
-            api.rasterize_bwd_hashgrid(cam, opts, desc, pos, h, T, ncon, g_img, ws_r, gtab)
+            api.rasterize_bwd_hashgrid(cam, opts, desc, pos, h, T, ncon, g_img, ws_r, gt)
+        if gx is not None:
+            gx.launch()
         mark(5)
 
     stages = ["sample", "query_fwd", "raster_fwd", "table_zero", "raster_bwd+query_bwd"] if not args.unfused else \
@@ -329,26 +372,43 @@ def main():
     sampler.start()
     time.sleep(0.3)
     launches0 = B.inpc_kernel_launches()
-    B.inpc_kernel_timer_read()  # drop records of earlier launches
-    B.inpc_kernel_timer_enable(True)
     for k in range(args.steps):
         flush.fill_(k & 0xFF)  # evict the previous step from L2 (outside the events)
         view(shard.view_ids(rank, world, k)[0], evs[k])
+    tail = None
+    if gx is not None:
+        # the last step's exchange belongs to the timed work
+        gx.finish()
+        tail = torch.cuda.Event(enable_timing=True)
+        tail.record(stream)
     torch.cuda.synchronize()
-    B.inpc_kernel_timer_enable(False)
     launches = B.inpc_kernel_launches() - launches0
-    kernel_ms = {}
-    for kname in KERNELS:
-        ms, cnt = B.inpc_kernel_timer_read(kname)
-        if cnt:
-            kernel_ms[kname] = (ms / args.steps, cnt // args.steps)
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
 
+    # per-kernel device times in a separate pass over the same views (the
+    # library's launch timer records two events around each launch, which
+    # stays out of the headline region)
+    k_steps = min(args.steps, 10)
+    B.inpc_kernel_timer_read()  # drop records of earlier launches
+    B.inpc_kernel_timer_enable(True)
+    for k in range(k_steps):
+        flush.fill_(k & 0xFF)
+        view(shard.view_ids(rank, world, k)[0])
+    if gx is not None:
+        gx.finish()
+    torch.cuda.synchronize()
+    B.inpc_kernel_timer_enable(False)
+    kernel_ms = {}
+    for kname in KERNELS:
+        ms, cnt = B.inpc_kernel_timer_read(kname)
+        if cnt:
+            kernel_ms[kname] = (ms / k_steps, cnt // k_steps)
+
     per_stage = {s: [evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)] for i, s in enumerate(stages)}
     step_ms = [evs[k][0].elapsed_time(evs[k][5]) for k in range(args.steps)]
-    total_ms = sum(step_ms)
+    total_ms = sum(step_ms) + (evs[-1][5].elapsed_time(tail) if tail is not None else 0.0)
     total_ms = shard.max_over_ranks(total_ms, dev)
     value = N * args.steps * world / (total_ms * 1e-3) / 1e9
     ms_per_step = total_ms / args.steps
@@ -387,12 +447,15 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config({"views_per_step_per_gpu": 1, "parallelism": "views sharded over %d GPU(s)" % world}),
+            "config": workload_config({"views_per_step_per_gpu": 1, "parallelism": "views sharded over %d GPU(s)" % world
+                                       + ("; FP32 table-gradient all-reduce per step, overlapped with the next view's "
+                                          "forward" if world > 1 else "")}),
             "stages_ms": {s: round(stage_mean[s], 4) for s in stages},
             "kernels_ms": {k: round(v[0], 4) for k, v in sorted(kernel_ms.items(), key=lambda kv: -kv[1][0])},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if achieved else None,
-                         "traffic": TRAFFIC.get(dom) if not args.unfused and SCALE == 1 else None,
+                         "traffic": captured(dom, "traffic") if not args.unfused else None,
+                         "counters_stamp": source_stamp(dom),
                          "peak_kind": peak_kind + " (copy bandwidth)", "launch_ms": dom_ms,
                          "algorithmic_bytes": dom_bytes, **atomic_ceiling(dom, N, dom_ms)},
             "step_roofline": {"algorithmic_bytes": total_bytes,
@@ -529,13 +592,29 @@ def run_forms(args, api, B, dev, world, rank):
     vb.capture()
     ms_batch = timed(lambda k: vb.step(), steps)
     errs = [nerr(imgs32[v], vb.views[v]["img"]) for v in range(len(cams))]
+    tiles = [(d["opts"].tile_w, d["opts"].tile_h) for d in vb.views]
+    del vb
+    torch.cuda.empty_cache()
+    # the same batch with the sampling and query of all views in one
+    # persistent work-queue launch (same autotuned tiles)
+    vp = ViewBatch(c, l, w, tree.root_size, d16, t16, cams, n5, grads, seed=0, n_streams=4, bf16=True, tune=False,
+                   persistent=True)
+    for d, (tw, th) in zip(vp.views, tiles):
+        d["opts"].tile_w, d["opts"].tile_h = tw, th
+    vp.capture()
+    ms_pers = timed(lambda k: vp.step(), steps)
+    errs_p = [nerr(imgs32[v], vp.views[v]["img"]) for v in range(len(cams))]
+    vb = vp
     out["bf16_batched_8views"] = {
         "workload": "8 views %s, 8,388,608 samples each from one 1,048,576-leaf octree, 16-level 2^21x4 BF16 grid, "
                     "one CUDA graph over 4 streams, autotuned tiles, fwd + fused bwd" % sizes,
         "ms_per_step": ms_batch, "ms_per_view": ms_batch / len(cams),
         "gpoints_s": n5 * len(cams) / (ms_batch * 1e-3) / 1e9,
         "fp32_unbatched_ms_per_step": ms_plain, "speedup_vs_plain_fp32": ms_plain / ms_batch,
-        "tiles": [[d["opts"].tile_w, d["opts"].tile_h] for d in vb.views],
+        "tiles": [list(t) for t in tiles],
+        "persistent_front": {"ms_per_step": ms_pers, "speedup_vs_plain_fp32": ms_plain / ms_pers,
+                             "speedup_vs_stream_fork": ms_batch / ms_pers,
+                             "image_max_err_over_views": max(errs_p)},
         "error_vs_fp32_normwise": {"image_max_over_views": max(errs), "grad_table": nerr(gt32, vb.grad_table)}}
     del vb
     torch.cuda.empty_cache()
@@ -558,6 +637,33 @@ def run_forms(args, api, B, dev, world, rank):
         "ms_per_step": ms_batch_s, "ms_per_view": ms_batch_s / len(cams_s),
         "unbatched_ms_per_step": ms_plain_s, "speedup_vs_unbatched": ms_plain_s / ms_batch_s}
     del vb
+    torch.cuda.empty_cache()
+
+    # ---- launch-dominated batch: 64 small views of 262,144 samples each,
+    # stream-fork graph against the persistent front end
+    tree64 = scenes.make_octree(0, 65536)
+    c64, l64, w64 = (torch.from_numpy(x).to(dev) for x in (tree64.centers, tree64.levels, tree64.weights))
+    n_ent19 = api.hashgrid_n_entries(res, 19)
+    t19 = torch.from_numpy(scenes.make_hashgrid(1, n_ent19, res, 19).table).to(dev)
+    d19 = api.hashgrid_desc(res, 19)
+    cams_t = scenes.orbit_cameras([(320, 240)] * 64, focal_ref=300.0, ref_height=240)
+    grads_t = [dgrad(q, 500 + v) for v, q in enumerate(cams_t)]
+    n_t = 1 << 18
+    res_t = {}
+    for pers in (False, True):
+        vb = ViewBatch(c64, l64, w64, tree64.root_size, d19, t19, cams_t, n_t, grads_t, seed=0, n_streams=8,
+                       bf16=False, tune=False, persistent=pers)
+        vb.capture()
+        res_t[pers] = timed(lambda k: vb.step(), steps)
+        del vb
+        torch.cuda.empty_cache()
+    out["fp32_batched_64_tiny_views"] = {
+        "workload": "64 views 320x240 on an orbit, 262,144 samples each from the 65,536-leaf octree, 16-level "
+                    "2^19x4 FP32 grid, one CUDA graph, fwd + fused bwd",
+        "stream_fork_ms_per_step": res_t[False], "persistent_front_ms_per_step": res_t[True],
+        "speedup_persistent_vs_fork": res_t[False] / res_t[True],
+        "gpoints_s_persistent": 64 * n_t / (res_t[True] * 1e-3) / 1e9}
+    del grads_t, t19
     torch.cuda.empty_cache()
 
     # ---- inference: a pre-extracted cloud rendered from several views

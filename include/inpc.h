@@ -46,6 +46,7 @@ typedef enum {
 #define INPC_DEV_NO_WEIGHT 0x2u    /* no leaf weight was positive */
 #define INPC_DEV_BAD_LEAF 0x4u      /* inpc_octree_update: a leaf index outside [0, n_leaves) (ignored) */
 #define INPC_DEV_BAD_BLEND_WEIGHT 0x8u /* inpc_octree_update: a negative or NaN weight (counted as 0) */
+#define INPC_DEV_TIMEOUT 0x10u     /* inpc_sample_query_batch: a bounded work-queue wait gave up (outputs undefined) */
 
 typedef enum { INPC_F32 = 0, INPC_BF16 = 1 } inpc_dtype;
 
@@ -69,7 +70,11 @@ int inpc_kernel_timer_enable(int on);
  * INPC_ERR_INVALID_ARG (null output pointer), INPC_ERR_CUDA. */
 inpc_status inpc_kernel_timer_read(const char* kernel, double* total_ms, int64_t* launches);
 /* Copies the device status word at the start of `workspace` (any workspace
- * of this library) to *status_out after synchronising `stream`. */
+ * of this library) to *status_out after synchronising `stream`.  A null
+ * `workspace` reads the status word of inpc_sample_octree_noalloc instead:
+ * the first word of its static scratch array on the current device, which
+ * every such call clears before it runs.  Errors: INPC_ERR_INVALID_ARG (null
+ * status_out), INPC_ERR_CUDA. */
 inpc_status inpc_read_device_status(const void* workspace, inpc_stream_t stream, uint32_t* status_out);
 
 /* ======================================================================== */
@@ -118,6 +123,22 @@ inpc_status inpc_sample_octree(const inpc_octree* tree, uint64_t seed, uint32_t 
                                int32_t* leaf_idx_out, float* pos_out, int32_t* leaf_counts_out,
                                void* workspace, size_t workspace_bytes, inpc_stream_t stream);
 
+/* The counter-based generator behind every random number of the sampler
+ * (Sec. 3.2 draws leaves and positions at random; this library takes them
+ * from Philox4x32-10, Salmon, Moraes, Dror and Shaw, SC'11, ten rounds with
+ * the published multipliers and Weyl key increments).  Evaluates it on n
+ * caller-given (key, counter) pairs, so that callers can reproduce the
+ * sampler's stream and tests can check the generator against its published
+ * known-answer values:
+ *   keys  uint32 [n, 2]   (k0, k1): the sampler uses (seed lo, seed hi)
+ *   ctrs  uint32 [n, 4]   (c0, c1, c2, c3): the sampler uses
+ *                         (index lo, index hi, view_id, purpose)
+ *   out   uint32 [n, 4]   the four output words
+ * All three are device pointers, 4-byte aligned; n >= 0.
+ * Errors: INPC_ERR_INVALID_ARG (null pointer with n > 0, negative n). */
+inpc_status inpc_philox4x32_10(const uint32_t* keys, const uint32_t* ctrs, int64_t n, uint32_t* out,
+                               inpc_stream_t stream);
+
 /* Allocation-free variant of inpc_sample_octree (the paper has no
  * counterpart; this is a deployment aid).  Some callers cannot allocate
  * device memory at all: a host application or engine that owns every byte of
@@ -127,13 +148,16 @@ inpc_status inpc_sample_octree(const inpc_octree* tree, uint64_t seed, uint32_t 
  * lives in a file-scope device array of INPC_SAMPLE_STATIC_SCRATCH_BYTES
  * (4 MiB + 576 KiB: about 266,000 leaves), which every GPU that loads this
  * library holds until the process exits.
- *   - Same definition, outputs and device status bits as inpc_sample_octree
- *     (the status word sits at the start of the static array).
+ *   - Same definition, outputs and device status bits as inpc_sample_octree;
+ *     the status word is the first word of the static array, read with
+ *     inpc_read_device_status(NULL, stream, &status) on the same device.
  *   - Returns INPC_ERR_CAPACITY, before touching the device, when the tree
  *     needs more scratch than the array holds.
  *   - The first call on a device looks up the array's device address (with
- *     that device current) and caches it; make that first call before any
- *     stream capture.
+ *     that device current) and caches it with the id of the current CUDA
+ *     context; a call in another context of that device (for instance after
+ *     cudaDeviceReset, which also discards the array's contents) looks it up
+ *     again.  Make the first call on a device before any stream capture.
  *   - Allocates nothing (no cudaMalloc, no library allocation); every call on
  *     a device shares the one array, each call clears what must start at
  *     zero, and calls whose GPU work overlaps (other streams, other host
@@ -520,6 +544,85 @@ typedef struct {
 inpc_status inpc_render_batch(const inpc_octree* tree, uint64_t seed, const inpc_hashgrid_desc* grid,
                               const void* table, const inpc_view_job* views, int32_t n_views, float* grad_table,
                               const inpc_stream_t* streams, int32_t n_streams);
+
+/* ------------------------------------------------------------------------ */
+/* Persistent front end of a batch of views (many camera views per launch:  */
+/* the paper renders one view at a time, Sec. 4.1 and Table 2 time it).    */
+/* ------------------------------------------------------------------------ */
+/* One view of inpc_sample_query_batch:
+ *   view_id    the view's Philox stream of the batch's seed (Sec. 3.2)
+ *   n_samples  points drawn for the view, in [0, 2^29]
+ *   leaf_idx   int32 [n_samples], pos float32 [n_samples, 3]: as
+ *              inpc_sample_octree's outputs
+ *   h          [n_samples, 4 * n_levels] of the grid's out_dtype: as
+ *              inpc_query_hashgrid's output (16-byte aligned for FP32,
+ *              8-byte for BF16) */
+typedef struct {
+  uint32_t view_id;
+  int64_t n_samples;
+  int32_t* leaf_idx;
+  float* pos;
+  void* h;
+} inpc_front_view;
+
+/* Workspace bytes of inpc_sample_query_batch for a tree of n_leaves and a
+ * batch of n_views views.  Errors: INPC_ERR_CAPACITY (n_leaves outside
+ * [1, 2^24], n_views outside [1, 64]). */
+inpc_status inpc_sample_query_batch_workspace_size(int64_t n_leaves, int32_t n_views, size_t* bytes);
+
+/* The sampling (Sec. 3.2, exactly inpc_sample_octree's definition) and the
+ * grid query (Sec. 3.3, exactly inpc_query_hashgrid's) of n_views views of
+ * one octree and one table, in ONE persistent kernel launch: CTAs take work
+ * items (stage, view, tile) from a queue in the workspace, and an item that
+ * depends on others waits for them.  The leaf CDF is built once for the
+ * batch.  Outputs are bit-identical to inpc_sample_octree followed by
+ * inpc_query_hashgrid for each view.
+ *   max_wait_us  bound of every wait, in microseconds of the GPU's global
+ *                timer, in [1, 6e7]; a wait that runs out sets
+ *                INPC_DEV_TIMEOUT in the workspace's status word (read with
+ *                inpc_read_device_status), every CTA then returns, and the
+ *                outputs are undefined.  No wait is longer than its bound.
+ * Device status bits as inpc_sample_octree (bad and all-zero weights) plus
+ * INPC_DEV_TIMEOUT.  The workspace must not be shared by calls whose GPU
+ * work overlaps.  Errors: INPC_ERR_INVALID_ARG (null pointer, misaligned
+ * output, workspace too small, max_wait_us out of range), INPC_ERR_CAPACITY
+ * (sizes), INPC_ERR_UNSUPPORTED (grid options), INPC_ERR_CUDA. */
+inpc_status inpc_sample_query_batch(const inpc_octree* tree, uint64_t seed, const inpc_hashgrid_desc* grid,
+                                    const void* table, const inpc_front_view* views, int32_t n_views,
+                                    int64_t max_wait_us, void* workspace, size_t workspace_bytes,
+                                    inpc_stream_t stream);
+
+/* inpc_render_batch with the sampling and query of all views in the
+ * persistent kernel of inpc_sample_query_batch (launches of up to 64 views
+ * each, on streams[0], before the fork), then each view's rasterizer
+ * forward and fused backward over the streams as in inpc_render_batch.  The
+ * jobs' sample_ws are not used; front_workspace holds
+ * inpc_sample_query_batch_workspace_size(n_leaves, min(n_views, 64)) bytes.
+ * Outputs are bit-identical to inpc_render_batch's (the table gradient up
+ * to the order of its atomic additions).  max_wait_us and the device status
+ * (in front_workspace) as for inpc_sample_query_batch.  Errors as for
+ * inpc_render_batch and inpc_sample_query_batch. */
+inpc_status inpc_render_batch_persistent(const inpc_octree* tree, uint64_t seed, const inpc_hashgrid_desc* grid,
+                                         const void* table, const inpc_view_job* views, int32_t n_views,
+                                         float* grad_table, const inpc_stream_t* streams, int32_t n_streams,
+                                         void* front_workspace, size_t front_workspace_bytes, int64_t max_wait_us);
+
+/* Host-side fault injection for failure tests (no counterpart in the
+ * paper).  spec (NULL or "" disarms):
+ *   "workspace_overflow"  every *_workspace_size query returns
+ *                         INPC_ERR_CAPACITY, as if the sizes overflowed
+ *   "corrupt_args"        every compute entry point sees its first array
+ *                         argument as NULL; its own validation must then
+ *                         return INPC_ERR_INVALID_ARG before enqueuing
+ *                         anything
+ *   "queue_short"         the next inpc_sample_query_batch launch waits for
+ *                         one more draw tile of its first view than exists,
+ *                         so that wait runs out (INPC_DEV_TIMEOUT) and the
+ *                         kernel returns; disarmed by that launch
+ * The INPC_FAULT environment variable, read at the library's first use,
+ * arms the same faults.  Nothing is injected on the device.  Errors:
+ * INPC_ERR_INVALID_ARG (unknown spec). */
+inpc_status inpc_set_fault(const char* spec);
 
 #ifdef __cplusplus
 }

@@ -26,6 +26,7 @@ INPC_DEV_BAD_WEIGHT = 0x1
 INPC_DEV_NO_WEIGHT = 0x2
 INPC_DEV_BAD_LEAF = 0x4
 INPC_DEV_BAD_BLEND_WEIGHT = 0x8
+INPC_DEV_TIMEOUT = 0x10
 
 INPC_F32 = 0
 INPC_BF16 = 1
@@ -45,7 +46,9 @@ DECLARED = [
     "inpc_view_weights", "inpc_sample_octree_view",
     "inpc_level_weights", "inpc_sample_octree_halton", "inpc_accumulate_image",
     "inpc_contract_positions", "inpc_sh_head_fwd", "inpc_sh_head_bwd",
-    "inpc_render_batch",
+    "inpc_render_batch", "inpc_philox4x32_10",
+    "inpc_sample_query_batch_workspace_size", "inpc_sample_query_batch", "inpc_render_batch_persistent",
+    "inpc_set_fault",
 ]
 
 
@@ -58,6 +61,11 @@ class InpcError(RuntimeError):
 class InpcOctree(C.Structure):
     _fields_ = [("centers", C.c_void_p), ("levels", C.c_void_p), ("weights", C.c_void_p),
                 ("root_size", C.c_float), ("n_leaves", C.c_int64)]
+
+
+class InpcFrontView(C.Structure):
+    _fields_ = [("view_id", C.c_uint32), ("n_samples", C.c_int64), ("leaf_idx", C.c_void_p), ("pos", C.c_void_p),
+                ("h", C.c_void_p)]
 
 
 class InpcHashgridDesc(C.Structure):
@@ -107,6 +115,7 @@ def load(path: str = LIB_PATH):
         L.inpc_sample_workspace_size.argtypes = [C.c_int64, C.c_int64, C.POINTER(C.c_size_t)]
         L.inpc_sample_octree.argtypes = [C.POINTER(InpcOctree), C.c_uint64, C.c_uint32, C.c_int64, _P, _P, _P, _P,
                                          C.c_size_t, _P]
+        L.inpc_philox4x32_10.argtypes = [_P, _P, C.c_int64, _P, _P]
         L.inpc_sample_octree_noalloc.argtypes = [C.POINTER(InpcOctree), C.c_uint64, C.c_uint32, C.c_int64, _P, _P,
                                                  _P, _P]
         L.inpc_hashgrid_n_entries.argtypes = [C.POINTER(InpcHashgridDesc), C.POINTER(C.c_int64)]
@@ -146,6 +155,13 @@ def load(path: str = LIB_PATH):
                                        _P]
         L.inpc_render_batch.argtypes = [C.POINTER(InpcOctree), C.c_uint64, C.POINTER(InpcHashgridDesc), _P,
                                         C.POINTER(InpcViewJob), C.c_int32, _P, C.POINTER(_P), C.c_int32]
+        L.inpc_sample_query_batch_workspace_size.argtypes = [C.c_int64, C.c_int32, C.POINTER(C.c_size_t)]
+        L.inpc_sample_query_batch.argtypes = [C.POINTER(InpcOctree), C.c_uint64, C.POINTER(InpcHashgridDesc), _P,
+                                              C.POINTER(InpcFrontView), C.c_int32, C.c_int64, _P, C.c_size_t, _P]
+        L.inpc_render_batch_persistent.argtypes = [C.POINTER(InpcOctree), C.c_uint64, C.POINTER(InpcHashgridDesc),
+                                                   _P, C.POINTER(InpcViewJob), C.c_int32, _P, C.POINTER(_P),
+                                                   C.c_int32, _P, C.c_size_t, C.c_int64]
+        L.inpc_set_fault.argtypes = [C.c_char_p]
         L.inpc_kernel_timer_enable.argtypes = [C.c_int]
         L.inpc_kernel_timer_read.argtypes = [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         for name in DECLARED:
@@ -200,13 +216,17 @@ def inpc_sample_octree(tree: InpcOctree, seed: int, view_id: int, n_samples: int
                                     pos_out, leaf_counts_out, workspace, workspace_bytes, stream))
 
 
-INPC_SAMPLE_STATIC_SCRATCH_BYTES = (4 << 20) + (64 << 10)
+INPC_SAMPLE_STATIC_SCRATCH_BYTES = (4 << 20) + (576 << 10)
 
 
 def inpc_sample_octree_noalloc(tree: InpcOctree, seed: int, view_id: int, n_samples: int, leaf_idx_out: int,
                                pos_out: int, leaf_counts_out, stream: int):
     check(load().inpc_sample_octree_noalloc(C.byref(tree), C.c_uint64(seed), C.c_uint32(view_id), n_samples,
                                             leaf_idx_out, pos_out, leaf_counts_out, stream))
+
+
+def inpc_philox4x32_10(keys: int, ctrs: int, n: int, out: int, stream: int):
+    check(load().inpc_philox4x32_10(keys, ctrs, n, out, stream))
 
 
 def inpc_hashgrid_n_entries(desc: InpcHashgridDesc) -> int:
@@ -346,3 +366,28 @@ def inpc_render_batch(tree: InpcOctree, seed: int, desc: InpcHashgridDesc, table
     st = (_P * len(streams))(*streams)
     check(load().inpc_render_batch(C.byref(tree), seed, C.byref(desc), table, arr, len(arr), grad_table, st,
                                    len(streams)))
+
+
+def inpc_render_batch_persistent(tree: InpcOctree, seed: int, desc: InpcHashgridDesc, table: int, jobs, grad_table,
+                                 streams, front_ws: int, front_ws_bytes: int, max_wait_us: int):
+    arr = jobs if isinstance(jobs, C.Array) else (InpcViewJob * len(jobs))(*jobs)
+    st = (_P * len(streams))(*streams)
+    check(load().inpc_render_batch_persistent(C.byref(tree), seed, C.byref(desc), table, arr, len(arr), grad_table,
+                                              st, len(streams), front_ws, front_ws_bytes, max_wait_us))
+
+
+def inpc_sample_query_batch_workspace_size(n_leaves: int, n_views: int) -> int:
+    out = C.c_size_t(0)
+    check(load().inpc_sample_query_batch_workspace_size(n_leaves, n_views, C.byref(out)))
+    return int(out.value)
+
+
+def inpc_sample_query_batch(tree: InpcOctree, seed: int, desc: InpcHashgridDesc, table: int, views, max_wait_us: int,
+                            workspace: int, workspace_bytes: int, stream: int):
+    arr = views if isinstance(views, C.Array) else (InpcFrontView * len(views))(*views)
+    check(load().inpc_sample_query_batch(C.byref(tree), C.c_uint64(seed), C.byref(desc), table, arr, len(arr),
+                                         max_wait_us, workspace, workspace_bytes, stream))
+
+
+def inpc_set_fault(spec):
+    check(load().inpc_set_fault(spec.encode() if spec else None))

@@ -5,6 +5,10 @@ step.  Views are spread over several streams so that their kernels overlap
 octree, the grid table and one FP32 table gradient (accumulated with atomic
 adds).  Tile sizes come from the autotuner.
 
+With ``persistent=True`` the sampling and grid query of all views run first
+as one persistent work-queue launch (the leaf CDF built once for the batch),
+and only the rasterizer's forward and backward are spread over the streams.
+
 Every computation runs in ``libinpc.so``; this module only owns buffers,
 streams and the graph.
 """
@@ -19,7 +23,7 @@ from .autotune import tuned_tiles
 
 class ViewBatch:
     def __init__(self, centers, levels, weights, root_size, desc, table, cams, n_samples, d_images, seed=0,
-                 n_streams=4, bf16=False, tune=True):
+                 n_streams=4, bf16=False, tune=True, persistent=False, max_wait_us=2_000_000):
         self.dev = table.device
         self.tree = (centers, levels, weights, float(root_size))
         self.desc = desc
@@ -50,6 +54,14 @@ class ViewBatch:
         for d in self.views:
             d["ws_r"] = api.workspace(api.rasterize_bwd_hashgrid_workspace_size(d["cam"], d["opts"], desc, self.n),
                                       self.dev)
+        # persistent form: the sampling and query of every view in one
+        # work-queue launch (inpc_render_batch_persistent)
+        self.persistent = bool(persistent)
+        self.max_wait_us = int(max_wait_us)
+        self.front_ws = None
+        if self.persistent:
+            nv = min(len(self.cams), 64)
+            self.front_ws = api.workspace(B.inpc_sample_query_batch_workspace_size(levels.shape[0], nv), self.dev)
         self.graph = None
         self._job_array = None
 
@@ -84,9 +96,19 @@ class ViewBatch:
         if self._job_array is None:
             self._job_array = self._jobs()
         tree = B.InpcOctree(c.data_ptr(), l.data_ptr(), w.data_ptr(), rs, l.shape[0])
-        streams = [main.cuda_stream] + [s.cuda_stream for s in self.streams]
-        B.inpc_render_batch(tree, self.seed, self.desc, self.table.data_ptr(), self._job_array,
-                            self.grad_table.data_ptr(), streams)
+        # torch hands out streams from a fixed pool, so a batch created after
+        # many others may get one twice (or the current stream): pass each once
+        streams = [main.cuda_stream]
+        for st in self.streams:
+            if st.cuda_stream not in streams:
+                streams.append(st.cuda_stream)
+        if self.persistent:
+            B.inpc_render_batch_persistent(tree, self.seed, self.desc, self.table.data_ptr(), self._job_array,
+                                           self.grad_table.data_ptr(), streams, self.front_ws.data_ptr(),
+                                           self.front_ws.numel(), self.max_wait_us)
+        else:
+            B.inpc_render_batch(tree, self.seed, self.desc, self.table.data_ptr(), self._job_array,
+                                self.grad_table.data_ptr(), streams)
 
     def run_eager(self):
         """One pass without the graph (also creates the library's side streams)."""

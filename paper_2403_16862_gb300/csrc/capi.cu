@@ -95,7 +95,14 @@ extern "C" const char* inpc_version(void) { return "inpc-gb300 0.1 (sm_103a)"; }
 extern "C" uint64_t inpc_kernel_launches(void) { return inpc::g_launches.load(); }
 
 extern "C" inpc_status inpc_read_device_status(const void* workspace, inpc_stream_t stream, uint32_t* status_out) {
-  if (!workspace || !status_out) return inpc::fail(INPC_ERR_INVALID_ARG, "inpc_read_device_status: null pointer");
+  if (!status_out) return inpc::fail(INPC_ERR_INVALID_ARG, "inpc_read_device_status: status_out is null");
+  if (!workspace) {
+    // the allocation-free sampler's status word: the first word of its static
+    // scratch array on the current device
+    void* p = nullptr;
+    INPC_TRY(inpc::noalloc_scratch_address(&p));
+    workspace = p;
+  }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   uint32_t v = 0;
   INPC_CUDA(cudaMemcpyAsync(&v, workspace, sizeof(v), cudaMemcpyDeviceToHost, s), "read status");

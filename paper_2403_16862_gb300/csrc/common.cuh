@@ -196,4 +196,18 @@ __host__ __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) { ret
 
 int device_sm_count();
 
+// Host-side fault injection (faults.cu, inpc_set_fault): size queries that
+// report an overflow, and a first array argument corrupted to NULL at the
+// entry of every compute call, which the call's own validation must catch.
+bool fault_workspace_overflow();
+bool fault_corrupt_args();
+template <class T>
+inline void fault_arg(T*& p) {
+  if (fault_corrupt_args()) p = nullptr;
+}
+
+// Device address of the allocation-free sampler's static scratch array on the
+// current device (sample_static.cu); its first word is that sampler's status.
+inpc_status noalloc_scratch_address(void** out);
+
 }  // namespace inpc

@@ -48,30 +48,8 @@ __global__ void __launch_bounds__(256) k_hash_fwd(GridParams P, const TT* __rest
     const uint32_t item = (valid ? i : total - 1) >> 1;  // spare lanes redo the last item
     const uint32_t p = item / (uint32_t)gl;
     const int l = l0 + (int)(item - p * gl);
-    uint32_t cx, cy, cz;
-    float gx[2], gy[2], gz[2];
-    const int N = P.res[l];
-    cell_frac(__ldg(pos + 3 * p + 0), N, cx, gx[0], gx[1]);
-    cell_frac(__ldg(pos + 3 * p + 1), N, cy, gy[0], gy[1]);
-    cell_frac(__ldg(pos + 3 * p + 2), N, cz, gz[0], gz[1]);
-    const TT* tab = table + 4 * P.offset[l];
-    const float wx = bx ? gx[1] : gx[0];
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int yz = 0; yz < 4; ++yz) {
-      const int by = yz & 1, bz = yz >> 1;
-      const float4 t = load_row<TT>(tab, vertex_row(P, l, cx + bx, cy + by, cz + bz), keep);
-      const float w = wx * (gy[by] * gz[bz]);
-      acc.x = fmaf(w, t.x, acc.x);
-      acc.y = fmaf(w, t.y, acc.y);
-      acc.z = fmaf(w, t.z, acc.z);
-      acc.w = fmaf(w, t.w, acc.w);
-    }
-    // lane 0 keeps features 0-1, lane 1 features 2-3
-    const float s0 = bx ? acc.x : acc.z, s1 = bx ? acc.y : acc.w;
-    const float r0 = __shfl_xor_sync(0xffffffffu, s0, 1), r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
-    const float2 mine = bx ? make_float2(acc.z + r0, acc.w + r1) : make_float2(acc.x + r0, acc.y + r1);
-    if (valid) store_half<OT>(h, (long long)p * P.n_levels + l, bx, mine);
+    query_pair<TT, OT>(P, table, __ldg(pos + 3 * p + 0), __ldg(pos + 3 * p + 1), __ldg(pos + 3 * p + 2), p, l, bx,
+                       valid, h, keep);
   }
 }
 
@@ -127,6 +105,7 @@ extern "C" inpc_status inpc_hashgrid_n_entries(const inpc_hashgrid_desc* g, int6
 
 extern "C" inpc_status inpc_query_hashgrid(const inpc_hashgrid_desc* g, const void* table, const float* pos,
                                            int64_t n, void* h_out, inpc_stream_t stream) {
+  inpc::fault_arg(table);
   GridParams P;
   int64_t total = 0;
   INPC_TRY(make_params(g, P, &total));
@@ -153,6 +132,7 @@ extern "C" inpc_status inpc_query_hashgrid(const inpc_hashgrid_desc* g, const vo
 
 extern "C" inpc_status inpc_query_hashgrid_bwd(const inpc_hashgrid_desc* g, const float* pos, const float* dh,
                                                int64_t n, float* grad_table, inpc_stream_t stream) {
+  inpc::fault_arg(pos);
   GridParams P;
   int64_t total = 0;
   INPC_TRY(make_params(g, P, &total));

@@ -158,6 +158,41 @@ __device__ __forceinline__ void store_half<__nv_bfloat16>(__nv_bfloat16* __restr
   __stcs(reinterpret_cast<unsigned int*>(out) + 2 * idx4 + half, *reinterpret_cast<unsigned int*>(&a));
 }
 
+// One lane of the query's lane pair for (point p, level l): lane bx
+// gathers the four corners at x + bx of the point's cell and weights them;
+// the pair adds its partial sums with one exchange (a warp shuffle, so the
+// whole warp calls this together) and each lane stores half of the level's
+// four features (valid lanes only).
+template <class TT, class OT>
+__device__ __forceinline__ void query_pair(const GridParams& P, const TT* __restrict__ table, float x, float y,
+                                           float z, uint32_t p, int l, uint32_t bx, bool valid, OT* __restrict__ h,
+                                           uint64_t keep) {
+  uint32_t cx, cy, cz;
+  float gx[2], gy[2], gz[2];
+  const int N = P.res[l];
+  cell_frac(x, N, cx, gx[0], gx[1]);
+  cell_frac(y, N, cy, gy[0], gy[1]);
+  cell_frac(z, N, cz, gz[0], gz[1]);
+  const TT* tab = table + 4 * P.offset[l];
+  const float wx = bx ? gx[1] : gx[0];
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int yz = 0; yz < 4; ++yz) {
+    const int by = yz & 1, bz = yz >> 1;
+    const float4 t = load_row<TT>(tab, vertex_row(P, l, cx + bx, cy + by, cz + bz), keep);
+    const float w = wx * (gy[by] * gz[bz]);
+    acc.x = fmaf(w, t.x, acc.x);
+    acc.y = fmaf(w, t.y, acc.y);
+    acc.z = fmaf(w, t.z, acc.z);
+    acc.w = fmaf(w, t.w, acc.w);
+  }
+  // lane 0 keeps features 0-1, lane 1 features 2-3
+  const float s0 = bx ? acc.x : acc.z, s1 = bx ? acc.y : acc.w;
+  const float r0 = __shfl_xor_sync(0xffffffffu, s0, 1), r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+  const float2 mine = bx ? make_float2(acc.z + r0, acc.w + r1) : make_float2(acc.x + r0, acc.y + r1);
+  if (valid) store_half<OT>(h, (long long)p * P.n_levels + l, bx, mine);
+}
+
 __device__ __forceinline__ void red_add_v4(float* addr, float4 v) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
                : "memory");

@@ -137,6 +137,7 @@ using namespace inpc;
 
 extern "C" inpc_status inpc_contract_positions(const float* pos, int64_t n, const float* center, float radius,
                                                float* out, inpc_stream_t stream) {
+  inpc::fault_arg(pos);
   if (n < 0) return fail(INPC_ERR_INVALID_ARG, "n < 0");
   if (n == 0) return INPC_OK;
   if (!pos || !center || !out) return fail(INPC_ERR_INVALID_ARG, "null pointer");
@@ -149,6 +150,7 @@ extern "C" inpc_status inpc_contract_positions(const float* pos, int64_t n, cons
 extern "C" inpc_status inpc_sh_head_fwd(const inpc_camera* cam, const float* pos, const void* h, int32_t h_dtype,
                                         int64_t n, int32_t n_channels, float* alpha_out, float* color_out,
                                         inpc_stream_t stream) {
+  inpc::fault_arg(pos);
   INPC_TRY(check_head(cam, pos, h, h_dtype, n, n_channels));
   if (n == 0) return INPC_OK;
   if (!alpha_out || !color_out || !aligned(color_out, 16)) return fail(INPC_ERR_INVALID_ARG, "bad output pointer");
@@ -166,6 +168,7 @@ extern "C" inpc_status inpc_sh_head_fwd(const inpc_camera* cam, const float* pos
 extern "C" inpc_status inpc_sh_head_bwd(const inpc_camera* cam, const float* pos, const void* h, int32_t h_dtype,
                                         int64_t n, int32_t n_channels, const float* d_alpha, const float* d_color,
                                         float* dh_out, inpc_stream_t stream) {
+  inpc::fault_arg(pos);
   INPC_TRY(check_head(cam, pos, h, h_dtype, n, n_channels));
   if (n == 0) return INPC_OK;
   if (!d_alpha || !d_color || !dh_out || !aligned(d_color, 16)) return fail(INPC_ERR_INVALID_ARG, "bad pointer");

@@ -265,6 +265,7 @@ extern "C" inpc_status inpc_rasterize_point_weights(const inpc_camera* cam, cons
                                                     const float* pos, int64_t n, const int32_t* n_contrib,
                                                     float* b_out, void* workspace, size_t workspace_bytes,
                                                     inpc_stream_t stream) {
+  inpc::fault_arg(pos);
   RP P;
   INPC_TRY(make_rp(cam, opts, n, P));
   const RasterWs need = carve(nullptr, P.n_pix, n);
@@ -286,6 +287,8 @@ extern "C" inpc_status inpc_rasterize_point_weights(const inpc_camera* cam, cons
 }
 
 extern "C" inpc_status inpc_octree_update_workspace_size(int64_t n_leaves, size_t* bytes) {
+  if (inpc::fault_workspace_overflow())
+    return inpc::fail(INPC_ERR_CAPACITY, "inpc_octree_update_workspace_size: size overflow (injected fault)");
   if (!bytes) return fail(INPC_ERR_INVALID_ARG, "bytes is null");
   if (n_leaves < 1 || n_leaves > (int64_t(1) << 24)) return fail(INPC_ERR_INVALID_ARG, "n_leaves must be in [1, 2^24]");
   *bytes = carve_update(nullptr, n_leaves).bytes;
@@ -295,6 +298,7 @@ extern "C" inpc_status inpc_octree_update_workspace_size(int64_t n_leaves, size_
 extern "C" inpc_status inpc_octree_update(const int32_t* leaf_idx, const float* b, int64_t n, double* p, double* q,
                                           int64_t n_leaves, double lambda_u, void* workspace,
                                           size_t workspace_bytes, inpc_stream_t stream) {
+  inpc::fault_arg(leaf_idx);
   if (n_leaves < 1 || n_leaves > (int64_t(1) << 24)) return fail(INPC_ERR_INVALID_ARG, "n_leaves must be in [1, 2^24]");
   if (n < 0 || n > INT32_MAX) return fail(INPC_ERR_CAPACITY, "n must be in [0, 2^31 - 1]");
   if (!p || !q || (n > 0 && (!leaf_idx || !b))) return fail(INPC_ERR_INVALID_ARG, "null pointer");
@@ -316,6 +320,8 @@ extern "C" inpc_status inpc_octree_update(const int32_t* leaf_idx, const float* 
 }
 
 extern "C" inpc_status inpc_octree_refine_workspace_size(int64_t n_leaves, size_t* bytes) {
+  if (inpc::fault_workspace_overflow())
+    return inpc::fail(INPC_ERR_CAPACITY, "inpc_octree_refine_workspace_size: size overflow (injected fault)");
   if (!bytes) return fail(INPC_ERR_INVALID_ARG, "bytes is null");
   if (n_leaves < 1 || n_leaves > (int64_t(1) << 24)) return fail(INPC_ERR_INVALID_ARG, "n_leaves must be in [1, 2^24]");
   *bytes = carve_refine(nullptr, n_leaves).bytes;
@@ -326,6 +332,7 @@ extern "C" inpc_status inpc_octree_subdivide(const inpc_octree* tree, const doub
                                              int64_t max_leaves, float* centers_out, int32_t* levels_out,
                                              double* p_out, double* q_out, int64_t out_capacity, int64_t* n_out,
                                              void* workspace, size_t workspace_bytes, inpc_stream_t stream) {
+  inpc::fault_arg(tree);
   INPC_TRY(check_tree(tree, q));
   const LeafOut out{centers_out, levels_out, p_out, q_out};
   INPC_TRY(check_out(out));
@@ -353,6 +360,7 @@ extern "C" inpc_status inpc_octree_prune(const inpc_octree* tree, const double* 
                                          int32_t* levels_out, double* p_out, double* q_out, int64_t out_capacity,
                                          int64_t* n_out, void* workspace, size_t workspace_bytes,
                                          inpc_stream_t stream) {
+  inpc::fault_arg(tree);
   INPC_TRY(check_tree(tree, q));
   const LeafOut out{centers_out, levels_out, p_out, q_out};
   INPC_TRY(check_out(out));

@@ -256,6 +256,7 @@ extern "C" inpc_status inpc_rasterize_bwd(const inpc_camera* cam, const inpc_ras
                                           const int32_t* n_contrib, const float* d_image, float* d_opacity,
                                           float* d_feat, void* workspace, size_t workspace_bytes,
                                           inpc_stream_t stream) {
+  inpc::fault_arg(pos);
   RP P;
   INPC_TRY(make_rp(cam, opts, n, P));
   const RasterWs need = carve(nullptr, P.n_pix, n);
@@ -288,6 +289,7 @@ extern "C" inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const
                                                    int64_t n, const float* T_final, const int32_t* n_contrib,
                                                    const float* d_image, float* grad_table, float* d_feat,
                                                    void* workspace, size_t workspace_bytes, inpc_stream_t stream) {
+  inpc::fault_arg(pos);
   RP P;
   INPC_TRY(make_rp(cam, opts, n, P));
   GridParams Gp;
@@ -335,6 +337,8 @@ extern "C" inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const
 extern "C" inpc_status inpc_rasterize_bwd_hashgrid_workspace_size(const inpc_camera* cam, const inpc_raster_opts* opts,
                                                                   const inpc_hashgrid_desc* grid, int64_t n,
                                                                   size_t* bytes) {
+  if (inpc::fault_workspace_overflow())
+    return inpc::fail(INPC_ERR_CAPACITY, "inpc_rasterize_bwd_hashgrid_workspace_size: size overflow (injected fault)");
   if (!bytes) return fail(INPC_ERR_INVALID_ARG, "bytes is null");
   RP P;
   INPC_TRY(make_rp(cam, opts, n, P));

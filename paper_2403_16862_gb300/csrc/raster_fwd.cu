@@ -5,6 +5,8 @@ using namespace inpc;
 
 extern "C" inpc_status inpc_rasterize_workspace_size(const inpc_camera* cam, const inpc_raster_opts* opts, int64_t n,
                                                      size_t* bytes) {
+  if (inpc::fault_workspace_overflow())
+    return inpc::fail(INPC_ERR_CAPACITY, "inpc_rasterize_workspace_size: size overflow (injected fault)");
   if (!bytes) return fail(INPC_ERR_INVALID_ARG, "bytes is null");
   RP P;
   INPC_TRY(make_rp(cam, opts, n, P, kMaxFwdPoints));
@@ -16,6 +18,7 @@ extern "C" inpc_status inpc_rasterize_fwd(const inpc_camera* cam, const inpc_ras
                                           const float* opacity, const void* feat, int64_t n, void* image,
                                           float* T_final, int32_t* n_contrib, void* workspace,
                                           size_t workspace_bytes, inpc_stream_t stream) {
+  inpc::fault_arg(pos);
   RP P;
   INPC_TRY(make_rp(cam, opts, n, P, kMaxFwdPoints));
   const RasterWs need = carve(nullptr, P.n_pix, n);

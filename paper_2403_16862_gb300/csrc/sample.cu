@@ -16,19 +16,10 @@
 
 #include <cuda_bf16.h>
 
-#include "common.cuh"
+#include "sample_impl.cuh"
 
 namespace inpc {
 namespace {
-
-constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
-constexpr int kScanBlock = kScanThreads * kScanItems;  // 2048 items per CTA
-constexpr int kCoarse = 2048;                          // coarse search table entries (shared memory)
-constexpr int kDrawThreads = 256;
-constexpr int kDrawPerThread = 16;
-constexpr int kDrawPerCta = kDrawThreads * kDrawPerThread;
-constexpr int kSmemLeaves = 4096;  // trees up to this many leaves count their draws in shared memory
 
 struct SampleWs {
   uint32_t* status;          // header word 0
@@ -41,14 +32,6 @@ struct SampleWs {
   uint32_t* guide;           // [2^guide_log2(L) + 1]
   size_t bytes;
 };
-
-// Draw buckets: the top guide_log2(L) bits of a draw's 53-bit random number
-// (about two leaves per bucket).
-int guide_log2(int64_t L) {
-  int f = 0;
-  while ((int64_t(1) << (f + 1)) <= L) ++f;  // floor(log2 L)
-  return f > 0 ? f - 1 : 0;
-}
 
 SampleWs carve(void* base, int64_t L) {
   Carver c(base);
@@ -84,11 +67,7 @@ struct QuantLoad {
   const double* w;
   const unsigned long long* wmax;
   __device__ double operator()(int64_t i) const {
-    const double m = __longlong_as_double((long long)*wmax);
-    if (!(m > 0.0)) return 0.0;
-    const double x = w[i];
-    if (!(x >= 0.0) || isinf(x)) return 0.0;
-    return rint(ldexp(__ddiv_rn(x, m), 29));
+    return quantised_weight(w[i], __longlong_as_double((long long)*wmax));
   }
 };
 
@@ -181,81 +160,12 @@ inpc_status scan(Load ld, int64_t L, T* out, T* tops, cudaStream_t s) {
   return check_launch("sample scan", nb > 1 ? 3 : 2);
 }
 
-// Two-level search tables: the last element of every stride-sized block
-// sits in shared memory, the rest is searched in global memory (L2).
-template <class T>
-__device__ __forceinline__ void load_coarse(const T* __restrict__ arr, int64_t L, int stride_log2, T* coarse,
-                                            int& n_coarse) {
-  n_coarse = (int)ceil_div(L, (int64_t)1 << stride_log2);
-  for (int j = threadIdx.x; j < n_coarse; j += blockDim.x) {
-    int64_t e = (((int64_t)j + 1) << stride_log2) - 1;
-    coarse[j] = arr[e < L ? e : L - 1];
-  }
-  __syncthreads();
-}
-
-// Order key of a searched value.  The CDF holds exact non-negative integers
-// as doubles, and non-negative doubles order like their IEEE-754 bit
-// patterns read as unsigned integers, so the searches compare 64-bit
-// integers (the same decisions, without the narrow FP64 pipe).
-__device__ __forceinline__ uint64_t ord(double x) { return (uint64_t)__double_as_longlong(x); }
-__device__ __forceinline__ uint32_t ord(uint32_t x) { return x; }
-
-// Smallest i with arr[i] > key (arr non-decreasing, non-negative); L when none.
-template <class T>
-__device__ __forceinline__ int64_t upper_bound2(const T* __restrict__ arr, int64_t L, const T* coarse, int n_coarse,
-                                                int stride_log2, T key_value) {
-  const auto key = ord(key_value);
-  int lo = 0, hi = n_coarse;  // first coarse block whose last element exceeds key
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (ord(coarse[mid]) > key) hi = mid; else lo = mid + 1;
-  }
-  if (lo == n_coarse) return L;
-  int64_t a = (int64_t)lo << stride_log2;
-  int64_t b = a + ((int64_t)1 << stride_log2) - 1;
-  if (b > L - 1) b = L - 1;
-  while (a < b) {  // arr[b] > key holds
-    const int64_t mid = (a + b) >> 1;
-    if (ord(arr[mid]) > key) b = mid; else a = mid + 1;
-  }
-  return a;
-}
-
-// Guide table (an indexed search): a draw's value r = floor(b Q / 2^53)
-// from the 53-bit random b lies, for b in bucket j = b >> (53 - G_l), in
-// [floor(j Q / 2^G_l), floor((j + 1) Q / 2^G_l)], and the leaf of r (the
-// smallest i with cdf[i] > r) is monotone in r, so guide[j] = the leaf of
-// floor(j Q / 2^G_l) and guide[j + 1] bound it.  The bucket bounds are
-// formed exactly from the 128-bit product j Q.
+// First leaf of every bucket of draw values (guide_entry).
 __global__ void k_guide(const double* __restrict__ cdf, int64_t L, int Gl, uint32_t* __restrict__ guide) {
   const uint64_t Q = (uint64_t)cdf[L - 1];
   const int64_t G = int64_t(1) << Gl;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= G; j += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t pl = (uint64_t)j * Q, ph = __umul64hi((uint64_t)j, Q);
-    const uint64_t lo = Gl == 0 ? pl : ((ph << (64 - Gl)) | (pl >> Gl));
-    const uint64_t key = ord((double)lo);  // lo <= Q <= 2^53: exact
-    int64_t a = 0, z = L;                  // smallest i with cdf[i] > lo; L when none
-    while (a < z) {
-      const int64_t mid = (a + z) >> 1;
-      if (ord(cdf[mid]) > key) z = mid; else a = mid + 1;
-    }
-    guide[j] = (uint32_t)a;
-  }
-}
-
-// Leaf of a draw: the smallest i with cdf[i] > r (key = the bits of r as a
-// double), searched between the guide entries of the draw's bucket j.
-// Returns L only when Q == 0 (flagged as a device status).
-__device__ __forceinline__ int64_t guided_leaf(const double* __restrict__ cdf, int64_t L,
-                                               const uint32_t* __restrict__ guide, uint32_t j, uint64_t key) {
-  int64_t a = guide[j], z = guide[j + 1];
-  if (z > L - 1) z = L - 1;
-  while (a < z) {  // cdf[z] > r holds
-    const int64_t mid = (a + z) >> 1;
-    if (ord(cdf[mid]) > key) z = mid; else a = mid + 1;
-  }
-  return a;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= G; j += (int64_t)gridDim.x * blockDim.x)
+    guide[j] = guide_entry(LdPlain(), cdf, L, Gl, Q, j);
 }
 
 // Draws land on leaves at random, so a CTA's draws only repeat leaves when
@@ -272,24 +182,13 @@ __global__ void __launch_bounds__(kDrawThreads) k_draw_count(const double* __res
     for (int j = threadIdx.x; j < L; j += blockDim.x) vals[j] = 0;
     __syncthreads();
   }
-  const double Q = cdf[L - 1];
-  const uint64_t Qi = (uint64_t)Q;
+  const uint64_t Qi = (uint64_t)cdf[L - 1];
   const int64_t base = (int64_t)blockIdx.x * kDrawPerCta;
   const int lane = threadIdx.x & 31;
   for (int k = 0; k < kDrawPerThread; ++k) {
     const int64_t s = base + (int64_t)k * kDrawThreads + threadIdx.x;
     int leaf = -1;
-    if (s < n_draws) {
-      const U32x4 r = philox4x32_10((uint32_t)s, (uint32_t)((uint64_t)s >> 32), view_id, 0u, k0, k1);
-      const uint64_t b = ((uint64_t)(r.y & 0x1FFFFFu) << 32) | (uint64_t)r.x;
-      // floor(b * Q / 2^53) from the exact 106-bit product
-      const uint64_t lo = b * Qi;
-      const uint64_t hi = __umul64hi(b, Qi);
-      const uint64_t rr = (hi << 11) | (lo >> 53);
-      int64_t i = guided_leaf(cdf, L, guide, (uint32_t)(b >> (53 - Gl)), ord((double)rr));
-      if (i >= L) i = L - 1;  // only reachable when Q == 0 (flagged as a device status)
-      leaf = (int)i;
-    }
+    if (s < n_draws) leaf = (int)draw_leaf(LdPlain(), cdf, L, guide, Gl, Qi, s, view_id, k0, k1);
     const unsigned peers = __match_any_sync(0xffffffffu, leaf);
     if (leaf >= 0 && lane == __ffs(peers) - 1) {
       if (kSmem) atomicAdd(&vals[leaf], (uint32_t)__popc(peers));
@@ -310,20 +209,12 @@ __global__ void __launch_bounds__(256) k_place(const uint32_t* __restrict__ star
                                                int32_t* __restrict__ leaf_out, float* __restrict__ pos_out) {
   __shared__ uint32_t coarse[kCoarse];
   int n_coarse;
-  load_coarse<uint32_t>(starts, L, stride_log2, coarse, n_coarse);
+  load_coarse(LdPlain(), starts, L, stride_log2, coarse, n_coarse);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     // leaf = (number of leaves whose first slot is <= k) - 1
-    int64_t leaf = upper_bound2<uint32_t>(starts, L, coarse, n_coarse, stride_log2, (uint32_t)k) - 1;
+    int64_t leaf = upper_bound2<uint32_t>(LdPlain(), starts, L, coarse, n_coarse, stride_log2, (uint32_t)k) - 1;
     if (leaf < 0) leaf = 0;
-    const U32x4 r = philox4x32_10((uint32_t)k, (uint32_t)((uint64_t)k >> 32), view_id, 1u, k0, k1);
-    const float edge = ldexpf(root_size, -levels[leaf]);
-    const float u0 = __fsub_rn((float)(r.x >> 8) * 0x1p-24f, 0.5f);
-    const float u1 = __fsub_rn((float)(r.y >> 8) * 0x1p-24f, 0.5f);
-    const float u2 = __fsub_rn((float)(r.z >> 8) * 0x1p-24f, 0.5f);
-    leaf_out[k] = (int32_t)leaf;
-    pos_out[3 * k + 0] = __fmaf_rn(u0, edge, centers[3 * leaf + 0]);
-    pos_out[3 * k + 1] = __fmaf_rn(u1, edge, centers[3 * leaf + 1]);
-    pos_out[3 * k + 2] = __fmaf_rn(u2, edge, centers[3 * leaf + 2]);
+    place_slot(k, leaf, view_id, k0, k1, centers, levels, root_size, leaf_out, pos_out);
   }
 }
 
@@ -409,16 +300,10 @@ __global__ void k_resample_round(const double* __restrict__ cdf, int64_t L, cons
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     if (in_view(cam, pos_out + 3 * k)) continue;
     const U32x4 r = philox4x32_10((uint32_t)k, (uint32_t)((uint64_t)k >> 32), view_id, 2u + 2u * round, k0, k1);
-    const uint64_t b = ((uint64_t)(r.y & 0x1FFFFFu) << 32) | (uint64_t)r.x;
-    const uint64_t lo = b * Qi, hi = __umul64hi(b, Qi);
-    int64_t leaf = guided_leaf(cdf, L, guide, (uint32_t)(b >> (53 - Gl)), ord((double)((hi << 11) | (lo >> 53))));
-    if (leaf >= L) leaf = L - 1;
+    const int64_t leaf = leaf_of_words(LdPlain(), cdf, L, guide, Gl, Qi, r);
     const U32x4 r2 = philox4x32_10((uint32_t)k, (uint32_t)((uint64_t)k >> 32), view_id, 3u + 2u * round, k0, k1);
-    const float edge = ldexpf(root_size, -levels[leaf]);
     leaf_out[k] = (int32_t)leaf;
-    pos_out[3 * k + 0] = __fmaf_rn(__fsub_rn((float)(r2.x >> 8) * 0x1p-24f, 0.5f), edge, centers[3 * leaf + 0]);
-    pos_out[3 * k + 1] = __fmaf_rn(__fsub_rn((float)(r2.y >> 8) * 0x1p-24f, 0.5f), edge, centers[3 * leaf + 1]);
-    pos_out[3 * k + 2] = __fmaf_rn(__fsub_rn((float)(r2.z >> 8) * 0x1p-24f, 0.5f), edge, centers[3 * leaf + 2]);
+    leaf_position(r2, leaf, centers, levels, root_size, pos_out + 3 * k);
   }
 }
 
@@ -453,9 +338,9 @@ __global__ void __launch_bounds__(256) k_place_halton(const uint32_t* __restrict
                                                       int32_t* __restrict__ leaf_out, float* __restrict__ pos_out) {
   __shared__ uint32_t coarse[kCoarse];
   int n_coarse;
-  load_coarse<uint32_t>(starts, L, stride_log2, coarse, n_coarse);
+  load_coarse(LdPlain(), starts, L, stride_log2, coarse, n_coarse);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    int64_t leaf = upper_bound2<uint32_t>(starts, L, coarse, n_coarse, stride_log2, (uint32_t)k) - 1;
+    int64_t leaf = upper_bound2<uint32_t>(LdPlain(), starts, L, coarse, n_coarse, stride_log2, (uint32_t)k) - 1;
     if (leaf < 0) leaf = 0;
     const uint64_t j = (uint64_t)(k - (int64_t)starts[leaf]) + 1;
     const double edge = ldexp((double)root_size, -levels[leaf]);
@@ -483,11 +368,6 @@ __global__ void k_accumulate(const T* __restrict__ img, float* __restrict__ acc,
     acc[i] = __fmaf_rn(scale, (float)img[i], acc[i]);
 }
 
-int coarse_stride_log2(int64_t L) {
-  int s = 0;
-  while (ceil_div(L, (int64_t)1 << s) > kCoarse) ++s;
-  return s;
-}
 
 }  // namespace
 }  // namespace inpc
@@ -495,6 +375,8 @@ int coarse_stride_log2(int64_t L) {
 using namespace inpc;
 
 extern "C" inpc_status inpc_sample_workspace_size(int64_t n_leaves, int64_t n_samples, size_t* bytes) {
+  if (inpc::fault_workspace_overflow())
+    return inpc::fail(INPC_ERR_CAPACITY, "inpc_sample_workspace_size: size overflow (injected fault)");
   if (!bytes) return fail(INPC_ERR_INVALID_ARG, "inpc_sample_workspace_size: bytes is null");
   if (n_leaves < 1 || n_leaves > (int64_t(1) << 24))
     return fail(INPC_ERR_CAPACITY, "n_leaves must be in [1, 2^24], got %lld", (long long)n_leaves);
@@ -515,6 +397,7 @@ extern "C" inpc_status inpc_sample_octree(const inpc_octree* tree, uint64_t seed
                                           int64_t n_samples, int32_t* leaf_idx_out, float* pos_out,
                                           int32_t* leaf_counts_out, void* workspace, size_t workspace_bytes,
                                           inpc_stream_t stream) {
+  inpc::fault_arg(tree);
   return sample_impl(tree, seed, view_id, n_samples, leaf_idx_out, pos_out, leaf_counts_out, workspace,
                      workspace_bytes, stream, false);
 }
@@ -522,12 +405,14 @@ extern "C" inpc_status inpc_sample_octree(const inpc_octree* tree, uint64_t seed
 extern "C" inpc_status inpc_sample_octree_halton(const inpc_octree* tree, uint64_t seed, int64_t n_samples,
                                                  int32_t* leaf_idx_out, float* pos_out, int32_t* leaf_counts_out,
                                                  void* workspace, size_t workspace_bytes, inpc_stream_t stream) {
+  inpc::fault_arg(tree);
   return sample_impl(tree, seed, 0u, n_samples, leaf_idx_out, pos_out, leaf_counts_out, workspace, workspace_bytes,
                      stream, true);
 }
 
 extern "C" inpc_status inpc_level_weights(const inpc_octree* tree, double lambda_l, double* w_out,
                                           inpc_stream_t stream) {
+  inpc::fault_arg(tree);
   if (!tree || !tree->levels || !tree->weights || !w_out) return fail(INPC_ERR_INVALID_ARG, "null pointer");
   if (tree->n_leaves < 1 || tree->n_leaves > (int64_t(1) << 24))
     return fail(INPC_ERR_INVALID_ARG, "n_leaves must be in [1, 2^24]");
@@ -541,8 +426,39 @@ extern "C" inpc_status inpc_level_weights(const inpc_octree* tree, double lambda
   return check_launch("k_level_weights");
 }
 
+namespace inpc {
+namespace {
+__global__ void k_philox(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ ctrs, int64_t n,
+                         uint32_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const U32x4 r = philox4x32_10(ctrs[4 * i], ctrs[4 * i + 1], ctrs[4 * i + 2], ctrs[4 * i + 3], keys[2 * i],
+                                  keys[2 * i + 1]);
+    out[4 * i] = r.x;
+    out[4 * i + 1] = r.y;
+    out[4 * i + 2] = r.z;
+    out[4 * i + 3] = r.w;
+  }
+}
+}  // namespace
+}  // namespace inpc
+
+extern "C" inpc_status inpc_philox4x32_10(const uint32_t* keys, const uint32_t* ctrs, int64_t n, uint32_t* out,
+                                          inpc_stream_t stream) {
+  inpc::fault_arg(keys);
+  if (n < 0) return fail(INPC_ERR_INVALID_ARG, "inpc_philox4x32_10: n < 0");
+  if (n == 0) return INPC_OK;
+  if (!keys || !ctrs || !out) return fail(INPC_ERR_INVALID_ARG, "inpc_philox4x32_10: null pointer");
+  if (!aligned(keys, 4) || !aligned(ctrs, 4) || !aligned(out, 4))
+    return fail(INPC_ERR_INVALID_ARG, "inpc_philox4x32_10: misaligned array");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t grid = std::min<int64_t>(ceil_div(n, 256), (int64_t)device_sm_count() * 8);
+  k_philox<<<(unsigned)grid, 256, 0, s>>>(keys, ctrs, n, out);
+  return check_launch("k_philox");
+}
+
 extern "C" inpc_status inpc_accumulate_image(const void* image, int32_t dtype, int64_t n_elems, float scale,
                                              float* acc, inpc_stream_t stream) {
+  inpc::fault_arg(image);
   if (n_elems < 0) return fail(INPC_ERR_INVALID_ARG, "n_elems < 0");
   if (n_elems == 0) return INPC_OK;
   if (!image || !acc) return fail(INPC_ERR_INVALID_ARG, "null pointer");
@@ -625,6 +541,7 @@ inpc_status sample_impl(const inpc_octree* tree, uint64_t seed, uint32_t view_id
 
 extern "C" inpc_status inpc_view_weights(const inpc_octree* tree, const inpc_camera* cam, double lambda_l,
                                          double tau_d, double* w_out, inpc_stream_t stream) {
+  inpc::fault_arg(tree);
   if (!tree || !cam || !w_out) return fail(INPC_ERR_INVALID_ARG, "inpc_view_weights: null pointer");
   if (!tree->centers || !tree->levels || !tree->weights)
     return fail(INPC_ERR_INVALID_ARG, "inpc_view_weights: null octree array");
@@ -648,6 +565,7 @@ extern "C" inpc_status inpc_sample_octree_view(const inpc_octree* tree, const in
                                                uint32_t view_id, int64_t n_samples, int32_t max_rounds,
                                                int32_t* leaf_idx_out, float* pos_out, uint32_t* n_left,
                                                void* workspace, size_t workspace_bytes, inpc_stream_t stream) {
+  inpc::fault_arg(tree);
   if (!cam) return fail(INPC_ERR_INVALID_ARG, "inpc_sample_octree_view: camera is null");
   if (max_rounds < 0 || max_rounds > 64) return fail(INPC_ERR_INVALID_ARG, "max_rounds must be in [0, 64]");
   if (!(cam->near_plane > 0.0f) || !(cam->far_plane > cam->near_plane) || cam->width < 1 || cam->height < 1)

@@ -131,3 +131,17 @@ def test_render_batch_argument_errors(B):
         B.inpc_render_batch(tree, 0, desc, 1, [given], 1, [1])
     assert e.value.status == B.INPC_ERR_INVALID_ARG and "head mode" in str(e.value)
     B.inpc_render_batch(tree, 0, desc, 1, [], 1, [1])  # an empty batch is a no-op
+
+
+def test_binding_constants_match_the_header(B):
+    # the Python constants mirror the header's macros and enum values
+    src = open(os.path.join(ROOT, "include", "inpc.h")).read()
+    m = re.search(r"#define INPC_SAMPLE_STATIC_SCRATCH_BYTES \(\((\d+)u << 20\) \+ \((\d+)u << 10\)\)", src)
+    assert m and B.INPC_SAMPLE_STATIC_SCRATCH_BYTES == (int(m.group(1)) << 20) + (int(m.group(2)) << 10)
+    for name in ("INPC_DEV_BAD_WEIGHT", "INPC_DEV_NO_WEIGHT", "INPC_DEV_BAD_LEAF", "INPC_DEV_BAD_BLEND_WEIGHT"):
+        v = re.search(r"#define %s (0x[0-9a-fA-F]+)u" % name, src)
+        assert v and getattr(B, name) == int(v.group(1), 16), name
+    for name in ("INPC_ERR_INVALID_ARG", "INPC_ERR_CUDA", "INPC_ERR_CAPACITY", "INPC_ERR_TIMEOUT",
+                 "INPC_ERR_UNSUPPORTED"):
+        v = re.search(r"%s = (\d+)" % name, src)
+        assert v and getattr(B, name) == int(v.group(1)), name

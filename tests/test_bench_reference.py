@@ -29,3 +29,13 @@ def test_reference_arm_json_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_loads_only_the_oracle():
+    # the reference arm sizes its table with the oracle's layout rule and
+    # maps no library of the GPU path
+    code = ("import sys, types, bench; a = types.SimpleNamespace(steps=1, warmup=0, gpus=1); "
+            "bench.run_reference(a, 0); maps = open('/proc/self/maps').read(); "
+            "sys.exit(3 if 'libinpc' in maps else (0 if 'liboracle' in maps else 4))")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, (r.returncode, r.stderr[-2000:])

@@ -22,7 +22,7 @@ import torch
 
 from paper_2403_16862_gb300 import api, scenes
 from paper_2403_16862_gb300.batch import ViewBatch
-from tests._parity import assert_cond_close
+from tests._parity import assert_cond_close, cond_ratio
 from tests.test_gpu_raster import _excluded_points, _product_widening
 
 pytestmark = pytest.mark.gpu
@@ -143,6 +143,9 @@ def test_precision_workload_full_size(gpu, oracle):
     assert_cond_close(r32["img"].cpu().numpy(), ref["image"], ref["abs"] * wp[..., None], mask=ok[..., None],
                       what="image")
     assert_cond_close(r32["T"].cpu().numpy(), ref["T_final"], ref["T_final"] * wp, mask=ok, what="T_final")
+    print("bound used without the long-blend widening: image %.3f, T_final %.3f"
+          % (cond_ratio(r32["img"].cpu().numpy(), ref["image"], ref["abs"], mask=ok[..., None]),
+             cond_ratio(r32["T"].cpu().numpy(), ref["T_final"], ref["T_final"], mask=ok)))
     e_img = _Err().add(r16["img"].float().cpu().numpy(), ref["image"], ref["abs"])
     e_T = _Err().add(r16["T"].cpu().numpy(), ref["T_final"], ref["T_final"])
     keep = ~_excluded_points(oracle, cam, o_pos, ref["flags"])

@@ -103,3 +103,23 @@ def test_query_table_alignments(gpu, oracle):
         t.copy_(torch.from_numpy(grid.table).to(gpu))
         h = api.query_hashgrid(desc, t, torch.from_numpy(pos).to(gpu))
         assert_cond_close(h.cpu().numpy(), ref, ab, what="h (shift %d)" % shift)
+
+
+def test_hashed_index_golden_on_device(gpu):
+    # the device query reads the row the hand-derived spatial hash names: a
+    # one-level grid (resolution 4096, T = 2^19, hashed) whose row r holds
+    # (r, r + 1/2, -r, 1), queried exactly on each golden vertex (weight 1 on
+    # that vertex, 0 on the other seven corners)
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hash_index.json")))
+    res, log2_T = [g["res"]], g["log2_T"]
+    n_ent = api.hashgrid_n_entries(res, log2_T)
+    r = np.arange(n_ent, dtype=np.float32)
+    table = np.stack([r, r + 0.5, -r, np.ones_like(r)], axis=1)
+    pos = np.array([c["v"] for c in g["cases"]], dtype=np.float32) / np.float32(g["res"])
+    desc = api.hashgrid_desc(res, log2_T)
+    h = api.query_hashgrid(desc, torch.from_numpy(table).to(gpu), torch.from_numpy(pos).to(gpu)).cpu().numpy()
+    for k, c in enumerate(g["cases"]):
+        i = c["index"]
+        assert h[k].tolist() == [float(i), i + 0.5, -float(i), 1.0], c

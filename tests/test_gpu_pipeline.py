@@ -10,7 +10,7 @@ import pytest
 import torch
 
 from paper_2403_16862_gb300 import api, scenes
-from tests._parity import assert_cond_close
+from tests._parity import assert_cond_close, cond_ratio
 from tests.test_gpu_raster import _excluded_points
 
 pytestmark = pytest.mark.gpu
@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 RES16 = scenes.geometric_resolutions(16, 16, 4096)
 
 
-def _pipeline(gpu, oracle, n_leaves, n_samples, log2_T, cam, seed=0, graph_check=False):
+def _pipeline(gpu, oracle, n_leaves, n_samples, log2_T, cam, seed=0, graph_check=False, margins=False):
     tree = scenes.make_octree(seed, n_leaves)
     grid = scenes.make_hashgrid(seed + 1, oracle.hash_entries(RES16, log2_T), RES16, log2_T)
     g_img = scenes.upstream_grad(seed + 2, (cam.height, cam.width, 64))
@@ -72,6 +72,24 @@ def _pipeline(gpu, oracle, n_leaves, n_samples, log2_T, cam, seed=0, graph_check
     print("pipeline: %d samples, %d fragments, max blended per pixel %d, flagged pixels %d"
           % (n_samples, int(ref["n_frags"].sum()), int(ref["n_contrib"].max()), int((~ok).sum())))
 
+    if margins:
+        # how much of the bound the outputs use under the plain scale: the
+        # rasterizer's sum T alpha |c| with the features' own magnitudes (not
+        # the query's sum |w t|), and the table gradient's scale from that
+        plain = oracle.raster_fwd(cam, o_pos, o_h, head_mode=True, with_abs=True)
+        rbp = oracle.raster_bwd(cam, o_pos, o_h, g_img, head_mode=True, with_abs=True)
+        _, o_gab_p = oracle.hash_bwd(RES16, log2_T, 4, o_pos, rb["d_feat"], with_abs=True, dh_abs=rbp["abs_feat"])
+        used = {
+            "image": (cond_ratio(img.cpu().numpy(), ref["image"], ref["abs"], mask=ok[..., None]),
+                      cond_ratio(img.cpu().numpy(), ref["image"], plain["abs"], mask=ok[..., None])),
+            "dh": (cond_ratio(dh.cpu().numpy(), rb["d_feat"], rb["abs_feat"], mask=keep[:, None]),
+                   cond_ratio(dh.cpu().numpy(), rb["d_feat"], rbp["abs_feat"], mask=keep[:, None])),
+            "grad_table": (cond_ratio(gt_fused.cpu().numpy(), o_gt, o_gab, mask=reach == 0),
+                           cond_ratio(gt_fused.cpu().numpy(), o_gt, o_gab_p, mask=reach == 0)),
+        }
+        for k, (a, b) in used.items():
+            print("bound used, %-10s scale of the test %.3f   plain scale %.3f" % (k, a, b))
+
     if graph_check:
         # the same sequence captured in a CUDA graph replays identically
         s = torch.cuda.Stream()
@@ -101,7 +119,7 @@ def test_pipeline_small(gpu, oracle):
 def test_pipeline_full_size(gpu, oracle):
     """65,536 leaves, 4,194,304 samples, 2^19 grid, 1280x832, fwd + bwd."""
     cam = scenes.make_camera((0.5, 0.5, -1.2), 900, 900, 640, 416, 1280, 832)
-    _pipeline(gpu, oracle, 65536, 4_194_304, 19, cam, seed=0)
+    _pipeline(gpu, oracle, 65536, 4_194_304, 19, cam, seed=0, margins=True)
 
 
 @pytest.mark.parametrize("n_levels", [6, 8, 24, 32])

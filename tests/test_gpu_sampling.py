@@ -96,3 +96,46 @@ def test_stream_ordering_and_determinism(gpu):
     b = api.sample_octree(c, l, w, 1.0, 11, 2, 300_000)
     torch.cuda.synchronize()
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+def _kat_cases():
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.json")))
+    return [([int(x, 16) for x in c["key"]], [int(x, 16) for x in c["ctr"]], [int(x, 16) for x in c["out"]])
+            for c in g["cases"]]
+
+
+def _device_philox(keys, ctrs, dev):
+    # uint32 words carried in int64 on the host, int32 bit patterns on the device
+    k = torch.from_numpy(np.asarray(keys, np.uint32).view(np.int32)).to(dev)
+    c = torch.from_numpy(np.asarray(ctrs, np.uint32).view(np.int32)).to(dev)
+    out = torch.empty(len(keys), 4, dtype=torch.int32, device=dev)
+    B.inpc_philox4x32_10(k.data_ptr(), c.data_ptr(), len(keys), out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(np.uint32)
+
+
+def test_device_philox_known_answers(gpu):
+    # the device generator (the one the sampler's kernels call) against the
+    # published known-answer values of Philox4x32-10
+    cases = _kat_cases()
+    got = _device_philox([c[0] for c in cases], [c[1] for c in cases], gpu)
+    for k, (_, _, want) in enumerate(cases):
+        assert [int(x) for x in got[k]] == want
+
+
+def test_sampler_positions_are_the_device_generator_words(gpu):
+    # one level-0 leaf centred at 1/2, edge 1: position = (r_d >> 8) 2^-24 of
+    # Philox(key = seed, counter = (slot, 0, view, 1)), exactly in FP32
+    seed, view, n = 0x0123456789ABCDEF, 7, 4096 + 3
+    c = torch.tensor([[0.5, 0.5, 0.5]], dtype=torch.float32, device=gpu)
+    l = torch.zeros(1, dtype=torch.int32, device=gpu)
+    w = torch.ones(1, dtype=torch.float64, device=gpu)
+    leaf, pos = api.sample_octree(c, l, w, 1.0, seed, view, n)
+    keys = [[seed & 0xFFFFFFFF, seed >> 32]] * n
+    ctrs = [[k, 0, view, 1] for k in range(n)]
+    r = _device_philox(keys, ctrs, gpu).astype(np.int64)
+    want = ((r[:, :3] >> 8).astype(np.float64) * 2.0 ** -24).astype(np.float32)
+    assert np.array_equal(pos.cpu().numpy(), want)
+    assert int(leaf.abs().sum()) == 0

@@ -51,6 +51,27 @@ def _rank(rank, world, port, out_dir):
         err = np.abs(g.numpy().astype(np.float64) - total)
         assert np.all(err <= 1e-6 * (scale + 1e-30) + 1e-7 * np.abs(total).max())
         np.save(os.path.join(out_dir, "rank%d.npy" % rank), g.numpy())
+
+        # the overlapped exchange: each step's gradient accumulates into the
+        # table GradExchange hands out, its sum starts asynchronously, and
+        # the next step goes on; a table is summed before it is cleared and
+        # written again two steps later
+        gx = shard.GradExchange(mine.shape)
+        for step in range(3):
+            buf = gx.begin()
+            buf += torch.from_numpy(_grads(oracle, tree, ids[step][0]).astype(np.float32))
+            gx.launch()
+            if step >= 1:
+                prev = gx.result(step - 1).numpy().astype(np.float64)
+                want = sum(_grads(oracle, tree, shard.view_ids(r, world, step - 1)[0]) for r in range(world))
+                ab = sum(np.abs(_grads(oracle, tree, shard.view_ids(r, world, step - 1)[0])) for r in range(world))
+                assert np.all(np.abs(prev - want) <= 1e-6 * (ab + 1e-30) + 1e-7 * np.abs(want).max()), step
+        gx.finish()
+        last = gx.result(2).numpy().astype(np.float64)
+        want = sum(_grads(oracle, tree, shard.view_ids(r, world, 2)[0]) for r in range(world))
+        assert np.allclose(last, want, rtol=0, atol=1e-6 * np.abs(want).max())
+        with pytest.raises(ValueError):
+            gx.result(0)
     finally:
         dist.destroy_process_group()
 

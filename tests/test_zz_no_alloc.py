@@ -60,3 +60,27 @@ def test_noalloc_rejects_trees_beyond_the_static_array(gpu):
     with pytest.raises(B.InpcError) as e:
         _run("noalloc", tree, 0, 0, 10, gpu)
     assert e.value.status == B.INPC_ERR_CAPACITY and "static" in str(e.value)
+
+
+def test_noalloc_device_status_is_readable(gpu):
+    # the sampler's device status word is the first word of the static array;
+    # inpc_read_device_status with a null workspace reads it.  A NaN weight
+    # and an all-zero tree are flagged, the outputs stay inside the tree, and
+    # the next good call clears the word again.
+    octree = scenes.make_octree(3, 4096 + 7 * 100)
+    stream = torch.cuda.current_stream().cuda_stream
+    keep, tree = _tree_struct(octree, gpu)
+    _run("noalloc", tree, 0, 0, 10_000, gpu)
+    assert B.inpc_read_device_status(None, stream) == 0
+    w_bad = keep[2].clone()
+    w_bad[17] = float("nan")
+    bad = B.InpcOctree(keep[0].data_ptr(), keep[1].data_ptr(), w_bad.data_ptr(), octree.root_size, octree.n_leaves)
+    _run("noalloc", bad, 0, 0, 10_000, gpu)
+    assert B.inpc_read_device_status(None, stream) & B.INPC_DEV_BAD_WEIGHT
+    w_zero = torch.zeros_like(keep[2])
+    zero = B.InpcOctree(keep[0].data_ptr(), keep[1].data_ptr(), w_zero.data_ptr(), octree.root_size, octree.n_leaves)
+    leaf, _, _ = _run("noalloc", zero, 0, 0, 10_000, gpu)
+    assert B.inpc_read_device_status(None, stream) & B.INPC_DEV_NO_WEIGHT
+    assert leaf.min() >= 0 and leaf.max() < octree.n_leaves, "outputs stay in bounds"
+    _run("noalloc", tree, 0, 0, 10_000, gpu)
+    assert B.inpc_read_device_status(None, stream) == 0
