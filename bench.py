@@ -93,9 +93,16 @@ KERNELS = ["k_draw_count", "k_place", "k_hash_fwd", "k_pix_count", "k_pix_scatte
 # reported as null rather than as figures of another kernel.
 CAPTURED = {"k_point_grad_hash": {"traffic": 2_769_795_072 + 724_850_944, "l2_reductions": 243_212_179,
                                   "stamp": "62c2bd64da4be2de"}}
-# the sources each kernel's code comes from (stamped for CAPTURED)
+# the sources each kernel's code comes from (stamped for CAPTURED); "step":
+# every kernel of one view
 KERNEL_SOURCES = {"k_point_grad_hash": ["raster_bwd.cu", "raster_impl.cuh", "hashgrid_impl.cuh", "common.cuh"],
-                  "k_hash_fwd": ["hashgrid.cu", "hashgrid_impl.cuh", "common.cuh"]}
+                  "k_hash_fwd": ["hashgrid.cu", "hashgrid_impl.cuh", "common.cuh"],
+                  "step": ["sample.cu", "sample_impl.cuh", "scan.cuh", "hashgrid.cu", "hashgrid_impl.cuh",
+                           "raster_impl.cuh", "raster_fwd.cu", "raster_bwd.cu", "common.cuh"]}
+# DRAM bytes (read + write) of every kernel of one view on the full workload,
+# the library's kernels and the table-gradient clear, summed from one ncu
+# capture of all launches (mean of its 5 views); profiles/ holds the command
+STEP_CAPTURED = {"dram_bytes": 9_281_000_000, "stamp": "83027c8a435ad3b4"}
 
 
 def source_stamp(kernel):
@@ -428,6 +435,8 @@ def main():
     dom = max(kernel_ms, key=lambda k: kernel_ms[k][0])
     dom_ms = kernel_ms[dom][0] / max(kernel_ms[dom][1], 1)
     dom_bytes = kernel_bytes(dom, N, n_entries, 4 * N, H * W)
+    step_dram = STEP_CAPTURED["dram_bytes"] if (SCALE == 1 and not args.unfused
+                                                and STEP_CAPTURED["stamp"] == source_stamp("step")) else None
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_bytes else None
 
     e2e = None
@@ -460,7 +469,11 @@ def main():
                          "algorithmic_bytes": dom_bytes, **atomic_ceiling(dom, N, dom_ms)},
             "step_roofline": {"algorithmic_bytes": total_bytes,
                               "achieved_gbs": total_bytes / (ms_per_step * 1e-3) / 1e9,
-                              "frac": total_bytes / (ms_per_step * 1e-3) / 1e9 / peak},
+                              "frac": total_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
+                              "measured_dram_bytes": step_dram,
+                              "measured_dram_gbs": step_dram / (ms_per_step * 1e-3) / 1e9 if step_dram else None,
+                              "measured_from": "ncu dram__bytes_read.sum + dram__bytes_write.sum of every kernel of "
+                                               "one view, full workload, sources stamp %s" % source_stamp("step")},
             "gpu_launches": int(launches),
             "clocks": clocks,
             "e2e": e2e,

@@ -572,11 +572,12 @@ inpc_status inpc_sample_query_batch_workspace_size(int64_t n_leaves, int32_t n_v
 
 /* The sampling (Sec. 3.2, exactly inpc_sample_octree's definition) and the
  * grid query (Sec. 3.3, exactly inpc_query_hashgrid's) of n_views views of
- * one octree and one table, in ONE persistent kernel launch: CTAs take work
- * items (stage, view, tile) from a queue in the workspace, and an item that
- * depends on others waits for them.  The leaf CDF is built once for the
- * batch.  Outputs are bit-identical to inpc_sample_octree followed by
- * inpc_query_hashgrid for each view.
+ * one octree and one table in two launches: the sampling of every view in
+ * ONE persistent kernel, whose CTAs take work items (stage, view, tile) from
+ * a queue in the workspace and wait for the items an item depends on; then
+ * the query of every view in one more launch.  The leaf CDF is built once
+ * for the batch.  Outputs are bit-identical to inpc_sample_octree followed
+ * by inpc_query_hashgrid for each view.
  *   max_wait_us  bound of every wait, in microseconds of the GPU's global
  *                timer, in [1, 6e7]; a wait that runs out sets
  *                INPC_DEV_TIMEOUT in the workspace's status word (read with
@@ -592,9 +593,9 @@ inpc_status inpc_sample_query_batch(const inpc_octree* tree, uint64_t seed, cons
                                     int64_t max_wait_us, void* workspace, size_t workspace_bytes,
                                     inpc_stream_t stream);
 
-/* inpc_render_batch with the sampling and query of all views in the
- * persistent kernel of inpc_sample_query_batch (launches of up to 64 views
- * each, on streams[0], before the fork), then each view's rasterizer
+/* inpc_render_batch with the sampling and query of all views through
+ * inpc_sample_query_batch (up to 64 views per call, on streams[0], before
+ * the fork), then each view's rasterizer
  * forward and fused backward over the streams as in inpc_render_batch.  The
  * jobs' sample_ws are not used; front_workspace holds
  * inpc_sample_query_batch_workspace_size(n_leaves, min(n_views, 64)) bytes.

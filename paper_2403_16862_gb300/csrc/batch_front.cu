@@ -1,11 +1,12 @@
-// batch_front.cu -- the persistent front end of a batch of views: the
-// octree sampling (Sec. 3.2) and the grid query (Sec. 3.3) of every view of
-// a batch in ONE launch, driven by a work queue with bounded waits.
+// batch_front.cu -- the front end of a batch of views in two launches: the
+// octree sampling (Sec. 3.2) of every view in ONE persistent kernel driven
+// by a work queue with bounded waits, then the grid query (Sec. 3.3) of
+// every view in one more launch.
 //
 // The batch shares one octree and one table (the views differ in view id,
 // sample count and outputs), so the quantised CDF and the guide table are
-// built once for the batch, not once per view.  Work items, in the order of
-// their tickets:
+// built once for the batch, not once per view.  Work items of the
+// persistent kernel, in the order of their tickets:
 //   W  tiles of leaves: max weight (+ weight validation)
 //   C  tiles of 2048 leaves: quantised weights, exact prefix sum (single
 //      pass: each tile publishes its total, then looks back for the sum of
@@ -15,17 +16,20 @@
 //   S  per view, tiles of 2048 leaves: exclusive prefix sum of the counts
 //      (single pass, as C) -> first output slot of every leaf
 //   P  per view, tiles of slots: leaf of the slot, position in the leaf
-//   Q  per level pair, per view, tiles of points: the query of those two
-//      levels (levels go in pairs for L2 residency of the table rows)
 // CTAs take tickets from one atomic counter and run the item to completion;
 // an item waits only for items with smaller tickets (a stage's counter, or a
 // predecessor tile's published prefix), which CTAs that run have already
 // taken, so the queue always progresses.  Every wait gives up after
 // max_wait_ns of the GPU's global timer: it then sets INPC_DEV_TIMEOUT in the
 // status word and the abort flag, and every CTA returns at its next wait or
-// ticket.  The per-item arithmetic is that of the per-view kernels
-// (sample_impl.cuh, query_pair), so the outputs are bit-identical to
-// inpc_sample_octree + inpc_query_hashgrid of each view.
+// ticket.  The query launch then takes (level pair, view, tile of points)
+// items, level-pair major so that the table rows of a pair stay in L2 while
+// all views' points visit them; it has no waits (its inputs are complete
+// when it starts) and keeps the query's full occupancy, which the sampling
+// stages' registers would not allow in one kernel.  The per-item arithmetic
+// is that of the per-view kernels (sample_impl.cuh, query_pair), so the
+// outputs are bit-identical to inpc_sample_octree + inpc_query_hashgrid of
+// each view.
 #include <algorithm>
 #include <atomic>
 
@@ -48,7 +52,7 @@ constexpr int kPlaceTile = 16384;     // slots per place item
 constexpr int kQueryPoints = 1024;    // points per query item (one level pair)
 constexpr int kLevelPair = 2;
 
-enum : int { kStW = 0, kStC, kStG, kStD, kStS, kStP, kStQ, kStEnd };
+enum : int { kStW = 0, kStC, kStG, kStD, kStS, kStP, kStEnd };
 
 struct FrontView {
   uint32_t view_id;
@@ -234,9 +238,8 @@ __device__ __forceinline__ int upper_idx(const uint32_t* pre, int n, uint32_t x)
   return lo;
 }
 
-template <class TT, class OT>
 __global__ void __launch_bounds__(kFrontThreads) k_front(const __grid_constant__ FrontPlan pl, inpc_octree tree,
-                                                          GridParams G, const TT* __restrict__ table, FrontWs ws) {
+                                                          FrontWs ws) {
   __shared__ FrontSmem sm;
   const int tid = threadIdx.x;
   const int64_t L = pl.L;
@@ -352,7 +355,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_front(const __grid_constant__
         acc += c[k];
       }
       block_signal(ws.done + 4 + 3 * v);
-    } else if (st == kStP) {
+    } else {
       // ---- slots of view v: leaf and position
       const int v = upper_idx(pl.preP, pl.n_views + 1, r);
       const uint32_t tile = r - pl.preP[v];
@@ -368,33 +371,41 @@ __global__ void __launch_bounds__(kFrontThreads) k_front(const __grid_constant__
         place_slot(k, leaf, V.view_id, pl.k0, pl.k1, tree.centers, tree.levels, tree.root_size, V.leaf, V.pos);
       }
       block_signal(ws.done + 5 + 3 * v);
-    } else {
-      // ---- query of one level pair for a tile of view v's points
-      const uint32_t per_group = pl.preQ[pl.n_views];
-      const int g = (int)(r / per_group);
-      const uint32_t rr = r - (uint32_t)g * per_group;
-      const int v = upper_idx(pl.preQ, pl.n_views + 1, rr);
-      const uint32_t tile = rr - pl.preQ[v];
-      if (!block_wait(ws.done + 5 + 3 * v, pl.preP[v + 1] - pl.preP[v], pl, ws, &sm.ok)) return;
-      const FrontView& V = pl.v[v];
-      const int l0 = g * kLevelPair;
-      const int gl = min(kLevelPair, G.n_levels - l0);
-      const uint32_t p0 = tile * kQueryPoints;
-      const uint32_t np = (uint32_t)min((int64_t)kQueryPoints, V.n - (int64_t)p0);
-      const uint32_t total = 2u * np * (uint32_t)gl;
-      const uint64_t keep = l2_evict_last();
-      const int lane = tid & 31;
-      const uint32_t bx = lane & 1u;
-      OT* h = static_cast<OT*>(V.h);
-      for (uint32_t base = (uint32_t)(tid - lane); base < total; base += kFrontThreads) {
-        const uint32_t i = base + lane;
-        const bool valid = i < total;
-        const uint32_t item = (valid ? i : total - 1) >> 1;
-        const uint32_t p = p0 + item / (uint32_t)gl;
-        const int l = l0 + (int)(item % (uint32_t)gl);
-        query_pair<TT, OT>(G, table, __ldcg(V.pos + 3 * p + 0), __ldcg(V.pos + 3 * p + 1),
-                           __ldcg(V.pos + 3 * p + 2), p, l, bx, valid, h, keep);
-      }
+    }
+  }
+}
+
+// The query of one level pair for a tile of view v's points (ticket r of
+// the query launch): the per-(point, level) arithmetic of k_hash_fwd.
+template <class TT, class OT>
+__global__ void __launch_bounds__(kFrontThreads, 8) k_front_query(const __grid_constant__ FrontPlan pl, GridParams G,
+                                                                  const TT* __restrict__ table) {
+  const uint32_t per_group = pl.preQ[pl.n_views];
+  const uint32_t total_items = per_group * (uint32_t)pl.n_groups;
+  const uint64_t keep = l2_evict_last();
+  const int lane = threadIdx.x & 31;
+  const uint32_t bx = lane & 1u;
+  for (uint32_t r = blockIdx.x; r < total_items; r += gridDim.x) {
+    const int g = (int)(r / per_group);
+    const uint32_t rr = r - (uint32_t)g * per_group;
+    const int v = upper_idx(pl.preQ, pl.n_views + 1, rr);
+    const uint32_t tile = rr - pl.preQ[v];
+    const FrontView& V = pl.v[v];
+    const int l0 = g * kLevelPair;
+    const int gl = min(kLevelPair, G.n_levels - l0);
+    const uint32_t p0 = tile * kQueryPoints;
+    const uint32_t np = (uint32_t)min((int64_t)kQueryPoints, V.n - (int64_t)p0);
+    const uint32_t total = 2u * np * (uint32_t)gl;
+    OT* h = static_cast<OT*>(V.h);
+    // warp-uniform trip count: the lane pair's exchange is a warp shuffle
+    for (uint32_t base = (uint32_t)(threadIdx.x - lane); base < total; base += kFrontThreads) {
+      const uint32_t i = base + lane;
+      const bool valid = i < total;
+      const uint32_t item = (valid ? i : total - 1) >> 1;
+      const uint32_t p = p0 + item / (uint32_t)gl;
+      const int l = l0 + (int)(item % (uint32_t)gl);
+      query_pair<TT, OT>(G, table, __ldg(V.pos + 3 * p + 0), __ldg(V.pos + 3 * p + 1), __ldg(V.pos + 3 * p + 2), p, l,
+                         bx, valid, h, keep);
     }
   }
 }
@@ -425,31 +436,39 @@ inpc_status make_plan(const inpc_octree* tree, uint64_t seed, const inpc_front_v
     pl.preP[v + 1] = (uint32_t)p;
     pl.preQ[v + 1] = (uint32_t)q;
   }
-  const int64_t counts[kStEnd] = {pl.Tw, pl.Tc, pl.Tg, d, (int64_t)pl.Tc * n_views, p, q * pl.n_groups};
+  const int64_t counts[kStEnd] = {pl.Tw, pl.Tc, pl.Tg, d, (int64_t)pl.Tc * n_views, p};
   int64_t f = 0;
   for (int s = 0; s < kStEnd; ++s) {
     pl.first[s] = (uint32_t)f;
     f += counts[s];
   }
-  if (f >= (int64_t(1) << 31)) return fail(INPC_ERR_CAPACITY, "inpc_sample_query_batch: %lld work items", (long long)f);
+  if (f >= (int64_t(1) << 31) || q * pl.n_groups >= (int64_t(1) << 31))
+    return fail(INPC_ERR_CAPACITY, "inpc_sample_query_batch: too many work items");
   pl.first[kStEnd] = (uint32_t)f;
   pl.short_by = fault_take_queue_short();
   return INPC_OK;
 }
 
-// Persistent grid: as many CTAs as fit on the GPU at once (more would only
-// queue behind them; fewer also completes, since a CTA waits only for
-// tickets taken before its own).
+// The sampling of all views: a persistent grid, as many CTAs as fit on the
+// GPU at once (more would only queue behind them; fewer also completes,
+// since a CTA waits only for tickets taken before its own).  Then the query
+// of all views: one launch over (level pair, view, tile) items, level-pair
+// major so that all views' points visit a pair's table rows while they are
+// in L2; it has no waits, so it runs at the query's own occupancy.
 template <class TT, class OT>
 inpc_status launch_front(const FrontPlan& pl, const inpc_octree& tree, const GridParams& G, const TT* table,
                          const FrontWs& ws, cudaStream_t s) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_front<TT, OT>, kFrontThreads, 0) != cudaSuccess ||
-      per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_front, kFrontThreads, 0) != cudaSuccess || per_sm < 1)
     per_sm = 1;
-  const int ctas = per_sm * device_sm_count();
-  INPC_TIMED("k_front", s, k_front<TT, OT><<<ctas, kFrontThreads, 0, s>>>(pl, tree, G, table, ws));
-  return check_launch("k_front");
+  const int sms = device_sm_count();
+  INPC_TIMED("k_front", s, k_front<<<per_sm * sms, kFrontThreads, 0, s>>>(pl, tree, ws));
+  INPC_TRY(check_launch("k_front"));
+  const long long items = (long long)pl.preQ[pl.n_views] * pl.n_groups;
+  if (items == 0) return INPC_OK;
+  const unsigned grid = (unsigned)std::min<long long>(items, (long long)sms * 8);
+  INPC_TIMED("k_front_query", s, k_front_query<TT, OT><<<grid, kFrontThreads, 0, s>>>(pl, G, table));
+  return check_launch("k_front_query");
 }
 
 }  // namespace
