@@ -644,11 +644,22 @@ def run_forms(args, api, B, dev, world, rank):
     vb = ViewBatch(c, l, w, tree.root_size, d32, t32, cams_s, n_s, grads_s, seed=0, n_streams=8, bf16=False, tune=True)
     vb.capture()
     ms_batch_s = timed(lambda k: vb.step(), steps)
+    tiles_s = [(d["opts"].tile_w, d["opts"].tile_h) for d in vb.views]
+    del vb
+    torch.cuda.empty_cache()
+    vb = ViewBatch(c, l, w, tree.root_size, d32, t32, cams_s, n_s, grads_s, seed=0, n_streams=8, bf16=False, tune=False,
+                   persistent=True)
+    for d, (tw, th) in zip(vb.views, tiles_s):
+        d["opts"].tile_w, d["opts"].tile_h = tw, th
+    vb.capture()
+    ms_pers_s = timed(lambda k: vb.step(), steps)
     out["fp32_batched_32_small_views"] = {
         "workload": "32 views 320x240 on an orbit, 1,048,576 samples each from the 1,048,576-leaf octree, "
                     "16-level 2^21x4 FP32 grid, one CUDA graph over 8 streams, autotuned tiles, fwd + fused bwd",
         "ms_per_step": ms_batch_s, "ms_per_view": ms_batch_s / len(cams_s),
-        "unbatched_ms_per_step": ms_plain_s, "speedup_vs_unbatched": ms_plain_s / ms_batch_s}
+        "unbatched_ms_per_step": ms_plain_s, "speedup_vs_unbatched": ms_plain_s / ms_batch_s,
+        "persistent_front_ms_per_step": ms_pers_s, "persistent_speedup_vs_unbatched": ms_plain_s / ms_pers_s,
+        "persistent_speedup_vs_stream_fork": ms_batch_s / ms_pers_s}
     del vb
     torch.cuda.empty_cache()
 

@@ -22,11 +22,12 @@
 // taken, so the queue always progresses.  Every wait gives up after
 // max_wait_ns of the GPU's global timer: it then sets INPC_DEV_TIMEOUT in the
 // status word and the abort flag, and every CTA returns at its next wait or
-// ticket.  The query launch then takes (level pair, view, tile of points)
-// items, level-pair major so that the table rows of a pair stay in L2 while
-// all views' points visit them; it has no waits (its inputs are complete
-// when it starts) and keeps the query's full occupancy, which the sampling
-// stages' registers would not allow in one kernel.  The per-item arithmetic
+// ticket.  The query launch then covers the views' points concatenated in
+// chunks of consecutive views, level pair after level pair within a chunk,
+// so that a pair's table rows and the chunk's positions stay in L2; it has
+// no waits (its inputs are complete when it starts) and keeps the query's
+// full occupancy, which the sampling stages' registers would not allow in
+// one kernel.  The per-item arithmetic
 // is that of the per-view kernels (sample_impl.cuh, query_pair), so the
 // outputs are bit-identical to inpc_sample_octree + inpc_query_hashgrid of
 // each view.
@@ -49,7 +50,11 @@ constexpr int kFrontMaxViews = 64;
 constexpr int kFrontThreads = 256;
 constexpr int kWTile = 8192;          // leaves per max item
 constexpr int kPlaceTile = 16384;     // slots per place item
-constexpr int kQueryPoints = 1024;    // points per query item (one level pair)
+constexpr int kQueryPad = 16;        // query launch: each view's points padded to a multiple of this
+// query launch: consecutive views are grouped into chunks of up to this
+// many points (a chunk of one view may be larger); the chunks go one after
+// another, and within a chunk the level pairs do
+constexpr int64_t kQueryChunkPoints = int64_t(1) << 22;
 constexpr int kLevelPair = 2;
 
 enum : int { kStW = 0, kStC, kStG, kStD, kStS, kStP, kStEnd };
@@ -74,7 +79,9 @@ struct FrontPlan {
   uint32_t first[kStEnd + 1];          // first ticket of each stage; first[kStEnd] = total
   uint32_t preD[kFrontMaxViews + 1];   // D tiles of views < v
   uint32_t preP[kFrontMaxViews + 1];
-  uint32_t preQ[kFrontMaxViews + 1];   // query tiles of views < v (per level pair)
+  uint32_t preQ[kFrontMaxViews + 1];   // points of views < v, each view's count padded to a multiple of 16
+  int n_chunks;
+  int chunk_v0[kFrontMaxViews + 1];    // first view of each query chunk; chunk_v0[n_chunks] = n_views
   uint32_t short_by;                   // fault injection: view 0's count scan waits for this many extra draw tiles
   long long max_wait_ns;
   uint32_t k0, k1;                     // Philox key (seed lo, seed hi)
@@ -375,37 +382,47 @@ __global__ void __launch_bounds__(kFrontThreads) k_front(const __grid_constant__
   }
 }
 
-// The query of one level pair for a tile of view v's points (ticket r of
-// the query launch): the per-(point, level) arithmetic of k_hash_fwd.
+// The query of every view in one launch, laid out as k_hash_fwd: grid y is
+// the level pair, grid x strides over the lane items of the points of a
+// chunk of views concatenated, grid z is the chunk.  Chunks run one after
+// another and within a chunk the level pairs do, so both the chunk's
+// positions (re-read once per pair) and a pair's table rows stay in L2:
+// small views share the table rows of a pair, a large view keeps its own
+// positions, as in k_hash_fwd on one view.  Each view's points are padded to
+// a multiple of 16 in that index space, so a warp's 8 (or 16) points belong
+// to one view and the view is looked up once per warp; padding lanes join
+// the pair exchange but store nothing.
 template <class TT, class OT>
-__global__ void __launch_bounds__(kFrontThreads, 8) k_front_query(const __grid_constant__ FrontPlan pl, GridParams G,
-                                                                  const TT* __restrict__ table) {
-  const uint32_t per_group = pl.preQ[pl.n_views];
-  const uint32_t total_items = per_group * (uint32_t)pl.n_groups;
+__global__ void __launch_bounds__(kFrontThreads) k_front_query(const __grid_constant__ FrontPlan pl, GridParams G,
+                                                               const TT* __restrict__ table) {
+  const int l0 = blockIdx.y * kLevelPair;
+  const int gl = min(kLevelPair, G.n_levels - l0);
+  const int v0 = pl.chunk_v0[blockIdx.z], v1 = pl.chunk_v0[blockIdx.z + 1];
+  const uint32_t first = 2u * pl.preQ[v0] * (uint32_t)gl;
   const uint64_t keep = l2_evict_last();
   const int lane = threadIdx.x & 31;
   const uint32_t bx = lane & 1u;
-  for (uint32_t r = blockIdx.x; r < total_items; r += gridDim.x) {
-    const int g = (int)(r / per_group);
-    const uint32_t rr = r - (uint32_t)g * per_group;
-    const int v = upper_idx(pl.preQ, pl.n_views + 1, rr);
-    const uint32_t tile = rr - pl.preQ[v];
-    const FrontView& V = pl.v[v];
-    const int l0 = g * kLevelPair;
-    const int gl = min(kLevelPair, G.n_levels - l0);
-    const uint32_t p0 = tile * kQueryPoints;
-    const uint32_t np = (uint32_t)min((int64_t)kQueryPoints, V.n - (int64_t)p0);
-    const uint32_t total = 2u * np * (uint32_t)gl;
-    OT* h = static_cast<OT*>(V.h);
-    // warp-uniform trip count: the lane pair's exchange is a warp shuffle
-    for (uint32_t base = (uint32_t)(threadIdx.x - lane); base < total; base += kFrontThreads) {
+  // the views of the chunk one after another: within a view the loop is
+  // k_hash_fwd's (view constants in registers), and the grid stride carries
+  // on from one view to the next, so every CTA keeps its share of items
+  const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t base = first + blockIdx.x * blockDim.x + (threadIdx.x - lane);
+  for (int v = v0; v < v1; ++v) {
+    const uint32_t hi = 2u * pl.preQ[v + 1] * (uint32_t)gl;
+    // the view's arrays indexed by the padded point index pp: shifted by
+    // the view's first padded point (pp - preQ[v] is the point's index)
+    const uint32_t vlo = pl.preQ[v], vend = vlo + (uint32_t)pl.v[v].n;
+    const float* vpos = pl.v[v].pos - 3ll * vlo;
+    OT* vh = static_cast<OT*>(pl.v[v].h) - (long long)vlo * 4 * G.n_levels;
+    for (; base < hi; base += stride) {
       const uint32_t i = base + lane;
-      const bool valid = i < total;
-      const uint32_t item = (valid ? i : total - 1) >> 1;
-      const uint32_t p = p0 + item / (uint32_t)gl;
-      const int l = l0 + (int)(item % (uint32_t)gl);
-      query_pair<TT, OT>(G, table, __ldg(V.pos + 3 * p + 0), __ldg(V.pos + 3 * p + 1), __ldg(V.pos + 3 * p + 2), p, l,
-                         bx, valid, h, keep);
+      const uint32_t item = i >> 1;
+      const uint32_t pp = item / (uint32_t)gl;
+      const int l = l0 + (int)(item - pp * (uint32_t)gl);
+      const bool valid = pp < vend;  // views end on warp boundaries: only padding lanes fail
+      const uint32_t pc = valid ? pp : vend - 1u;  // a padding lane redoes the view's last point
+      query_pair<TT, OT>(G, table, __ldg(vpos + 3 * pc + 0), __ldg(vpos + 3 * pc + 1), __ldg(vpos + 3 * pc + 2), pc,
+                         l, bx, valid, vh, keep);
     }
   }
 }
@@ -431,18 +448,30 @@ inpc_status make_plan(const inpc_octree* tree, uint64_t seed, const inpc_front_v
     pl.v[v] = FrontView{fv.view_id, fv.n_samples, fv.leaf_idx, fv.pos, fv.h};
     d += ceil_div(fv.n_samples, kDrawPerCta);
     p += ceil_div(fv.n_samples, kPlaceTile);
-    q += ceil_div(fv.n_samples, kQueryPoints);
+    q += ceil_div(fv.n_samples, kQueryPad) * kQueryPad;
     pl.preD[v + 1] = (uint32_t)d;
     pl.preP[v + 1] = (uint32_t)p;
     pl.preQ[v + 1] = (uint32_t)q;
   }
+  // query chunks: consecutive views up to kQueryChunkPoints points
+  pl.n_chunks = 0;
+  for (int v = 0; v < n_views;) {
+    pl.chunk_v0[pl.n_chunks++] = v;
+    int64_t pts = (int64_t)pl.preQ[v + 1] - pl.preQ[v];
+    ++v;
+    while (v < n_views && pts + ((int64_t)pl.preQ[v + 1] - pl.preQ[v]) <= kQueryChunkPoints) {
+      pts += (int64_t)pl.preQ[v + 1] - pl.preQ[v];
+      ++v;
+    }
+  }
+  pl.chunk_v0[pl.n_chunks] = n_views;
   const int64_t counts[kStEnd] = {pl.Tw, pl.Tc, pl.Tg, d, (int64_t)pl.Tc * n_views, p};
   int64_t f = 0;
   for (int s = 0; s < kStEnd; ++s) {
     pl.first[s] = (uint32_t)f;
     f += counts[s];
   }
-  if (f >= (int64_t(1) << 31) || q * pl.n_groups >= (int64_t(1) << 31))
+  if (f >= (int64_t(1) << 31) || 2 * q * kLevelPair >= (int64_t(1) << 32))
     return fail(INPC_ERR_CAPACITY, "inpc_sample_query_batch: too many work items");
   pl.first[kStEnd] = (uint32_t)f;
   pl.short_by = fault_take_queue_short();
@@ -464,9 +493,13 @@ inpc_status launch_front(const FrontPlan& pl, const inpc_octree& tree, const Gri
   const int sms = device_sm_count();
   INPC_TIMED("k_front", s, k_front<<<per_sm * sms, kFrontThreads, 0, s>>>(pl, tree, ws));
   INPC_TRY(check_launch("k_front"));
-  const long long items = (long long)pl.preQ[pl.n_views] * pl.n_groups;
-  if (items == 0) return INPC_OK;
-  const unsigned grid = (unsigned)std::min<long long>(items, (long long)sms * 8);
+  long long work = 0;  // lane items of the largest chunk's level pair
+  for (int c = 0; c < pl.n_chunks; ++c)
+    work = std::max<long long>(work, 2ll * (pl.preQ[pl.chunk_v0[c + 1]] - pl.preQ[pl.chunk_v0[c]]) *
+                                         std::min(kLevelPair, G.n_levels));
+  if (work == 0) return INPC_OK;
+  const dim3 grid((unsigned)std::max<long long>(1, std::min<long long>(ceil_div(work, kFrontThreads), (long long)sms * 16)),
+                  (unsigned)pl.n_groups, (unsigned)pl.n_chunks);
   INPC_TIMED("k_front_query", s, k_front_query<TT, OT><<<grid, kFrontThreads, 0, s>>>(pl, G, table));
   return check_launch("k_front_query");
 }

@@ -1190,7 +1190,7 @@ __device__ __forceinline__ void fill_empty(const RP& P, int tx, int ty, const Ti
 // Tile-order kernel for small buckets (at most 2 registers per lane): high
 // occupancy; the groups take the tile's pixels from a shared cursor.
 template <int V, int GA, class FT>
-__global__ void __launch_bounds__(kThreads, 4) k_blend_fwd(RP P, const FT* __restrict__ feat, RasterWs ws,
+__global__ void __launch_bounds__(kThreads, 5) k_blend_fwd(RP P, const FT* __restrict__ feat, RasterWs ws,
                                                          FT* __restrict__ image, float* __restrict__ T_final,
                                                          int32_t* __restrict__ n_contrib) {
   __shared__ TileSmem S;
