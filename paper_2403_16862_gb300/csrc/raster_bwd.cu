@@ -87,16 +87,22 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
   // the cell whose corners the accumulators hold (kFar: none yet)
   constexpr uint32_t kFar = 1u << 30;
   uint32_t hx = kFar, hy = kFar, hz = kFar;
-  __shared__ PointRec rec_s[kThreads / 32][32];
   // Per-point values (fragment scalars, pixel, position, the h0 term) are
-  // formed once per point: each lane of a warp computes them for one of the
-  // next kBatch x kPW points into a record, and the level lanes then read
-  // the records, instead of every level lane repeating the projection and
-  // the fragment gathers.
-  PointRec* rec = rec_s[warp];
-  const int base = (int)blockIdx.x * chunk + (warp >> 1) * kPW;  // the warp's first point slot
-  for (int t0 = 0; base + t0 * kGroups < last; t0 += kBatch) {
-    {
+  // formed once per point: one lane per point computes them for the next
+  // kBatch x kPW points of the warp pair into records, and the level lanes
+  // of both warps then read the records, instead of every level lane
+  // repeating the projection and the fragment gathers.  The pair's warps
+  // take turns (even batches: the coarse warp, odd: the fine warp); the
+  // records are double-buffered, so one barrier of the pair per batch
+  // orders both the writes before the reads and the reads of a buffer
+  // before its next writes.
+  __shared__ PointRec rec_s[kThreads / 64][2][32];
+  const int pair = warp >> 1;
+  const int base = (int)blockIdx.x * chunk + pair * kPW;  // the pair's first point slot
+  int buf = 0;
+  for (int t0 = 0; base + t0 * kGroups < last; t0 += kBatch, buf ^= 1) {
+    PointRec* rec = rec_s[pair][buf];
+    if ((warp & 1) == buf) {
       const int pid = base + lane % kPW + (t0 + lane / kPW) * kGroups;
       PointRec R;
       R.mask = 0;
@@ -136,7 +142,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
       }
       rec[lane] = R;
     }
-    __syncwarp();
+    // the pair's named barrier (id 1 + pair, the two warps' 64 threads)
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + pair) : "memory");
     for (int t = 0; t < kBatch; ++t) {
       const int id = first + (t0 + t) * kGroups;
       if (id >= last) break;
@@ -217,7 +224,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
       hy = cy;
       hz = cz;
     }
-    __syncwarp();
   }
   if (!active || !coarse || hx == kFar) return;
   const uint32_t qx = hx & 1u, qy = hy & 1u, qz = hz & 1u;
