@@ -40,6 +40,56 @@ struct __align__(16) PointRec {
   float y, z, pad0, pad1;
 };
 
+// The named barrier of warp pair `pair` (id 1 + pair, the pair's 64
+// threads).  The warp first reconverges (a level loop may end early for
+// half of its lanes at the end of a chunk), then meets the other warp.
+__device__ __forceinline__ void pair_barrier(int pair) {
+  __syncwarp();
+  asm volatile("barrier.sync %0, 64;" ::"r"(1 + pair) : "memory");
+}
+
+// The record of point pid (< last; an empty record otherwise).
+template <class FT>
+__device__ __forceinline__ PointRec point_record(const RP& P, const float* __restrict__ pos,
+                                                 const FT* __restrict__ feat, const RasterWs& ws, int pid, int last,
+                                                 uint64_t stream) {
+  PointRec R;
+  R.mask = 0;
+  R.pix0 = 0;
+  R.h0term = 0.f;
+  R.sc = make_float4(0.f, 0.f, 0.f, 0.f);
+  R.x = R.y = R.z = 0.f;
+  R.pad0 = R.pad1 = 0.f;
+  if (pid >= last) return R;
+  const uint4 sl = ld_hint_u4(reinterpret_cast<const uint4*>(ws.pslot) + pid, stream);
+  const uint32_t slots[4] = {sl.x, sl.y, sl.z, sl.w};
+  R.x = __ldg(pos + 3 * pid + 0);
+  R.y = __ldg(pos + 3 * pid + 1);
+  R.z = __ldg(pos + 3 * pid + 2);
+  if ((sl.x & sl.y & sl.z & sl.w) == kNoSlot) return R;
+  Splat sp;
+  splat_xyz(P, R.x, R.y, R.z, sp);
+  float e_h0 = 0.f;
+  const float ah = point_alpha_h(P, nullptr, feat, pid, &e_h0);
+  float2 sc[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sc[k] = slots[k] == kNoSlot ? make_float2(0.f, 0.f) : ld_hint_f2(ws.fscal + slots[k], stream);
+  float dah = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (slots[k] == kNoSlot) continue;
+    R.mask |= 1u << k;
+    const float w = corner_weight(sp.f, k & 1, k >> 1);
+    if (__fmul_rn(ah, w) <= P.alpha_max) dah = __fmaf_rn(w, sc[k].y, dah);
+  }
+  // channel 0 of the blended color is the constant 1; the opacity gradient
+  // reaches h0 through alpha_h = 1 - exp(-exp(h0))
+  R.h0term = dah * (e_h0 * expf(-e_h0));
+  R.pix0 = sp.f.j0 * P.cam.W + sp.f.i0;
+  R.sc = make_float4(sc[0].x, sc[1].x, sc[2].x, sc[3].x);
+  return R;
+}
+
 template <int GA, class FT>
 __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParams Gp, const float* __restrict__ pos,
                                                                const FT* __restrict__ feat,
@@ -91,59 +141,24 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
   // formed once per point: one lane per point computes them for the next
   // kBatch x kPW points of the warp pair into records, and the level lanes
   // of both warps then read the records, instead of every level lane
-  // repeating the projection and the fragment gathers.  The pair's warps
-  // take turns (even batches: the coarse warp, odd: the fine warp); the
-  // records are double-buffered, so one barrier of the pair per batch
-  // orders both the writes before the reads and the reads of a buffer
-  // before its next writes.
+  // repeating the projection and the fragment gathers.  The fine warp, whose
+  // level loop is the shorter one, forms the records of the next batch
+  // before its level loop of the current batch, so the coarse warp never
+  // waits for them; the records are double-buffered, so one barrier of the
+  // pair per batch orders both the writes before the reads and the reads
+  // of a buffer before its next writes.
   __shared__ PointRec rec_s[kThreads / 64][2][32];
   const int pair = warp >> 1;
   const int base = (int)blockIdx.x * chunk + pair * kPW;  // the pair's first point slot
+  if (!coarse && base < last)
+    rec_s[pair][0][lane] = point_record(P, pos, feat, ws, base + lane % kPW + (lane / kPW) * kGroups, last, stream);
+  pair_barrier(pair);
   int buf = 0;
   for (int t0 = 0; base + t0 * kGroups < last; t0 += kBatch, buf ^= 1) {
     PointRec* rec = rec_s[pair][buf];
-    if ((warp & 1) == buf) {
-      const int pid = base + lane % kPW + (t0 + lane / kPW) * kGroups;
-      PointRec R;
-      R.mask = 0;
-      R.pix0 = 0;
-      R.h0term = 0.f;
-      R.sc = make_float4(0.f, 0.f, 0.f, 0.f);
-      R.x = R.y = R.z = 0.f;
-      if (pid < last) {
-        const uint4 sl = ld_hint_u4(reinterpret_cast<const uint4*>(ws.pslot) + pid, stream);
-        const uint32_t slots[4] = {sl.x, sl.y, sl.z, sl.w};
-        R.x = __ldg(pos + 3 * pid + 0);
-        R.y = __ldg(pos + 3 * pid + 1);
-        R.z = __ldg(pos + 3 * pid + 2);
-        if ((sl.x & sl.y & sl.z & sl.w) != kNoSlot) {
-          Splat sp;
-          splat_xyz(P, R.x, R.y, R.z, sp);
-          float e_h0 = 0.f;
-          const float ah = point_alpha_h(P, nullptr, feat, pid, &e_h0);
-          float2 sc[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            sc[k] = slots[k] == kNoSlot ? make_float2(0.f, 0.f) : ld_hint_f2(ws.fscal + slots[k], stream);
-          float dah = 0.f;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            if (slots[k] == kNoSlot) continue;
-            R.mask |= 1u << k;
-            const float w = corner_weight(sp.f, k & 1, k >> 1);
-            if (__fmul_rn(ah, w) <= P.alpha_max) dah = __fmaf_rn(w, sc[k].y, dah);
-          }
-          // channel 0 of the blended color is the constant 1; the opacity
-          // gradient reaches h0 through alpha_h = 1 - exp(-exp(h0))
-          R.h0term = dah * (e_h0 * expf(-e_h0));
-          R.pix0 = sp.f.j0 * P.cam.W + sp.f.i0;
-          R.sc = make_float4(sc[0].x, sc[1].x, sc[2].x, sc[3].x);
-        }
-      }
-      rec[lane] = R;
-    }
-    // the pair's named barrier (id 1 + pair, the two warps' 64 threads)
-    asm volatile("bar.sync %0, 64;" ::"r"(1 + pair) : "memory");
+    if (!coarse && base + (t0 + kBatch) * kGroups < last)
+      rec_s[pair][buf ^ 1][lane] =
+          point_record(P, pos, feat, ws, base + lane % kPW + (t0 + kBatch + lane / kPW) * kGroups, last, stream);
     for (int t = 0; t < kBatch; ++t) {
       const int id = first + (t0 + t) * kGroups;
       if (id >= last) break;
@@ -224,6 +239,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
       hy = cy;
       hz = cz;
     }
+    pair_barrier(pair);
   }
   if (!active || !coarse || hx == kFar) return;
   const uint32_t qx = hx & 1u, qy = hy & 1u, qz = hz & 1u;
