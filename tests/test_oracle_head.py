@@ -107,3 +107,25 @@ def test_contraction(oracle):
     far = r > 2
     np.testing.assert_allclose(norm[far], 2 - 1 / r[far], atol=1e-5)
     assert np.all((qq / 4 + 0.5 >= 0) & (qq / 4 + 0.5 <= 1))
+
+
+def test_contraction_against_the_fp64_definition(oracle):
+    # the FP32 contraction (kernel operation order) against the plain FP64
+    # definition: y = (x - c)/r, y for |y| <= 1, else (2 - 1/|y|) y/|y|,
+    # query position contract(y)/4 + 1/2; within a few FP32 roundings, and
+    # the same grid cell at the finest resolution wherever the FP64 value is
+    # not within that distance of a cell border
+    rng = np.random.default_rng(22)
+    center = np.array([0.1, -0.2, 0.3], np.float32)
+    radius = np.float32(0.75)
+    pts = np.concatenate([rng.normal(0, 1, size=(20000, 3)), rng.normal(0, 30, size=(20000, 3))]).astype(np.float32)
+    got = oracle.contract(pts, center, radius).astype(np.float64)
+    y = (pts.astype(np.float64) - center.astype(np.float64)) / float(radius)
+    n = np.linalg.norm(y, axis=1, keepdims=True)
+    want = np.where(n <= 1.0, y, (2.0 - 1.0 / n) * y / n) / 4.0 + 0.5
+    tol = 16 * 2.0 ** -24
+    assert np.all(np.abs(got - want) <= tol)
+    N = 4096
+    far = np.abs(want * N - np.rint(want * N)) > tol * N
+    assert np.all((np.floor(got * N) == np.floor(want * N))[far])
+    assert np.all((got >= 0.0) & (got <= 1.0))

@@ -343,3 +343,43 @@ def test_differentiation_subcase_finite_differences(oracle):
         if done == 20:
             break
     assert done == 20
+
+
+def test_projection_against_the_fp64_definition(oracle):
+    """The oracle's FP32 projection (Eq. 5 in the kernel's operation order)
+    against Eq. 5 evaluated in FP64: within the rounding bound of the FP32
+    steps, and the same top-left pixel (floor(u - 1/2), floor(v - 1/2))
+    wherever the FP64 value is farther than that bound from a pixel border.
+    A wrong operand, sign or order in the FP32 steps fails it."""
+    rng = np.random.default_rng(21)
+    eps = 2.0 ** -24
+    cams = [scenes.make_camera((0.5, 0.5, -1.2), 900.0, 900.0, 640.0, 416.0, 1280, 832)]
+    cams += scenes.orbit_cameras([(1920, 1080), (640, 480)])
+    pts = rng.uniform(0.0, 1.0, size=(20000, 3)).astype(np.float32)
+    ambiguous = 0
+    for cam in cams:
+        uvd, ok = oracle.project(cam, pts)
+        R = np.asarray(cam.R, np.float64)
+        t = np.asarray(cam.t, np.float64)
+        x = pts.astype(np.float64)
+        xc = x @ R.T + t
+        mag = np.abs(x) @ np.abs(R).T + np.abs(t)  # size of the camera coordinates' terms
+        z = xc[:, 2]
+        assert np.array_equal(ok, (z > cam.near) & (z < cam.far))
+        for k, (f, c) in enumerate(((cam.fx, cam.cx), (cam.fy, cam.cy))):
+            q = xc[:, k] / z
+            u64 = f * q + c
+            # rounding of the FP32 steps: three roundings in each camera
+            # coordinate, one in the division, one in the final fma
+            dq = (3 * eps * mag[:, k] + np.abs(q) * 3 * eps * mag[:, 2]) / z + eps * np.abs(q)
+            bound = 2.0 * (f * dq + eps * np.abs(u64) + eps * abs(c))
+            u32 = uvd[:, k].astype(np.float64)
+            assert np.all(np.abs(u32 - u64)[ok] <= bound[ok])
+            # the pixel decision (Sec. 3.4: the 2x2 nearest pixel centers)
+            far_from_border = np.abs((u64 - 0.5) - np.rint(u64 - 0.5)) > bound
+            same = np.floor(u32 - 0.5) == np.floor(u64 - 0.5)
+            assert np.all(same[ok & far_from_border])
+            ambiguous += int((ok & ~far_from_border).sum())
+        assert np.array_equal(uvd[ok, 2].astype(np.float64), z[ok].astype(np.float32).astype(np.float64)) or \
+            np.all(np.abs(uvd[ok, 2] - z[ok]) <= 3 * eps * mag[ok, 2])
+    assert ambiguous < 1e-3 * 3 * 2 * len(pts)
