@@ -12,7 +12,8 @@ the fused backward).
   one CUDA graph over 4 streams with autotuned tiles.  Every view's image
   is bitwise the image of that view rendered on its own (a path the
   precision check compares with the oracle), and the shared table gradient
-  is the sum of the views' own gradients up to the order of FP32 additions.
+  is the sum of the views' own gradients up to the order of FP32 additions;
+  the persistent front end renders the same images and features bitwise.
 
 The oracle's FP64 arrays at 16M samples take about 40 GB of host memory;
 the precision check skips on hosts with less available."""
@@ -201,3 +202,19 @@ def test_batching_workload_full_size(gpu, tmp_path, monkeypatch):
     e = (torch.linalg.norm(vb.grad_table.double() - total) / torch.linalg.norm(total)).item()
     print("batched table gradient against the sum of the views' own: norm-wise rel. difference %.3e" % e)
     assert e < 1e-5
+    # the persistent front end (sampling of all views in one work-queue
+    # launch, their query in one more) renders the same batch bitwise
+    tiles = [(d["opts"].tile_w, d["opts"].tile_h) for d in vb.views]
+    vp = ViewBatch(*tree_t, d16, t16, cams, n, grads, seed=0, n_streams=4, bf16=True, tune=False, persistent=True)
+    for d, (tw, th) in zip(vp.views, tiles):
+        d["opts"].tile_w, d["opts"].tile_h = tw, th
+    vp.capture()
+    vp.step()
+    torch.cuda.synchronize()
+    from paper_2403_16862_gb300 import _binding as B
+    assert B.inpc_read_device_status(vp.front_ws.data_ptr(), torch.cuda.current_stream().cuda_stream) == 0
+    for v in range(len(cams)):
+        assert torch.equal(vp.views[v]["img"], vb.views[v]["img"]), "view %d image (persistent front end)" % v
+        assert torch.equal(vp.views[v]["h"], vb.views[v]["h"]), "view %d features (persistent front end)" % v
+    ep = (torch.linalg.norm(vp.grad_table.double() - total) / torch.linalg.norm(total)).item()
+    assert ep < 1e-5
