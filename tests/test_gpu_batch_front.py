@@ -150,3 +150,67 @@ def test_persistent_batch_renders_as_the_fork_form(gpu, tmp_path, monkeypatch):
     assert float(e) < 1e-6
     st = B.inpc_read_device_status(b.front_ws.data_ptr(), torch.cuda.current_stream().cuda_stream)
     assert st == 0
+
+
+def test_persistent_batch_beyond_one_front_launch(gpu, tmp_path, monkeypatch):
+    # more than 64 views: inpc_render_batch_persistent runs its front end in
+    # launches of 64 views; every view still renders as in the fork form
+    monkeypatch.setenv("INPC_TUNE_CACHE", str(tmp_path / "tune.json"))
+    octree = scenes.make_octree(9, 4096 + 7 * 50)
+    tree_t, _ = _tree(octree, gpu)
+    grid = scenes.make_hashgrid(10, api.hashgrid_n_entries(RES16, 14), RES16, 14)
+    table = torch.from_numpy(grid.table).to(gpu)
+    desc = api.hashgrid_desc(RES16, 14)
+    sizes = [(48, 32)] * 70
+    cams = scenes.orbit_cameras(sizes, focal_ref=48.0, ref_height=32)
+    grads = [torch.from_numpy(scenes.upstream_grad(40 + v, (h, w, 64))).to(gpu) for v, (w, h) in enumerate(sizes)]
+    a = ViewBatch(*tree_t, octree.root_size, desc, table, cams, 3000, grads, seed=4, n_streams=4, tune=False)
+    b = ViewBatch(*tree_t, octree.root_size, desc, table, cams, 3000, grads, seed=4, n_streams=4, tune=False,
+                  persistent=True)
+    a.run_eager()
+    b.run_eager()
+    torch.cuda.synchronize()
+    for v, (va, vb) in enumerate(zip(a.views, b.views)):
+        assert torch.equal(va["pos"], vb["pos"]) and torch.equal(va["h"], vb["h"]), v
+        assert torch.equal(va["img"], vb["img"]), v
+    e = (torch.linalg.norm(a.grad_table.double() - b.grad_table.double()) / torch.linalg.norm(a.grad_table.double()))
+    assert float(e) < 1e-6
+
+
+def test_injected_argument_corruption_launches_nothing(gpu):
+    # with real device buffers, a corrupted first array argument (host-side
+    # fault "corrupt_args") is caught by each call's own validation: the call
+    # returns INPC_ERR_INVALID_ARG and launches no kernel
+    octree = scenes.make_octree(11, 4096 + 7 * 10)
+    tree_t, tree_c = _tree(octree, gpu)
+    desc = api.hashgrid_desc(RES16, 14)
+    table = torch.zeros(api.hashgrid_n_entries(RES16, 14), 4, dtype=torch.float32, device=gpu)
+    n = 5000
+    leaf = torch.empty(n, dtype=torch.int32, device=gpu)
+    pos = torch.rand(n, 3, device=gpu)
+    h = torch.empty(n, 64, device=gpu)
+    ws_s = api.workspace(B.inpc_sample_workspace_size(octree.n_leaves, n), gpu)
+    fws = api.workspace(B.inpc_sample_query_batch_workspace_size(octree.n_leaves, 1), gpu)
+    stream = torch.cuda.current_stream().cuda_stream
+    fv = [B.InpcFrontView(view_id=0, n_samples=n, leaf_idx=leaf.data_ptr(), pos=pos.data_ptr(), h=h.data_ptr())]
+    calls = [
+        lambda: B.inpc_sample_octree(tree_c, 0, 0, n, leaf.data_ptr(), pos.data_ptr(), None, ws_s.data_ptr(),
+                                     ws_s.numel(), stream),
+        lambda: B.inpc_query_hashgrid(desc, table.data_ptr(), pos.data_ptr(), n, h.data_ptr(), stream),
+        lambda: B.inpc_sample_query_batch(tree_c, 0, desc, table.data_ptr(), fv, 1000, fws.data_ptr(), fws.numel(),
+                                          stream),
+    ]
+    torch.cuda.synchronize()
+    before = B.inpc_kernel_launches()
+    B.inpc_set_fault("corrupt_args")
+    try:
+        for call in calls:
+            with pytest.raises(B.InpcError) as e:
+                call()
+            assert e.value.status == B.INPC_ERR_INVALID_ARG
+    finally:
+        B.inpc_set_fault(None)
+    assert B.inpc_kernel_launches() == before
+    calls[0]()  # disarmed: the same call runs
+    torch.cuda.synchronize()
+    assert B.inpc_kernel_launches() > before
