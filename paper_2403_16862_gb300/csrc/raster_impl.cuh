@@ -80,6 +80,8 @@ struct RasterWs {
   uint32_t* large_count;     // header word 2
   uint32_t* large_next;      // header word 3: the list kernel's next list entry (forward, then backward)
   uint32_t* heavy_next;      // header word 4: the forward CTA kernel's next list entry
+  uint32_t* wide_count;      // header word 5: forward list entries with 8 registers per lane (at the list's end)
+  uint32_t* wide_next;       // header word 6: their cursor
   uint32_t* pix_count;       // [n_pix]
   uint32_t* pix_start;       // [n_pix + 1]
   uint32_t* tops;            // prefix-sum block totals
@@ -105,6 +107,8 @@ RasterWs carve(void* base, long long n_pix, long long n) {
   w.large_count = base ? reinterpret_cast<uint32_t*>(base) + 2 : nullptr;
   w.large_next = base ? reinterpret_cast<uint32_t*>(base) + 3 : nullptr;
   w.heavy_next = base ? reinterpret_cast<uint32_t*>(base) + 4 : nullptr;
+  w.wide_count = base ? reinterpret_cast<uint32_t*>(base) + 5 : nullptr;
+  w.wide_next = base ? reinterpret_cast<uint32_t*>(base) + 6 : nullptr;
   const long long nf = std::max<long long>(4 * n, 1);
   w.pix_count = c.take<uint32_t>(n_pix);
   w.pix_start = c.take<uint32_t>(n_pix + 1);
@@ -302,19 +306,22 @@ struct CountLoad {
 };
 
 // Bucket-size classes: up to cap_small fragments (at most 2 registers per
-// lane) stay with the tile-order kernel; up to cap_large go to the list of
-// the register kernel with 4 or 8 registers per lane; larger ones go to the
-// CTA path.
+// lane) stay with the tile-order kernel; up to cap_mid go to the front of
+// the list of the register kernel with 4 registers per lane, up to
+// cap_large to its back, for the kernel with 8 (two kernels, each with half
+// the code: the unrolled sorting networks of both sizes in one kernel
+// stalled it on instruction fetch); larger ones go to the CTA path.
 __global__ void k_classify(const uint32_t* __restrict__ pix_start, long long n_pix, const uint32_t* __restrict__ tops,
                            long long nb, uint32_t cap_small, uint32_t cap_large, uint32_t* __restrict__ heavy,
                            uint32_t* heavy_count, uint32_t* __restrict__ large, uint32_t* large_count,
-                           uint32_t* __restrict__ pix_start_w) {
+                           uint32_t* __restrict__ pix_start_w, uint32_t cap_mid, uint32_t* wide_count) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q == 0) pix_start_w[n_pix] = tops[nb];
   if (q >= n_pix) return;
   const uint32_t end = q + 1 < n_pix ? pix_start[q + 1] : tops[nb];
   const uint32_t m = end - pix_start[q];
   if (m > cap_large) heavy[atomicAdd(heavy_count, 1u)] = (uint32_t)q;
+  else if (m > cap_mid) large[n_pix - 1 - atomicAdd(wide_count, 1u)] = (uint32_t)q;
   else if (m > cap_small) large[atomicAdd(large_count, 1u)] = (uint32_t)q;
 }
 
@@ -1211,25 +1218,29 @@ __global__ void __launch_bounds__(kThreads, 5) k_blend_fwd(RP P, const FT* __res
   }
 }
 
-// List kernel for buckets of 2 * GA < m <= kRegMax * GA.
-template <int V, int GA, class FT>
-__global__ void __launch_bounds__(kThreads, 3) k_blend_fwd_large(RP P, const FT* __restrict__ feat, RasterWs ws,
-                                                               FT* __restrict__ image, float* __restrict__ T_final,
-                                                               int32_t* __restrict__ n_contrib) {
+// List kernel for buckets of 2 GA < m <= 4 GA (R = 4, the list's front) or
+// 4 GA < m <= kRegMax GA (R = kRegMax, the list's back): each group takes
+// the next pixel of its list when it is done with one (bucket sizes differ
+// by up to 4x, so a fixed stride leaves tails).
+template <int V, int GA, class FT, int R>
+__global__ void __launch_bounds__(kThreads, R == kRegMax ? 3 : 4) k_blend_fwd_large(RP P, const FT* __restrict__ feat,
+                                                                                    RasterWs ws,
+                                                                                    FT* __restrict__ image,
+                                                                                    float* __restrict__ T_final,
+                                                                                    int32_t* __restrict__ n_contrib) {
   const Group<GA> G;
-  const uint32_t n_large = *ws.large_count;
-  // each group takes the next pixel of the list when it is done with one
-  // (bucket sizes differ by up to 4x, so a fixed stride leaves tails)
+  const bool wide = R == kRegMax;
+  const uint32_t n_list = wide ? *ws.wide_count : *ws.large_count;
+  uint32_t* cursor = wide ? ws.wide_next : ws.large_next;
   for (;;) {
     uint32_t h = 0;
-    if (G.lg == 0) h = atomicAdd(ws.large_next, 1u);
+    if (G.lg == 0) h = atomicAdd(cursor, 1u);
     h = G.bcast(h, 0);
-    if (h >= n_large) break;
-    const long long q = ws.large[h];
+    if (h >= n_list) break;
+    const long long q = wide ? ws.large[P.n_pix - 1 - h] : ws.large[h];
     const uint32_t s0 = ws.pix_start[q];
     const int m = (int)(ws.pix_start[q + 1] - s0);
-    if (m <= 4 * GA) blend_fwd_reg<V, GA, FT, 4>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
-    else blend_fwd_reg<V, GA, FT, kRegMax>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
+    blend_fwd_reg<V, GA, FT, R>(G, P, ws, s0, m, q, feat, image, T_final, n_contrib);
   }
 }
 
@@ -2038,7 +2049,7 @@ inpc_status bin_fragments(const RP& P, const float* pos, const float* opacity, c
   const long long nb = ceil_div(P.n_pix, scan::kBlock);
   k_classify<<<(unsigned)ceil_div(P.n_pix, 256), 256, 0, s>>>(ws.pix_start, P.n_pix, ws.tops, nb, cap_small, cap_group,
                                                                ws.heavy, ws.heavy_count, ws.large, ws.large_count,
-                                                               ws.pix_start);
+                                                               ws.pix_start, 4 * (cap_small / 2), ws.wide_count);
   INPC_TRY(check_launch("k_classify"));
   if (P.n > 0) {
     INPC_TIMED("k_pix_scatter", s,
@@ -2059,8 +2070,12 @@ inpc_status launch_fwd(const RP& P, const float* pos, const float* opacity, cons
              k_blend_fwd<V, GA, FT><<<P.n_tiles, kThreads, 0, s>>>(P, feat, ws, image, T_final, n_contrib));
   INPC_TRY(check_launch("k_blend_fwd"));
   INPC_TIMED("k_blend_fwd_large", s,
-             k_blend_fwd_large<V, GA, FT><<<device_sm_count() * 3, kThreads, 0, s>>>(P, feat, ws, image, T_final,
-                                                                                   n_contrib));
+             k_blend_fwd_large<V, GA, FT, 4><<<device_sm_count() * 4, kThreads, 0, s>>>(P, feat, ws, image, T_final,
+                                                                                      n_contrib));
+  INPC_TRY(check_launch("k_blend_fwd_large"));
+  INPC_TIMED("k_blend_fwd_large", s,
+             k_blend_fwd_large<V, GA, FT, kRegMax><<<device_sm_count() * 3, kThreads, 0, s>>>(P, feat, ws, image,
+                                                                                            T_final, n_contrib));
   INPC_TRY(check_launch("k_blend_fwd_large"));
   INPC_TIMED("k_blend_fwd_heavy", s,
              k_blend_fwd_heavy<V, GA, FT><<<device_sm_count() * 4, kThreads, HeavyBuf::bytes(), s>>>(
