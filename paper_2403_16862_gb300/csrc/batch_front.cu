@@ -22,13 +22,12 @@
 // taken, so the queue always progresses.  Every wait gives up after
 // max_wait_ns of the GPU's global timer: it then sets INPC_DEV_TIMEOUT in the
 // status word and the abort flag, and every CTA returns at its next wait or
-// ticket.  The query launch then covers the views' points concatenated in
-// chunks of consecutive views, level pair after level pair within a chunk,
-// so that a pair's table rows and the chunk's positions stay in L2; it has
-// no waits (its inputs are complete when it starts) and keeps the query's
-// full occupancy, which the sampling stages' registers would not allow in
-// one kernel.  The per-item arithmetic
-// is that of the per-view kernels (sample_impl.cuh, query_pair), so the
+// ticket.  The query launch then covers the views' points concatenated,
+// each warp taking 16 points of one view through a group of levels whose
+// rows stay in L2; it has no waits (its inputs are complete when it starts)
+// and keeps the query's full occupancy, which the sampling stages'
+// registers would not allow in one kernel.  The per-item arithmetic
+// is that of the per-view kernels (sample_impl.cuh, query_half), so the
 // outputs are bit-identical to inpc_sample_octree + inpc_query_hashgrid of
 // each view.
 #include <algorithm>
@@ -51,11 +50,6 @@ constexpr int kFrontThreads = 256;
 constexpr int kWTile = 8192;          // leaves per max item
 constexpr int kPlaceTile = 16384;     // slots per place item
 constexpr int kQueryPad = 16;        // query launch: each view's points padded to a multiple of this
-// query launch: consecutive views are grouped into chunks of up to this
-// many points (a chunk of one view may be larger); the chunks go one after
-// another, and within a chunk the level pairs do
-constexpr int64_t kQueryChunkPoints = int64_t(1) << 22;
-constexpr int kLevelPair = 2;
 
 enum : int { kStW = 0, kStC, kStG, kStD, kStS, kStP, kStEnd };
 
@@ -74,14 +68,11 @@ struct FrontPlan {
   int64_t L;
   int Gl;            // guide table: 2^Gl + 1 entries
   int stride_log2;   // coarse search table of the slot starts
-  int n_groups;      // level pairs
   uint32_t Tw, Tc, Tg;
   uint32_t first[kStEnd + 1];          // first ticket of each stage; first[kStEnd] = total
   uint32_t preD[kFrontMaxViews + 1];   // D tiles of views < v
   uint32_t preP[kFrontMaxViews + 1];
   uint32_t preQ[kFrontMaxViews + 1];   // points of views < v, each view's count padded to a multiple of 16
-  int n_chunks;
-  int chunk_v0[kFrontMaxViews + 1];    // first view of each query chunk; chunk_v0[n_chunks] = n_views
   uint32_t short_by;                   // fault injection: view 0's count scan waits for this many extra draw tiles
   long long max_wait_ns;
   uint32_t k0, k1;                     // Philox key (seed lo, seed hi)
@@ -382,47 +373,49 @@ __global__ void __launch_bounds__(kFrontThreads) k_front(const __grid_constant__
   }
 }
 
-// The query of every view in one launch, laid out as k_hash_fwd: grid y is
-// the level pair, grid x strides over the lane items of the points of a
-// chunk of views concatenated, grid z is the chunk.  Chunks run one after
-// another and within a chunk the level pairs do, so both the chunk's
-// positions (re-read once per pair) and a pair's table rows stay in L2:
-// small views share the table rows of a pair, a large view keeps its own
-// positions, as in k_hash_fwd on one view.  Each view's points are padded to
-// a multiple of 16 in that index space, so a warp's 8 (or 16) points belong
-// to one view and the view is looked up once per warp; padding lanes join
-// the pair exchange but store nothing.
+// The query of every view in one launch, laid out as k_hash_fwd: a warp
+// takes 16 consecutive points, two lanes per point, through the levels of
+// one level group (grid y); within a group the views go one after another.
+// The views' points are concatenated, each view's count padded to a
+// multiple of 16, so a warp's points belong to one view; padding lanes join
+// the pair exchanges but store nothing.  The grid strides over the groups
+// of 16 of all views, view after view, so every CTA keeps its share of
+// groups while the view's constants stay in registers for the whole view.
 template <class TT, class OT>
 __global__ void __launch_bounds__(kFrontThreads) k_front_query(const __grid_constant__ FrontPlan pl, GridParams G,
-                                                               const TT* __restrict__ table) {
-  const int l0 = blockIdx.y * kLevelPair;
-  const int gl = min(kLevelPair, G.n_levels - l0);
-  const int v0 = pl.chunk_v0[blockIdx.z], v1 = pl.chunk_v0[blockIdx.z + 1];
-  const uint32_t first = 2u * pl.preQ[v0] * (uint32_t)gl;
+                                                               LevelGroups LG, const TT* __restrict__ table) {
+  const int lb = LG.begin[blockIdx.y], le = LG.begin[blockIdx.y + 1];
   const uint64_t keep = l2_evict_last();
-  const int lane = threadIdx.x & 31;
+  const uint32_t lane = threadIdx.x & 31u;
   const uint32_t bx = lane & 1u;
-  // the views of the chunk one after another: within a view the loop is
-  // k_hash_fwd's (view constants in registers), and the grid stride carries
-  // on from one view to the next, so every CTA keeps its share of items
-  const uint32_t stride = gridDim.x * blockDim.x;
-  uint32_t base = first + blockIdx.x * blockDim.x + (threadIdx.x - lane);
-  for (int v = v0; v < v1; ++v) {
-    const uint32_t hi = 2u * pl.preQ[v + 1] * (uint32_t)gl;
+  const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+  uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int v = 0; v < pl.n_views; ++v) {
+    const uint32_t g_end = pl.preQ[v + 1] / kQueryPad;
     // the view's arrays indexed by the padded point index pp: shifted by
     // the view's first padded point (pp - preQ[v] is the point's index)
     const uint32_t vlo = pl.preQ[v], vend = vlo + (uint32_t)pl.v[v].n;
     const float* vpos = pl.v[v].pos - 3ll * vlo;
     OT* vh = static_cast<OT*>(pl.v[v].h) - (long long)vlo * 4 * G.n_levels;
-    for (; base < hi; base += stride) {
-      const uint32_t i = base + lane;
-      const uint32_t item = i >> 1;
-      const uint32_t pp = item / (uint32_t)gl;
-      const int l = l0 + (int)(item - pp * (uint32_t)gl);
+    for (; g < g_end; g += n_warps) {
+      const uint32_t pp = g * kQueryPad + (lane >> 1);
       const bool valid = pp < vend;  // views end on warp boundaries: only padding lanes fail
       const uint32_t pc = valid ? pp : vend - 1u;  // a padding lane redoes the view's last point
-      query_pair<TT, OT>(G, table, __ldg(vpos + 3 * pc + 0), __ldg(vpos + 3 * pc + 1), __ldg(vpos + 3 * pc + 2), pc,
-                         l, bx, valid, vh, keep);
+      const float x = __ldg(vpos + 3 * pc + 0), y = __ldg(vpos + 3 * pc + 1), z = __ldg(vpos + 3 * pc + 2);
+      OT* hp = vh + (long long)pc * G.n_levels * 4;
+      for (int l = lb; l < le; l += 2) {
+        const float2 a = query_half<TT>(G, table, x, y, z, l, bx, keep);
+        if (l + 1 < le) {
+          const float2 b = query_half<TT>(G, table, x, y, z, l + 1, bx, keep);
+          // lane 0 keeps level l's row, lane 1 level l + 1's
+          const float2 give = bx ? a : b;
+          const float r0 = __shfl_xor_sync(0xffffffffu, give.x, 1), r1 = __shfl_xor_sync(0xffffffffu, give.y, 1);
+          const float4 row = bx ? make_float4(r0, r1, b.x, b.y) : make_float4(a.x, a.y, r0, r1);
+          if (valid) store_out<OT>(hp, l + (int)bx, row);
+        } else if (valid) {
+          store_half<OT>(hp, l, bx, a);
+        }
+      }
     }
   }
 }
@@ -434,7 +427,6 @@ inpc_status make_plan(const inpc_octree* tree, uint64_t seed, const inpc_front_v
   pl.L = L;
   pl.Gl = guide_log2(L);
   pl.stride_log2 = coarse_stride_log2(L);
-  pl.n_groups = (G.n_levels + kLevelPair - 1) / kLevelPair;
   pl.Tw = (uint32_t)ceil_div(L, kWTile);
   pl.Tc = (uint32_t)ceil_div(L, kScanBlock);
   pl.Tg = (uint32_t)ceil_div((int64_t(1) << pl.Gl) + 1, kScanBlock);
@@ -453,25 +445,13 @@ inpc_status make_plan(const inpc_octree* tree, uint64_t seed, const inpc_front_v
     pl.preP[v + 1] = (uint32_t)p;
     pl.preQ[v + 1] = (uint32_t)q;
   }
-  // query chunks: consecutive views up to kQueryChunkPoints points
-  pl.n_chunks = 0;
-  for (int v = 0; v < n_views;) {
-    pl.chunk_v0[pl.n_chunks++] = v;
-    int64_t pts = (int64_t)pl.preQ[v + 1] - pl.preQ[v];
-    ++v;
-    while (v < n_views && pts + ((int64_t)pl.preQ[v + 1] - pl.preQ[v]) <= kQueryChunkPoints) {
-      pts += (int64_t)pl.preQ[v + 1] - pl.preQ[v];
-      ++v;
-    }
-  }
-  pl.chunk_v0[pl.n_chunks] = n_views;
   const int64_t counts[kStEnd] = {pl.Tw, pl.Tc, pl.Tg, d, (int64_t)pl.Tc * n_views, p};
   int64_t f = 0;
   for (int s = 0; s < kStEnd; ++s) {
     pl.first[s] = (uint32_t)f;
     f += counts[s];
   }
-  if (f >= (int64_t(1) << 31) || 2 * q * kLevelPair >= (int64_t(1) << 32))
+  if (f >= (int64_t(1) << 31) || q >= (int64_t(1) << 31))
     return fail(INPC_ERR_CAPACITY, "inpc_sample_query_batch: too many work items");
   pl.first[kStEnd] = (uint32_t)f;
   pl.short_by = fault_take_queue_short();
@@ -481,9 +461,8 @@ inpc_status make_plan(const inpc_octree* tree, uint64_t seed, const inpc_front_v
 // The sampling of all views: a persistent grid, as many CTAs as fit on the
 // GPU at once (more would only queue behind them; fewer also completes,
 // since a CTA waits only for tickets taken before its own).  Then the query
-// of all views: one launch over (level pair, view, tile) items, level-pair
-// major so that all views' points visit a pair's table rows while they are
-// in L2; it has no waits, so it runs at the query's own occupancy.
+// of all views in one launch; it has no waits, so it runs at the query's
+// own occupancy.
 template <class TT, class OT>
 inpc_status launch_front(const FrontPlan& pl, const inpc_octree& tree, const GridParams& G, const TT* table,
                          const FrontWs& ws, cudaStream_t s) {
@@ -493,14 +472,12 @@ inpc_status launch_front(const FrontPlan& pl, const inpc_octree& tree, const Gri
   const int sms = device_sm_count();
   INPC_TIMED("k_front", s, k_front<<<per_sm * sms, kFrontThreads, 0, s>>>(pl, tree, ws));
   INPC_TRY(check_launch("k_front"));
-  long long work = 0;  // lane items of the largest chunk's level pair
-  for (int c = 0; c < pl.n_chunks; ++c)
-    work = std::max<long long>(work, 2ll * (pl.preQ[pl.chunk_v0[c + 1]] - pl.preQ[pl.chunk_v0[c]]) *
-                                         std::min(kLevelPair, G.n_levels));
+  const long long work = 2ll * pl.preQ[pl.n_views];  // two lanes per padded point
   if (work == 0) return INPC_OK;
+  const LevelGroups LG = plan_level_groups(G, sizeof(TT) * 4);
   const dim3 grid((unsigned)std::max<long long>(1, std::min<long long>(ceil_div(work, kFrontThreads), (long long)sms * 16)),
-                  (unsigned)pl.n_groups, (unsigned)pl.n_chunks);
-  INPC_TIMED("k_front_query", s, k_front_query<TT, OT><<<grid, kFrontThreads, 0, s>>>(pl, G, table));
+                  (unsigned)LG.n);
+  INPC_TIMED("k_front_query", s, k_front_query<TT, OT><<<grid, kFrontThreads, 0, s>>>(pl, G, LG, table));
   return check_launch("k_front_query");
 }
 

@@ -1,12 +1,11 @@
 // hashgrid.cu -- multi-resolution hash-grid query (Sec. 3.3, App. A.5) and
 // its adjoint (the table gradient).
 //
-// The query runs two threads per (point, level), each gathering the four
-// corners on one side of the cell along x; levels go in groups of two along
-// grid y so that the rows in use at any time fit in L2, and within a group
-// a warp covers 8 points x 2 levels.  Corner rows are gathered as 16-byte
-// vectors (FP32) or 8-byte vectors (BF16).  The output is written with
-// streaming stores so that it does not evict the table from L2.
+// The query runs two threads per point, each gathering the four corners on
+// one side of the cell along x; a warp takes 16 consecutive points through
+// all levels.  Corner rows are gathered as 16-byte vectors (FP32) or 8-byte
+// vectors (BF16).  The output is written with streaming stores so that it
+// does not evict the table from L2.
 //
 // The backward uses red.global.add.v4.f32 (one 16-byte vector reduction per
 // corner and level), accumulating into an FP32 gradient table.
@@ -17,39 +16,60 @@
 namespace inpc {
 namespace {
 
-// Levels are processed in groups of kLevelGroup along grid y: blocks are
+// The adjoint processes levels in groups of kLevelGroup along grid y: blocks are
 // dispatched in linear order, so all points visit one group of levels
 // before the next, and the rows touched at a time (one or two 8 MB levels)
 // stay resident in L2 instead of the whole table.
 constexpr int kLevelGroup = 2;
 
-// Two lanes per (point, level): lane bx gathers the four corners at x + bx.
-// The x neighbours' rows differ only in their lowest bits (hashed: x is
-// multiplied by 1 before the XOR; dense: consecutive rows), so they share
-// one 128-byte line unless the carry of x + 1 reaches bit 3 (FP32) or bit 4
-// (BF16).  Loading both from one instruction then costs one L1 wavefront
-// instead of two, and the L1 wavefront rate bounds this kernel.  The pair
-// adds its partial sums with one exchange, and each lane stores half of
-// the four features.
+// A warp takes 16 consecutive points, two lanes per point, through the
+// levels of one level group (grid y, plan_level_groups), two levels at a
+// time: lane bx gathers the four corners at x + bx
+// of the point's cell.  The x neighbours' rows differ only in their lowest
+// bits (hashed: x is multiplied by 1 before the XOR; dense: consecutive
+// rows), so they share one 128-byte line unless the carry of x + 1 reaches
+// bit 3 (FP32) or bit 4 (BF16): loading both from one instruction costs one
+// L1 wavefront instead of two, and the L1 wavefront rate bounds this
+// kernel.  Consecutive points come from the same octree leaf, so at the
+// coarse levels the 16 points of an instruction mostly fall in a few cells
+// and share their lines as well (about 2.6 distinct lines per point and
+// level on average over the benchmark's 16 levels, against 2.9 with 8
+// points of two levels per instruction).  A group's rows stay in L2 under
+// evict_last while positions and outputs stream past them.  After each pair of levels the two lanes swap halves so that each stores
+// one level's whole 16-byte row: the warp writes each point's two levels
+// as one full 32-byte sector.
 template <class TT, class OT>
-__global__ void __launch_bounds__(256) k_hash_fwd(GridParams P, const TT* __restrict__ table,
+__global__ void __launch_bounds__(256) k_hash_fwd(GridParams P, LevelGroups LG, const TT* __restrict__ table,
                                                   const float* __restrict__ pos, long long n, OT* __restrict__ h) {
-  const int l0 = blockIdx.y * kLevelGroup;
-  const int gl = min(kLevelGroup, P.n_levels - l0);
-  // n <= 2^29 (checked by the caller): 32-bit indices do not overflow
-  const uint32_t total = 2u * (uint32_t)n * (uint32_t)gl;
+  const int lb = LG.begin[blockIdx.y], le = LG.begin[blockIdx.y + 1];
   const uint64_t keep = l2_evict_last();
-  const int lane = threadIdx.x & 31;
+  const uint32_t lane = threadIdx.x & 31u;
   const uint32_t bx = lane & 1u;
-  // warp-uniform trip count: the pair exchange is a warp shuffle
-  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x - lane); base < total; base += gridDim.x * blockDim.x) {
-    const uint32_t i = base + lane;
-    const bool valid = i < total;
-    const uint32_t item = (valid ? i : total - 1) >> 1;  // spare lanes redo the last item
-    const uint32_t p = item / (uint32_t)gl;
-    const int l = l0 + (int)(item - p * gl);
-    query_pair<TT, OT>(P, table, __ldg(pos + 3 * p + 0), __ldg(pos + 3 * p + 1), __ldg(pos + 3 * p + 2), p, l, bx,
-                       valid, h, keep);
+  // n <= 2^29 (checked by the caller): 32-bit indices do not overflow
+  const uint32_t n_groups = (uint32_t)((n + 15) >> 4);
+  const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+  // warp-uniform trip counts: the pair exchanges are warp shuffles
+  for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_groups; g += n_warps) {
+    const uint32_t pr = g * 16u + (lane >> 1);
+    const bool valid = pr < (uint32_t)n;
+    const uint32_t p = valid ? pr : (uint32_t)n - 1u;  // spare lanes redo the last point
+    const float x = __ldg(pos + 3 * p + 0), y = __ldg(pos + 3 * p + 1), z = __ldg(pos + 3 * p + 2);
+    OT* hp = h + (long long)p * P.n_levels * 4;
+    for (int l = lb; l < le; l += 2) {
+      const float2 a = query_half<TT>(P, table, x, y, z, l, bx, keep);
+      if (l + 1 < le) {
+        const float2 b = query_half<TT>(P, table, x, y, z, l + 1, bx, keep);
+        // lane 0 holds features 0-1 of both levels, lane 1 features 2-3:
+        // lane 0 gives level l + 1's half away and takes level l's, lane 1
+        // the other way round
+        const float2 give = bx ? a : b;
+        const float r0 = __shfl_xor_sync(0xffffffffu, give.x, 1), r1 = __shfl_xor_sync(0xffffffffu, give.y, 1);
+        const float4 row = bx ? make_float4(r0, r1, b.x, b.y) : make_float4(a.x, a.y, r0, r1);
+        if (valid) store_out<OT>(hp, l + (int)bx, row);
+      } else if (valid) {
+        store_half<OT>(hp, l, bx, a);
+      }
+    }
   }
 }
 
@@ -116,17 +136,21 @@ extern "C" inpc_status inpc_query_hashgrid(const inpc_hashgrid_desc* g, const vo
   if (!aligned(table, ta) || !aligned(h_out, oa) || !aligned(pos, 4))
     return fail(INPC_ERR_INVALID_ARG, "inpc_query_hashgrid: misaligned table/output/pos");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const dim3 grid = grid_for(2 * n, P.n_levels, 256);
+  // two lanes per point; grid y: the level groups
+  const LevelGroups LG = plan_level_groups(P, g->table_dtype == INPC_F32 ? 16 : 8);
+  const long long cap = (long long)device_sm_count() * 16;
+  const dim3 grid((unsigned)std::max<long long>(1, std::min<long long>((long long)ceil_div(2 * n, 256), cap)),
+                  (unsigned)LG.n);
   TimedLaunch timed("k_hash_fwd", s);
   if (g->table_dtype == INPC_F32 && g->out_dtype == INPC_F32)
-    k_hash_fwd<float, float><<<grid, 256, 0, s>>>(P, (const float*)table, pos, n, (float*)h_out);
+    k_hash_fwd<float, float><<<grid, 256, 0, s>>>(P, LG, (const float*)table, pos, n, (float*)h_out);
   else if (g->table_dtype == INPC_F32)
-    k_hash_fwd<float, __nv_bfloat16><<<grid, 256, 0, s>>>(P, (const float*)table, pos, n, (__nv_bfloat16*)h_out);
+    k_hash_fwd<float, __nv_bfloat16><<<grid, 256, 0, s>>>(P, LG, (const float*)table, pos, n, (__nv_bfloat16*)h_out);
   else if (g->out_dtype == INPC_F32)
-    k_hash_fwd<__nv_bfloat16, float><<<grid, 256, 0, s>>>(P, (const __nv_bfloat16*)table, pos, n, (float*)h_out);
+    k_hash_fwd<__nv_bfloat16, float><<<grid, 256, 0, s>>>(P, LG, (const __nv_bfloat16*)table, pos, n, (float*)h_out);
   else
     k_hash_fwd<__nv_bfloat16, __nv_bfloat16>
-        <<<grid, 256, 0, s>>>(P, (const __nv_bfloat16*)table, pos, n, (__nv_bfloat16*)h_out);
+        <<<grid, 256, 0, s>>>(P, LG, (const __nv_bfloat16*)table, pos, n, (__nv_bfloat16*)h_out);
   return check_launch("k_hash_fwd");
 }
 

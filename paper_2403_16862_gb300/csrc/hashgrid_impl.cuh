@@ -58,6 +58,44 @@ inpc_status make_params(const inpc_hashgrid_desc* g, GridParams& p, int64_t* tot
   return INPC_OK;
 }
 
+// The query's level groups: a launch covers one group per grid y index,
+// every point going through the group's levels before the next group
+// starts, so the rows in use at a time are one group's.  Groups hold an
+// even number of levels (pairs, so that a point's output for a pair is
+// one 32-byte sector), as many pairs as keep the group's rows within
+// kQueryL2Budget bytes: a table that fits in L2 beside the streamed
+// positions and outputs is one group (each point's position read once),
+// a larger one is split so that a group's rows stay resident.
+#ifndef INPC_QUERY_L2_BUDGET_MB
+#define INPC_QUERY_L2_BUDGET_MB 64
+#endif
+constexpr long long kQueryL2Budget = (long long)INPC_QUERY_L2_BUDGET_MB << 20;
+
+struct LevelGroups {
+  int n;
+  int begin[kMaxLevels + 1];  // group j covers levels begin[j] .. begin[j + 1] - 1
+};
+
+inline LevelGroups plan_level_groups(const GridParams& P, int row_bytes) {
+  LevelGroups g;
+  g.n = 0;
+  long long bytes = 0;
+  for (int l = 0; l < P.n_levels; l += 2) {
+    long long pair = 0;
+    for (int k = l; k < l + 2 && k < P.n_levels; ++k) {
+      const long long side = P.side[k];
+      pair += (P.dense[k] ? side * side * side : (long long)P.hash_mask + 1) * row_bytes;
+    }
+    if (g.n == 0 || bytes + pair > kQueryL2Budget) {
+      g.begin[g.n++] = l;
+      bytes = 0;
+    }
+    bytes += pair;
+  }
+  g.begin[g.n] = P.n_levels;
+  return g;
+}
+
 // Cell of x in [0, 1] at resolution N and both linear weights of that cell:
 // with s = fl(x N) and e = x N - s exactly (FMA), the upper-corner weight
 // f1 = x N - cell and the lower-corner weight f0 = cell + 1 - x N are each
@@ -158,15 +196,14 @@ __device__ __forceinline__ void store_half<__nv_bfloat16>(__nv_bfloat16* __restr
   __stcs(reinterpret_cast<unsigned int*>(out) + 2 * idx4 + half, *reinterpret_cast<unsigned int*>(&a));
 }
 
-// One lane of the query's lane pair for (point p, level l): lane bx
-// gathers the four corners at x + bx of the point's cell and weights them;
-// the pair adds its partial sums with one exchange (a warp shuffle, so the
-// whole warp calls this together) and each lane stores half of the level's
-// four features (valid lanes only).
-template <class TT, class OT>
-__device__ __forceinline__ void query_pair(const GridParams& P, const TT* __restrict__ table, float x, float y,
-                                           float z, uint32_t p, int l, uint32_t bx, bool valid, OT* __restrict__ h,
-                                           uint64_t keep) {
+// One lane of the query's lane pair for a point at (x, y, z) and level l:
+// lane bx gathers the four corners at x + bx of the point's cell and
+// weights them; the pair adds its partial sums with one exchange (a warp
+// shuffle, so the whole warp calls this together) and the lane returns
+// features 2 bx and 2 bx + 1 of the level.
+template <class TT>
+__device__ __forceinline__ float2 query_half(const GridParams& P, const TT* __restrict__ table, float x, float y,
+                                             float z, int l, uint32_t bx, uint64_t keep) {
   uint32_t cx, cy, cz;
   float gx[2], gy[2], gz[2];
   const int N = P.res[l];
@@ -189,8 +226,7 @@ __device__ __forceinline__ void query_pair(const GridParams& P, const TT* __rest
   // lane 0 keeps features 0-1, lane 1 features 2-3
   const float s0 = bx ? acc.x : acc.z, s1 = bx ? acc.y : acc.w;
   const float r0 = __shfl_xor_sync(0xffffffffu, s0, 1), r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
-  const float2 mine = bx ? make_float2(acc.z + r0, acc.w + r1) : make_float2(acc.x + r0, acc.y + r1);
-  if (valid) store_half<OT>(h, (long long)p * P.n_levels + l, bx, mine);
+  return bx ? make_float2(acc.z + r0, acc.w + r1) : make_float2(acc.x + r0, acc.y + r1);
 }
 
 __device__ __forceinline__ void red_add_v4(float* addr, float4 v) {
