@@ -130,13 +130,13 @@ def kernel_bytes(kernel, n, n_entries, n_frag, n_pix):
     """Algorithmic bytes of one launch (FP32, head mode, C channels).
 
     k_point_grad_hash (fused rasterizer backward tail + grid adjoint): per
-    point its four fragment slots (16 B), position (12 B), channel 0 of its
-    feature row (4 B); per fragment the blend backward's two scalars (8 B);
+    point its position (12 B) and channel 0 of its feature row (4 B); per
+    fragment slot the blend backward's two scalars (8 B, stored point-major);
     the upstream image gradient once (4 C per pixel); the table gradient
     read and written once (2 x 16 B per row).
     k_hash_fwd: positions, the table once, the feature rows written once."""
     if kernel == "k_point_grad_hash":
-        return 32 * n + 8 * n_frag + 4 * C * n_pix + 32 * n_entries
+        return 16 * n + 8 * n_frag + 4 * C * n_pix + 32 * n_entries
     if kernel == "k_hash_fwd":
         return 12 * n + 16 * n_entries + 4 * C * n
     return None

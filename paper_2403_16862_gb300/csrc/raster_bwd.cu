@@ -33,7 +33,7 @@ namespace {
 // A point's values shared by its level lanes.
 struct __align__(16) PointRec {
   int pix0;        // pixel of footprint corner 0 (j0 W + i0)
-  uint32_t mask;   // bit k: corner k has a fragment
+  uint32_t mask;   // bit k: corner k's fragment has T_k alpha_k != 0
   float h0term;    // level-0 channel-0 gradient: the opacity path into h0
   float x;
   float4 sc;       // T_k alpha_k of the four fragments (0 without one)
@@ -61,24 +61,28 @@ __device__ __forceinline__ PointRec point_record(const RP& P, const float* __res
   R.x = R.y = R.z = 0.f;
   R.pad0 = R.pad1 = 0.f;
   if (pid >= last) return R;
-  const uint4 sl = ld_hint_u4(reinterpret_cast<const uint4*>(ws.pslot) + pid, stream);
-  const uint32_t slots[4] = {sl.x, sl.y, sl.z, sl.w};
+  // the point's four (T_k alpha_k, dL/dalpha_k) pairs, one per footprint
+  // corner (zero where no fragment blended), as one 32-byte sector
+  const uint4 fa = ld_hint_u4(reinterpret_cast<const uint4*>(ws.fscal) + 2 * (long long)pid, stream);
+  const uint4 fb = ld_hint_u4(reinterpret_cast<const uint4*>(ws.fscal) + 2 * (long long)pid + 1, stream);
+  const float2 sc[4] = {make_float2(__uint_as_float(fa.x), __uint_as_float(fa.y)),
+                        make_float2(__uint_as_float(fa.z), __uint_as_float(fa.w)),
+                        make_float2(__uint_as_float(fb.x), __uint_as_float(fb.y)),
+                        make_float2(__uint_as_float(fb.z), __uint_as_float(fb.w))};
   R.x = __ldg(pos + 3 * pid + 0);
   R.y = __ldg(pos + 3 * pid + 1);
   R.z = __ldg(pos + 3 * pid + 2);
-  if ((sl.x & sl.y & sl.z & sl.w) == kNoSlot) return R;
+  if (((fa.x | fa.y | fa.z | fa.w | fb.x | fb.y | fb.z | fb.w) & 0x7fffffffu) == 0u) return R;
   Splat sp;
   splat_xyz(P, R.x, R.y, R.z, sp);
   float e_h0 = 0.f;
   const float ah = point_alpha_h(P, nullptr, feat, pid, &e_h0);
-  float2 sc[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) sc[k] = slots[k] == kNoSlot ? make_float2(0.f, 0.f) : ld_hint_f2(ws.fscal + slots[k], stream);
   float dah = 0.f;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    if (slots[k] == kNoSlot) continue;
-    R.mask |= 1u << k;
+    // a corner whose fragment has T_k alpha_k = 0 adds nothing to the
+    // colour gradient: its image-gradient row is not gathered
+    if (sc[k].x != 0.f) R.mask |= 1u << k;
     const float w = corner_weight(sp.f, k & 1, k >> 1);
     if (__fmul_rn(ah, w) <= P.alpha_max) dah = __fmaf_rn(w, sc[k].y, dah);
   }

@@ -27,10 +27,11 @@
 // Backward.  Per pixel, T_k is recomputed by the forward's own scan (same
 // rounding, nothing stored between the passes) and the suffix sums
 // S_k = sum_{j>k} T_j alpha_j (c_j . g) run back to front.  Each fragment's
-// two scalars (T_k alpha_k, dL/dalpha_k) go to its bucket slot; a per-point
-// kernel then gathers its (at most four) slots and the matching
-// upstream-gradient rows and writes the point's gradient with plain stores:
-// no atomics, no zero-fill pass.
+// two scalars (T_k alpha_k, dL/dalpha_k) go to the point's entry for the
+// footprint corner the fragment came from (point-major, zero where nothing
+// blended); a per-point kernel then reads its four pairs together, gathers
+// the matching upstream-gradient rows and writes the point's gradient with
+// plain stores: no atomics.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -90,7 +91,9 @@ struct RasterWs {
   unsigned long long* keys;  // [4n] bucketed fragment keys
   float* alpha;              // [4n] fragment alphas
   uint32_t* pslot;           // [4n] bucket slot of each point corner (kNoSlot off-image)
-  float2* fscal;             // [4n] backward per-fragment scalars
+  float2* fscal;             // [4n] backward per-fragment scalars, point-major: entry 4 p + c is point p's
+                             // footprint corner c (the per-point blending weights keep their own slot-major
+                             // values here)
   unsigned long long* ka;    // [4n] global-sort result (largest buckets only)
   uint32_t* va;
   unsigned long long* kb;    // [4n] global-sort scratch, then per-fragment (T_k, c_k . g)
@@ -351,6 +354,15 @@ __device__ __forceinline__ uint2 order_at(const RP& P, const RasterWs& ws, uint3
   if (o.x >= (uint32_t)m) o.x = 0;
   if ((long long)o.y >= P.n) o.y = 0;
   return o;
+}
+
+// Point-major index of the backward scalars of the fragment that point pid
+// placed at bucket slot `slot`: 4 pid + c, c the footprint corner whose slot
+// it is (from the point's slot record).  The per-point pass then reads a
+// point's four pairs as one 32-byte sector instead of four scattered ones.
+__device__ __forceinline__ uint32_t frag_index(const RasterWs& ws, uint32_t pid, uint32_t slot) {
+  const uint4 sl = __ldg(reinterpret_cast<const uint4*>(ws.pslot) + pid);
+  return 4u * pid + (sl.x == slot ? 0u : sl.y == slot ? 1u : sl.z == slot ? 2u : 3u);
 }
 
 // ------------------------------------------------------------- ordering ---
@@ -1036,6 +1048,8 @@ __device__ void blend_bwd_slots(const Group<32>& G, const RP& P, const RasterWs&
     if (b >= nb) continue;
     const bool valid = b + G.lg < nb;
     const uint32_t id = idr[r];
+    // issued here, used at the end of the chunk
+    const uint32_t dst = valid ? frag_index(ws, id, s0 + slot[r]) : 0u;
     const ChunkT<32> ct = chunk_transmittance<32>(G, P, a[r], valid, min(32, nb - b), Tc[r]);
     float mydot = 0.f;
 #pragma unroll 2
@@ -1062,7 +1076,7 @@ __device__ void blend_bwd_slots(const Group<32>& G, const RP& P, const RasterWs&
     const float suf = G.suffix_scan(term);             // this chunk, at or behind k
     const float Sk = __fadd_rn(S, G.shift_down(suf));  // strictly behind k
     const float da = __fsub_rn(__fmul_rn(ct.Tk, mydot), __fdiv_rn(Sk, __fsub_rn(1.0f, a[r])));
-    if (mine) ws.fscal[s0 + slot[r]] = make_float2(wk, da);
+    if (mine) ws.fscal[dst] = make_float2(wk, da);
     S = __fadd_rn(S, G.bcast(suf, 0));
   }
 }
@@ -1248,7 +1262,8 @@ __global__ void __launch_bounds__(kThreads, R == kRegMax ? 3 : 4) k_blend_fwd_la
 // Pass 1 recomputes the forward's chunk scans (front to back) and keeps the
 // transmittance in front of each chunk; pass 2 walks the blended chunks back
 // to front accumulating S_k = sum_{j>k} T_j alpha_j (c_j . g) and writes
-// fscal[slot_k] = (T_k alpha_k, dL/dalpha_k = T_k (c_k . g) - S_k / (1 - alpha_k)).
+// fscal[4 p + c] = (T_k alpha_k, dL/dalpha_k = T_k (c_k . g) - S_k / (1 - alpha_k)) for the
+// fragment k of point p at its footprint corner c.
 template <int V, int GA, class FT, int R>
 __device__ void blend_bwd_reg(const Group<GA>& G, const RP& P, const RasterWs& ws, uint32_t s0, int m, int nb,
                               long long pix, const FT* __restrict__ feat, const float* __restrict__ d_image) {
@@ -1292,6 +1307,8 @@ __device__ void blend_bwd_reg(const Group<GA>& G, const RP& P, const RasterWs& w
     if (b >= nb) continue;
     const bool valid = b + G.lg < nb;
     const long long id = idr[r];
+    // issued here, used at the end of the chunk
+    const uint32_t dst = valid ? frag_index(ws, (uint32_t)id, s0 + slot[r]) : 0u;
     const ChunkT<GA> ct = chunk_transmittance<GA>(G, P, a[r], valid, min(GA, nb - b), Tc[r]);
     float mydot = 0.f;
 #pragma unroll 2
@@ -1313,7 +1330,7 @@ __device__ void blend_bwd_reg(const Group<GA>& G, const RP& P, const RasterWs& w
     const float suf = G.suffix_scan(term);             // this chunk, at or behind k
     const float Sk = __fadd_rn(S, G.shift_down(suf));  // strictly behind k
     const float da = __fsub_rn(__fmul_rn(ct.Tk, mydot), __fdiv_rn(Sk, __fsub_rn(1.0f, a[r])));
-    if (mine) ws.fscal[s0 + slot[r]] = make_float2(wk, da);
+    if (mine) ws.fscal[dst] = make_float2(wk, da);
     S = __fadd_rn(S, G.bcast(suf, 0));
   }
 }
@@ -1545,8 +1562,8 @@ __device__ void blend_fwd_cta(const RP& P, KeyAt key_at, AlphaAt alpha_at, TLoad
 
 // Backward on the CTA path: T_k via the forward's scan, c_k . g split over
 // the groups, suffix sums by a CTA-wide reverse scan.
-template <int V, int GA, class FT, class KeyAt, class AlphaAt, class SlotAt, class TLoad, class DStore, class DLoad>
-__device__ void blend_bwd_cta(const RP& P, KeyAt key_at, AlphaAt alpha_at, SlotAt slot_at, TLoad t_load,
+template <int V, int GA, class FT, class KeyAt, class AlphaAt, class DstAt, class TLoad, class DStore, class DLoad>
+__device__ void blend_bwd_cta(const RP& P, KeyAt key_at, AlphaAt alpha_at, DstAt dst_at, TLoad t_load,
                               DStore d_store, DLoad d_load, int nb, long long pix, const FT* __restrict__ feat,
                               const float* __restrict__ d_image, float2* __restrict__ fscal, HeavySmem& H) {
   constexpr int kGroups = kThreads / GA;
@@ -1585,7 +1602,7 @@ __device__ void blend_bwd_cta(const RP& P, KeyAt key_at, AlphaAt alpha_at, SlotA
     __syncthreads();
     const float behind = threadIdx.x + 1 < kThreads ? H.prev[threadIdx.x + 1] : 0.f;
     const float Sk = __fadd_rn(S, behind);
-    if (valid) fscal[slot_at(k)] = make_float2(wk, __fsub_rn(__fmul_rn(Tk, dk), __fdiv_rn(Sk, __fsub_rn(1.0f, a))));
+    if (valid) fscal[dst_at(k)] = make_float2(wk, __fsub_rn(__fmul_rn(Tk, dk), __fdiv_rn(Sk, __fsub_rn(1.0f, a))));
     S = __fadd_rn(S, H.prev[0]);
     __syncthreads();
   }
@@ -1846,19 +1863,22 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd_heavy(RP P, const FT* __
     const int nb = blended_count(n_contrib, q, m);
     auto key_at = [&](int k) { return (unsigned long long)order_at(P, ws, s0, m, k).y; };
     auto alpha_at = [&](int k) { return ws.alpha[s0 + order_at(P, ws, s0, m, k).x]; };
-    auto slot_at = [&](int k) { return s0 + order_at(P, ws, s0, m, k).x; };
+    auto dst_at = [&](int k) {
+      const uint2 o = order_at(P, ws, s0, m, k);
+      return frag_index(ws, o.y, s0 + o.x);
+    };
     float T;
     if (nb <= kHeavyKeys) {
       cta_transmittance(P, alpha_at, nb, [&](int k, float v) { B.Tk[k] = v; }, H, &T);
       __syncthreads();
-      blend_bwd_cta<V, GA, FT>(P, key_at, alpha_at, slot_at, [&](int k) { return B.Tk[k]; },
+      blend_bwd_cta<V, GA, FT>(P, key_at, alpha_at, dst_at, [&](int k) { return B.Tk[k]; },
                            [&](int k, float v) { B.D[k] = v; }, [&](int k) { return B.D[k]; }, nb, q, feat, d_image,
                            ws.fscal, H);
     } else {
       float2* tmp = reinterpret_cast<float2*>(ws.kb + s0);
       cta_transmittance(P, alpha_at, nb, [&](int k, float v) { tmp[k].x = v; }, H, &T);
       __syncthreads();
-      blend_bwd_cta<V, GA, FT>(P, key_at, alpha_at, slot_at, [&](int k) { return tmp[k].x; },
+      blend_bwd_cta<V, GA, FT>(P, key_at, alpha_at, dst_at, [&](int k) { return tmp[k].x; },
                            [&](int k, float v) { tmp[k].y = v; }, [&](int k) { return tmp[k].y; }, nb, q, feat,
                            d_image, ws.fscal, H);
     }
@@ -1894,7 +1914,7 @@ __global__ void __launch_bounds__(kThreads) k_point_grad(RP P, const float* __re
       const float ah = point_alpha_h(P, opacity, feat, id, &e_h0);
       float2 sc[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) sc[k] = slots[k] == kNoSlot ? make_float2(0.f, 0.f) : __ldg(ws.fscal + slots[k]);
+      for (int k = 0; k < 4; ++k) sc[k] = slots[k] == kNoSlot ? make_float2(0.f, 0.f) : __ldg(ws.fscal + 4 * id + k);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (slots[k] == kNoSlot) continue;
