@@ -91,6 +91,7 @@ struct RasterWs {
   unsigned long long* keys;  // [4n] bucketed fragment keys
   float* alpha;              // [4n] fragment alphas
   uint32_t* pslot;           // [4n] bucket slot of each point corner (kNoSlot off-image)
+  uint32_t* porg;            // [n] footprint origin of each point: (i0 + 1) | (j0 + 1) << 16
   float2* fscal;             // [4n] backward per-fragment scalars, point-major: entry 4 p + c is point p's
                              // footprint corner c (the per-point blending weights keep their own slot-major
                              // values here)
@@ -121,6 +122,7 @@ RasterWs carve(void* base, long long n_pix, long long n) {
   w.keys = c.take<unsigned long long>(nf);
   w.alpha = c.take<float>(nf);
   w.pslot = c.take<uint32_t>(nf);
+  w.porg = c.take<uint32_t>(std::max<long long>(n, 1));
   w.fscal = c.take<float2>(nf);
   w.ka = c.take<unsigned long long>(nf);
   w.va = c.take<uint32_t>(nf);
@@ -243,7 +245,8 @@ __global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restri
                                                      const uint32_t* __restrict__ pix_start,
                                                      uint32_t* __restrict__ pix_count,
                                                      unsigned long long* __restrict__ keys,
-                                                     float* __restrict__ alpha, uint32_t* __restrict__ pslot) {
+                                                     float* __restrict__ alpha, uint32_t* __restrict__ pslot,
+                                                     uint32_t* __restrict__ porg) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int n = (int)P.n;  // <= 2^28
@@ -267,9 +270,11 @@ __global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restri
     int q[4] = {-1, -1, -1, -1};
     Splat s;
     float ah = 0.f;
+    bool splat_ok = false;
     if (id < n && splat_xyz(P, x, y, z, s)) {
       for (int k = 0; k < 4; ++k) q[k] = corner_pixel(P, s.f, k);
       ah = alpha_from_input(P, av);
+      splat_ok = true;
     }
     x = nx; y = ny; z = nz; av = na;
     const unsigned long long key = ((unsigned long long)(__float_as_uint(s.d) - P.dbase) << P.idb) | (unsigned long long)id;
@@ -300,6 +305,7 @@ __global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restri
       }
     }
     if (id < n) reinterpret_cast<uint4*>(pslot)[id] = make_uint4(slots[0], slots[1], slots[2], slots[3]);
+    if (id < n) porg[id] = splat_ok ? ((uint32_t)(s.f.i0 + 1) & 0xffffu) | ((uint32_t)(s.f.j0 + 1) << 16) : 0u;
   }
 }
 
@@ -356,13 +362,16 @@ __device__ __forceinline__ uint2 order_at(const RP& P, const RasterWs& ws, uint3
   return o;
 }
 
-// Point-major index of the backward scalars of the fragment that point pid
-// placed at bucket slot `slot`: 4 pid + c, c the footprint corner whose slot
-// it is (from the point's slot record).  The per-point pass then reads a
-// point's four pairs as one 32-byte sector instead of four scattered ones.
-__device__ __forceinline__ uint32_t frag_index(const RasterWs& ws, uint32_t pid, uint32_t slot) {
-  const uint4 sl = __ldg(reinterpret_cast<const uint4*>(ws.pslot) + pid);
-  return 4u * pid + (sl.x == slot ? 0u : sl.y == slot ? 1u : sl.z == slot ? 2u : 3u);
+// Point-major index of the backward scalars of point pid's fragment at
+// pixel (qx, qy): 4 pid + c, c = (qx - i0) + 2 (qy - j0) the footprint
+// corner of that pixel, from the point's footprint origin (a 4-byte record
+// per point that stays in L2).  The per-point pass then reads a point's four
+// pairs as one 32-byte sector instead of four scattered ones.  (A
+// mismatched pixel stays within the point's four entries.)
+__device__ __forceinline__ uint32_t frag_index(const RasterWs& ws, uint32_t pid, int qx, int qy) {
+  const uint32_t o = __ldg(ws.porg + pid);
+  const int c = (qx + 1 - (int)(o & 0xffffu)) + 2 * (qy + 1 - (int)(o >> 16));
+  return 4u * pid + ((uint32_t)c & 3u);
 }
 
 // ------------------------------------------------------------- ordering ---
@@ -1015,6 +1024,7 @@ __device__ void blend_fwd_slots(const Group<32>& G, const RP& P, const RasterWs&
 template <class FT, int R>
 __device__ void blend_bwd_slots(const Group<32>& G, const RP& P, const RasterWs& ws, uint32_t s0, int m, int nb,
                                 long long pix, const FT* __restrict__ feat, const float* __restrict__ d_image) {
+  const int qy = (int)(pix / P.cam.W), qx = (int)(pix - (long long)qy * P.cam.W);  // this pixel
   if (nb == 0) return;
   uint32_t slot[R], idr[R];
   float a[R], Tc[R];
@@ -1049,7 +1059,7 @@ __device__ void blend_bwd_slots(const Group<32>& G, const RP& P, const RasterWs&
     const bool valid = b + G.lg < nb;
     const uint32_t id = idr[r];
     // issued here, used at the end of the chunk
-    const uint32_t dst = valid ? frag_index(ws, id, s0 + slot[r]) : 0u;
+    const uint32_t dst = valid ? frag_index(ws, id, qx, qy) : 0u;
     const ChunkT<32> ct = chunk_transmittance<32>(G, P, a[r], valid, min(32, nb - b), Tc[r]);
     float mydot = 0.f;
 #pragma unroll 2
@@ -1267,6 +1277,7 @@ __global__ void __launch_bounds__(kThreads, R == kRegMax ? 3 : 4) k_blend_fwd_la
 template <int V, int GA, class FT, int R>
 __device__ void blend_bwd_reg(const Group<GA>& G, const RP& P, const RasterWs& ws, uint32_t s0, int m, int nb,
                               long long pix, const FT* __restrict__ feat, const float* __restrict__ d_image) {
+  const int qy = (int)(pix / P.cam.W), qx = (int)(pix - (long long)qy * P.cam.W);  // this pixel
   if constexpr (V == 2 && GA == 32) {  // F = 64
     blend_bwd_slots<FT, R>(G, P, ws, s0, m, nb, pix, feat, d_image);
     return;
@@ -1308,7 +1319,7 @@ __device__ void blend_bwd_reg(const Group<GA>& G, const RP& P, const RasterWs& w
     const bool valid = b + G.lg < nb;
     const long long id = idr[r];
     // issued here, used at the end of the chunk
-    const uint32_t dst = valid ? frag_index(ws, (uint32_t)id, s0 + slot[r]) : 0u;
+    const uint32_t dst = valid ? frag_index(ws, (uint32_t)id, qx, qy) : 0u;
     const ChunkT<GA> ct = chunk_transmittance<GA>(G, P, a[r], valid, min(GA, nb - b), Tc[r]);
     float mydot = 0.f;
 #pragma unroll 2
@@ -1863,10 +1874,8 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd_heavy(RP P, const FT* __
     const int nb = blended_count(n_contrib, q, m);
     auto key_at = [&](int k) { return (unsigned long long)order_at(P, ws, s0, m, k).y; };
     auto alpha_at = [&](int k) { return ws.alpha[s0 + order_at(P, ws, s0, m, k).x]; };
-    auto dst_at = [&](int k) {
-      const uint2 o = order_at(P, ws, s0, m, k);
-      return frag_index(ws, o.y, s0 + o.x);
-    };
+    const int qy = (int)(q / P.cam.W), qx = (int)(q - (long long)qy * P.cam.W);
+    auto dst_at = [&](int k) { return frag_index(ws, order_at(P, ws, s0, m, k).y, qx, qy); };
     float T;
     if (nb <= kHeavyKeys) {
       cta_transmittance(P, alpha_at, nb, [&](int k, float v) { B.Tk[k] = v; }, H, &T);
@@ -2074,7 +2083,7 @@ inpc_status bin_fragments(const RP& P, const float* pos, const float* opacity, c
   if (P.n > 0) {
     INPC_TIMED("k_pix_scatter", s,
                k_pix_scatter<FT><<<point_grid(P.n), 256, 0, s>>>(P, pos, opacity, feat, ws.pix_start, ws.pix_count,
-                                                                 ws.keys, ws.alpha, ws.pslot));
+                                                                 ws.keys, ws.alpha, ws.pslot, ws.porg));
     INPC_TRY(check_launch("k_pix_scatter"));
   }
   return INPC_OK;
