@@ -75,8 +75,10 @@ __device__ __forceinline__ PointRec point_record(const RP& P, const float* __res
   if (((fa.x | fa.y | fa.z | fa.w | fb.x | fb.y | fb.z | fb.w) & 0x7fffffffu) == 0u) return R;
   Splat sp;
   splat_xyz(P, R.x, R.y, R.z, sp);
-  float e_h0 = 0.f;
-  const float ah = point_alpha_h(P, nullptr, feat, pid, &e_h0);
+  // exp(h0) as the forward's binning pass stored it (head mode), and
+  // alpha_h = 1 - exp(-exp(h0)) from it with the same operations
+  const float e_h0 = __ldg(ws.pexp + pid);
+  const float ah = -expm1f(-e_h0);
   float dah = 0.f;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {

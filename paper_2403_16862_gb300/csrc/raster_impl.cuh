@@ -92,6 +92,7 @@ struct RasterWs {
   float* alpha;              // [4n] fragment alphas
   uint32_t* pslot;           // [4n] bucket slot of each point corner (kNoSlot off-image)
   uint32_t* porg;            // [n] footprint origin of each point: (i0 + 1) | (j0 + 1) << 16
+  float* pexp;               // [n] exp(h0) of each point (head mode)
   float2* fscal;             // [4n] backward per-fragment scalars, point-major: entry 4 p + c is point p's
                              // footprint corner c (the per-point blending weights keep their own slot-major
                              // values here)
@@ -123,6 +124,7 @@ RasterWs carve(void* base, long long n_pix, long long n) {
   w.alpha = c.take<float>(nf);
   w.pslot = c.take<uint32_t>(nf);
   w.porg = c.take<uint32_t>(std::max<long long>(n, 1));
+  w.pexp = c.take<float>(std::max<long long>(n, 1));
   w.fscal = c.take<float2>(nf);
   w.ka = c.take<unsigned long long>(nf);
   w.va = c.take<uint32_t>(nf);
@@ -177,14 +179,13 @@ __device__ __forceinline__ float point_alpha_h(const RP& P, const float* __restr
 }
 
 // ---------------------------------------------------------------- binning ---
-// The input of a point's alpha_h (h0 in head mode, else the given opacity)
-// and alpha_h from it, the same operations as point_alpha_h.
+// The input of a point's alpha_h: h0 in head mode, else the given opacity
+// (the scatter forms alpha_h from it with point_alpha_h's operations).
 template <class FT>
 __device__ __forceinline__ float alpha_input(const RP& P, const float* __restrict__ opacity,
                                              const FT* __restrict__ feat, long long id) {
   return P.head ? ld1(feat + (long long)P.F * id) : __ldg(opacity + id);
 }
-__device__ __forceinline__ float alpha_from_input(const RP& P, float v) { return P.head ? -expm1f(-expf(v)) : v; }
 
 // Warp aggregation of the per-pixel counters: points come grouped by leaf,
 // so consecutive lanes often hit the same pixel.  A run of equal pixels over
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restri
                                                      uint32_t* __restrict__ pix_count,
                                                      unsigned long long* __restrict__ keys,
                                                      float* __restrict__ alpha, uint32_t* __restrict__ pslot,
-                                                     uint32_t* __restrict__ porg) {
+                                                     uint32_t* __restrict__ porg, float* __restrict__ pexp) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int n = (int)P.n;  // <= 2^28
@@ -271,9 +272,13 @@ __global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restri
     Splat s;
     float ah = 0.f;
     bool splat_ok = false;
+    float e_h0 = 0.f;
     if (id < n && splat_xyz(P, x, y, z, s)) {
       for (int k = 0; k < 4; ++k) q[k] = corner_pixel(P, s.f, k);
-      ah = alpha_from_input(P, av);
+      // head mode: alpha_h = 1 - exp(-exp(h0)) as in point_alpha_h, with
+      // exp(h0) kept for the backward's opacity path
+      e_h0 = P.head ? expf(av) : 0.f;
+      ah = P.head ? -expm1f(-e_h0) : av;
       splat_ok = true;
     }
     x = nx; y = ny; z = nz; av = na;
@@ -306,6 +311,7 @@ __global__ void __launch_bounds__(256) k_pix_scatter(RP P, const float* __restri
     }
     if (id < n) reinterpret_cast<uint4*>(pslot)[id] = make_uint4(slots[0], slots[1], slots[2], slots[3]);
     if (id < n) porg[id] = splat_ok ? ((uint32_t)(s.f.i0 + 1) & 0xffffu) | ((uint32_t)(s.f.j0 + 1) << 16) : 0u;
+    if (id < n && P.head) pexp[id] = e_h0;
   }
 }
 
@@ -2083,7 +2089,7 @@ inpc_status bin_fragments(const RP& P, const float* pos, const float* opacity, c
   if (P.n > 0) {
     INPC_TIMED("k_pix_scatter", s,
                k_pix_scatter<FT><<<point_grid(P.n), 256, 0, s>>>(P, pos, opacity, feat, ws.pix_start, ws.pix_count,
-                                                                 ws.keys, ws.alpha, ws.pslot, ws.porg));
+                                                                 ws.keys, ws.alpha, ws.pslot, ws.porg, ws.pexp));
     INPC_TRY(check_launch("k_pix_scatter"));
   }
   return INPC_OK;
