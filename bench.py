@@ -82,7 +82,7 @@ def algorithmic_bytes(n, n_leaves, n_entries, n_frag, n_pix):
 
 KERNELS = ["k_draw_count", "k_place", "k_hash_fwd", "k_pix_count", "k_pix_scatter", "k_blend_fwd",
            "k_blend_fwd_large", "k_blend_fwd_heavy", "k_blend_bwd", "k_blend_bwd_large", "k_blend_bwd_heavy",
-           "k_point_grad_hash", "k_point_grad", "k_hash_bwd"]
+           "k_point_grad_hash", "k_grad_fine", "k_point_grad", "k_hash_bwd"]
 
 # Counters of one launch of the dominant kernel on the full workload, from one
 # ncu capture each (profiles/ holds the command and the summary):

@@ -314,9 +314,13 @@ inpc_status inpc_rasterize_bwd(const inpc_camera* cam, const inpc_raster_opts* o
  *   grad_table  float32 [n_entries, n_feats], accumulated (+=)
  *   d_feat      optional float32 [n, F]: also written when non-NULL
  * The workspace is the forward's, sized by
- * inpc_rasterize_bwd_hashgrid_workspace_size (the same size as the
- * rasterizer's).  Additions into grad_table are atomic, so several calls
- * may accumulate into one table concurrently.  Other arguments as for
+ * inpc_rasterize_bwd_hashgrid_workspace_size: the rasterizer's size, plus,
+ * when the gradient rows of the fine half of the levels (levels n_levels/2
+ * and up for 16 levels) exceed 64 MB, n * (those levels) * 16 bytes in which
+ * the fine levels' gradient rows wait for a second pass that adds them
+ * level group by level group, so that the rows receiving additions stay in
+ * L2.  Additions into grad_table are atomic, so several calls may
+ * accumulate into one table concurrently.  Other arguments as for
  * inpc_rasterize_bwd. */
 inpc_status inpc_rasterize_bwd_hashgrid_workspace_size(const inpc_camera* cam, const inpc_raster_opts* opts,
                                                        const inpc_hashgrid_desc* grid, int64_t n, size_t* bytes);

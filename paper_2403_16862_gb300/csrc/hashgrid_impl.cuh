@@ -76,16 +76,20 @@ struct LevelGroups {
   int begin[kMaxLevels + 1];  // group j covers levels begin[j] .. begin[j + 1] - 1
 };
 
-inline LevelGroups plan_level_groups(const GridParams& P, int row_bytes) {
+// Rows of level l.
+inline long long level_rows(const GridParams& P, int l) {
+  const long long side = P.side[l];
+  return P.dense[l] ? side * side * side : (long long)P.hash_mask + 1;
+}
+
+// Level groups of the levels l_first .. n_levels - 1.
+inline LevelGroups plan_level_groups(const GridParams& P, int row_bytes, int l_first = 0) {
   LevelGroups g;
   g.n = 0;
   long long bytes = 0;
-  for (int l = 0; l < P.n_levels; l += 2) {
+  for (int l = l_first; l < P.n_levels; l += 2) {
     long long pair = 0;
-    for (int k = l; k < l + 2 && k < P.n_levels; ++k) {
-      const long long side = P.side[k];
-      pair += (P.dense[k] ? side * side * side : (long long)P.hash_mask + 1) * row_bytes;
-    }
+    for (int k = l; k < l + 2 && k < P.n_levels; ++k) pair += level_rows(P, k) * row_bytes;
     if (g.n == 0 || bytes + pair > kQueryL2Budget) {
       g.begin[g.n++] = l;
       bytes = 0;

@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
                                                                const FT* __restrict__ feat,
                                                                const float* __restrict__ d_image, RasterWs ws,
                                                                float* __restrict__ grad_table,
-                                                               float* __restrict__ d_feat, int chunk) {
+                                                               float* __restrict__ d_feat, float* __restrict__ dfine,
+                                                               int chunk) {
   constexpr int kH = GA / 2;                      // levels per half
   constexpr int kPW = 16 / kH;                    // points per warp (two lanes per level)
   constexpr int kGroups = (kThreads / 64) * kPW;  // points in flight per CTA
@@ -189,6 +190,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
       if (!active) continue;
       if (d_feat && bx == 0)
         *reinterpret_cast<float4*>(d_feat + (long long)id * P.F + ch) = make_float4(dc[0], dc[1], dc[2], dc[3]);
+      if (!coarse && dfine) {
+        // deferred fine levels: the row goes to k_grad_fine (level-major, so
+        // that pass reads a level's rows of consecutive points together)
+        if (bx == 0) __stcs(reinterpret_cast<float4*>(dfine) + (long long)lvl * P.n + id, make_float4(dc[0], dc[1], dc[2], dc[3]));
+        continue;
+      }
       if (dc[0] == 0.f && dc[1] == 0.f && dc[2] == 0.f && dc[3] == 0.f) continue;
       uint32_t cx, cy, cz;
       float gx[2], gy[2], gz[2];
@@ -256,10 +263,73 @@ __global__ void __launch_bounds__(kThreads, 4) k_point_grad_hash(RP P, GridParam
   }
 }
 
+// The fine levels of the grid adjoint, deferred: for tables whose fine
+// levels do not fit in L2, reductions into them from the fused kernel miss
+// L2 and go to DRAM twice (a read before the add, a write-back later).  The
+// fused kernel then stores each point's gradient row of every fine level
+// (dL/dh of the level, 4 floats; level-major in dfine) instead of reducing
+// it, and this pass adds the corner contributions level group after level
+// group (plan_level_groups), so the rows receiving reductions at a time are
+// one group's and stay in L2.  Two lanes per point, one per x vertex of the
+// cell, 16 consecutive points per warp; the contributions are the fused
+// kernel's own, (w_x w_y) w_z times the row.
+__global__ void __launch_bounds__(256) k_grad_fine(GridParams Gp, LevelGroups LG, int l_first,
+                                                   const float* __restrict__ pos, const float* __restrict__ dfine,
+                                                   long long n, float* __restrict__ grad_table) {
+  const int lb = LG.begin[blockIdx.y], le = LG.begin[blockIdx.y + 1];
+  const uint64_t keep = l2_evict_last(), stream = l2_evict_first();
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t bx = lane & 1u;
+  // n <= 2^25 (the limit of the backward calls): 32-bit point indices
+  const uint32_t n_groups = (uint32_t)((n + 15) >> 4);
+  const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_groups; g += n_warps) {
+    const uint32_t p = g * 16u + (lane >> 1);
+    if (p >= (uint32_t)n) continue;  // nothing below is warp-collective
+    const float x = __ldg(pos + 3 * p + 0), y = __ldg(pos + 3 * p + 1), z = __ldg(pos + 3 * p + 2);
+    for (int l = lb; l < le; ++l) {
+      const uint4 r = ld_hint_u4(reinterpret_cast<const uint4*>(dfine) + (long long)(l - l_first) * n + p, stream);
+      const float4 d = make_float4(__uint_as_float(r.x), __uint_as_float(r.y), __uint_as_float(r.z),
+                                   __uint_as_float(r.w));
+      if (d.x == 0.f && d.y == 0.f && d.z == 0.f && d.w == 0.f) continue;
+      uint32_t cx, cy, cz;
+      float gx[2], gy[2], gz[2];
+      const int N = Gp.res[l];
+      cell_frac(x, N, cx, gx[0], gx[1]);
+      cell_frac(y, N, cy, gy[0], gy[1]);
+      cell_frac(z, N, cz, gz[0], gz[1]);
+      float* gl = grad_table + 4 * Gp.offset[l];
+      const float wx = gx[bx];
+#pragma unroll
+      for (int yz = 0; yz < 4; ++yz) {
+        const int by = yz & 1, bz = yz >> 1;
+        const float w = wx * gy[by] * gz[bz];
+        const uint32_t row = vertex_row(Gp, l, cx + bx, cy + by, cz + bz);
+        red_add_v4(gl + 4ull * row, make_float4(w * d.x, w * d.y, w * d.z, w * d.w), keep);
+      }
+    }
+  }
+}
+
+// Levels per half of the fused kernel's warp pairs for a grid of n_levels
+// levels (the template size it is launched with, halved).
+inline int adjoint_half(int n_levels) { return n_levels <= 8 ? 4 : n_levels <= 16 ? 8 : 16; }
+
+// Whether the fine half's gradient rows are deferred to k_grad_fine (they
+// do not fit the L2 budget), and the bytes of its row buffer.
+inline size_t fine_defer_bytes(const GridParams& Gp, long long n) {
+  const int kH = adjoint_half(Gp.n_levels);
+  if (Gp.n_levels <= kH) return 0;
+  long long rows = 0;
+  for (int l = kH; l < Gp.n_levels; ++l) rows += level_rows(Gp, l);
+  if (rows * 16 <= kQueryL2Budget) return 0;
+  return (size_t)std::max<long long>(n, 1) * (size_t)(Gp.n_levels - kH) * 16;
+}
+
 template <int GA, class FT>
 inpc_status launch_point_grad_hash(const RP& P, const GridParams& Gp, const float* pos, const FT* feat,
                                    const float* d_image, const RasterWs& ws, float* grad_table, float* d_feat,
-                                   cudaStream_t s) {
+                                   float* dfine, cudaStream_t s) {
   constexpr int kGroups = (kThreads / 64) * (32 / GA);  // points in flight per CTA
   // kRun points per group and CTA chunk, as many CTAs as that needs up to
   // 32 per SM (longer runs beyond that)
@@ -269,9 +339,16 @@ inpc_status launch_point_grad_hash(const RP& P, const GridParams& Gp, const floa
   const long long grid = ceil_div(P.n, chunk);
   INPC_TIMED("k_point_grad_hash", s,
              k_point_grad_hash<GA, FT><<<(unsigned)std::max<long long>(grid, 1), kThreads, 0, s>>>(
-                 P, Gp, pos, feat, d_image, ws, grad_table, d_feat, (int)chunk));
+                 P, Gp, pos, feat, d_image, ws, grad_table, d_feat, dfine, (int)chunk));
   INPC_TRY(check_launch("k_point_grad_hash"));
-  return INPC_OK;
+  if (!dfine) return INPC_OK;
+  constexpr int kH = GA / 2;
+  const LevelGroups LG = plan_level_groups(Gp, 16, kH);
+  const long long cap = (long long)device_sm_count() * 16;
+  const dim3 g2((unsigned)std::max<long long>(1, std::min<long long>((long long)ceil_div(2 * P.n, 256), cap)),
+                (unsigned)LG.n);
+  INPC_TIMED("k_grad_fine", s, k_grad_fine<<<g2, 256, 0, s>>>(Gp, LG, kH, pos, dfine, P.n, grad_table));
+  return check_launch("k_grad_fine");
 }
 
 }  // namespace
@@ -327,7 +404,10 @@ extern "C" inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const
   if (P.F != 4 * Gp.n_levels)
     return fail(INPC_ERR_INVALID_ARG, "n_channels (%d) must equal n_levels * n_feats (%d)", P.F, 4 * Gp.n_levels);
   const RasterWs need = carve(nullptr, P.n_pix, n);
-  const size_t total = need.bytes;
+  // the deferred fine-level rows (large tables) follow the rasterizer's part
+  const size_t fine_off = (need.bytes + 255) / 256 * 256;
+  const size_t fine_bytes = fine_defer_bytes(Gp, n);
+  const size_t total = fine_bytes ? fine_off + fine_bytes : need.bytes;
   if (!workspace || workspace_bytes < total || !aligned(workspace, 256))
     return fail(INPC_ERR_INVALID_ARG,
                 "workspace null, unaligned or smaller than %zu bytes (inpc_rasterize_bwd_hashgrid_workspace_size)",
@@ -340,6 +420,7 @@ extern "C" inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const
     return fail(INPC_ERR_INVALID_ARG, "feat/d_image/grad_table/d_feat misaligned");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   RasterWs ws = carve(workspace, P.n_pix, n);
+  float* dfine = fine_bytes ? reinterpret_cast<float*>(static_cast<char*>(workspace) + fine_off) : nullptr;
   return dispatch(P.F, [&](auto Vc, auto Gc) -> inpc_status {
     constexpr int V = decltype(Vc)::value, GA = decltype(Gc)::value;
     auto run = [&](auto ftag) -> inpc_status {
@@ -347,10 +428,10 @@ extern "C" inpc_status inpc_rasterize_bwd_hashgrid(const inpc_camera* cam, const
       const FT* f = static_cast<const FT*>(feat);
       INPC_TRY((launch_blend_bwd<V, GA, FT>(P, f, n_contrib, d_image, ws, s)));
       if (Gp.n_levels <= 8)
-        return launch_point_grad_hash<8, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, s);
+        return launch_point_grad_hash<8, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, dfine, s);
       if (Gp.n_levels <= 16)
-        return launch_point_grad_hash<16, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, s);
-      return launch_point_grad_hash<32, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, s);
+        return launch_point_grad_hash<16, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, dfine, s);
+      return launch_point_grad_hash<32, FT>(P, Gp, pos, f, d_image, ws, grad_table, d_feat, dfine, s);
     };
     if constexpr (GA != 32) {
       if (P.bf16) return fail(INPC_ERR_UNSUPPORTED, "BF16 features need n_channels = 32, 64 or 128");
@@ -373,6 +454,8 @@ extern "C" inpc_status inpc_rasterize_bwd_hashgrid_workspace_size(const inpc_cam
   GridParams Gp;
   int64_t n_entries = 0;
   INPC_TRY(make_params(grid, Gp, &n_entries));
-  *bytes = carve(nullptr, P.n_pix, n).bytes;
+  const size_t base = carve(nullptr, P.n_pix, n).bytes;
+  const size_t fine_bytes = fine_defer_bytes(Gp, n);
+  *bytes = fine_bytes ? (base + 255) / 256 * 256 + fine_bytes : base;
   return INPC_OK;
 }

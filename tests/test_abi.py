@@ -55,6 +55,24 @@ def test_workspace_sizes(B):
     assert s1 % 256 == 0 and w % 256 == 0
 
 
+def test_fused_backward_defers_fine_levels_of_large_tables(B):
+    # The fused backward's fine half (levels 8..15 of 16) reduces in place
+    # while its gradient rows fit the 64 MB L2 budget (2^19 rows of 16 B per
+    # level: 64 MB); larger tables store those levels' rows, 16 B per point
+    # and level, for the level-grouped pass: the workspace grows by that
+    # buffer, 256-byte aligned.
+    from paper_2403_16862_gb300 import api
+    cam = scenes.make_camera((0.5, 0.5, -1.2), 900, 900, 640, 416, 1280, 832)
+    opts = api.RasterOptions(n_channels=64, head_mode=True)
+    res = scenes.geometric_resolutions(16, 16, 4096)
+    n = 1 << 20 | 3
+    base = api.rasterize_bwd_hashgrid_workspace_size(cam, opts, api.hashgrid_desc(res, 19), n)
+    assert base == api.rasterize_workspace_size(cam, opts, n)
+    for log2_T in (20, 21):
+        big = api.rasterize_bwd_hashgrid_workspace_size(cam, opts, api.hashgrid_desc(res, log2_T), n)
+        assert big == (base + 255) // 256 * 256 + n * 8 * 16, log2_T
+
+
 def test_argument_errors_are_reported(B):
     from paper_2403_16862_gb300 import api
     with pytest.raises(B.InpcError) as e:

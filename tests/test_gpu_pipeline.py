@@ -122,6 +122,14 @@ def test_pipeline_full_size(gpu, oracle):
     _pipeline(gpu, oracle, 65536, 4_194_304, 19, cam, seed=0, margins=True)
 
 
+def test_pipeline_large_table(gpu, oracle):
+    """A 2^20 grid: the fine levels' gradient rows (8 x 16 MB) exceed the L2
+    budget, so the fused backward stores them and the level-grouped pass
+    (k_grad_fine) reduces them."""
+    cam = scenes.make_camera((0.5, 0.5, -1.2), 900 * 0.25, 900 * 0.25, 160, 104, 320, 208)
+    _pipeline(gpu, oracle, 4096 + 7 * 300, 200_000, 20, cam, seed=5)
+
+
 @pytest.mark.parametrize("n_levels", [6, 8, 24, 32])
 def test_fused_backward_level_counts(gpu, oracle, n_levels):
     """The fused rasterizer backward + grid adjoint for level counts other
