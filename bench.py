@@ -91,8 +91,8 @@ KERNELS = ["k_draw_count", "k_place", "k_hash_fwd", "k_pix_count", "k_pix_scatte
 # with the stamp of the kernel's sources at the time of the capture.  A
 # different stamp means the kernel changed since: the counters are then
 # reported as null rather than as figures of another kernel.
-CAPTURED = {"k_point_grad_hash": {"traffic": 2_204_281_344 + 552_597_760, "l2_reductions": 243_215_743,
-                                  "stamp": "c27205694823d259"}}
+CAPTURED = {"k_point_grad_hash": {"traffic": 695_734_272 + 217_977_344, "l2_reductions": 243_242_201,
+                                  "stamp": "90bcd4f3ad395052"}}
 # the sources each kernel's code comes from (stamped for CAPTURED); "step":
 # every kernel of one view
 KERNEL_SOURCES = {"k_point_grad_hash": ["raster_bwd.cu", "raster_impl.cuh", "hashgrid_impl.cuh", "common.cuh"],
@@ -102,7 +102,7 @@ KERNEL_SOURCES = {"k_point_grad_hash": ["raster_bwd.cu", "raster_impl.cuh", "has
 # DRAM bytes (read + write) of every kernel of one view on the full workload,
 # the library's kernels and the table-gradient clear, summed from one ncu
 # capture of all launches (mean of its 5 views); profiles/ holds the command
-STEP_CAPTURED = {"dram_bytes": 8_614_000_000, "stamp": "a2ef0992ced6fc31"}
+STEP_CAPTURED = {"dram_bytes": 7_068_000_000, "stamp": "a377b99269f29254"}
 
 
 def source_stamp(kernel):
@@ -439,6 +439,25 @@ def main():
                                                 and STEP_CAPTURED["stamp"] == source_stamp("step")) else None
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_bytes else None
 
+    # the L2 reduction ceiling the grid adjoint's table additions run into,
+    # measured on this GPU after the timed region (8 MB region, the size of
+    # one hashed level's gradient rows)
+    l2_ceiling = None
+    if dom == "k_point_grad_hash" and not args.unfused:
+        cal = torch.zeros(1 << 19, 4, dtype=torch.float32, device=dev)
+        cs = torch.cuda.current_stream().cuda_stream
+        single = B.inpc_l2_reduction_rate(cal.data_ptr(), 1 << 19, False, cs)
+        paired = B.inpc_l2_reduction_rate(cal.data_ptr(), 1 << 19, True, cs)
+        del cal
+        red = captured(dom, "l2_reductions")
+        rate = red / (dom_ms * 1e-3) / 1e9 if red else None
+        l2_ceiling = {
+            "probe": "inpc_l2_reduction_rate: 16-byte red.global.add.v4.f32 into random rows of an 8 MB region, "
+                     "8 CTAs x 256 threads per SM, evict_last",
+            "single_row_requests_gops": single, "paired_rows_gops": paired, "paired_requests_gops": paired / 2,
+            "kernel_requests_gops": rate,
+            "frac_of_single_row_requests": rate / single if rate else None}
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, api, B, tree, grid, cam, g_np, res, desc, opts, dev, world, rank)
@@ -466,7 +485,8 @@ def main():
                          "traffic": captured(dom, "traffic") if not args.unfused else None,
                          "counters_stamp": source_stamp(dom),
                          "peak_kind": peak_kind + " (copy bandwidth)", "launch_ms": dom_ms,
-                         "algorithmic_bytes": dom_bytes, **atomic_ceiling(dom, N, dom_ms)},
+                         "algorithmic_bytes": dom_bytes, **atomic_ceiling(dom, N, dom_ms),
+                         "l2_reduction_ceiling": l2_ceiling},
             "step_roofline": {"algorithmic_bytes": total_bytes,
                               "achieved_gbs": total_bytes / (ms_per_step * 1e-3) / 1e9,
                               "frac": total_bytes / (ms_per_step * 1e-3) / 1e9 / peak,

@@ -629,6 +629,25 @@ inpc_status inpc_render_batch_persistent(const inpc_octree* tree, uint64_t seed,
  * INPC_ERR_INVALID_ARG (unknown spec). */
 inpc_status inpc_set_fault(const char* spec);
 
+/* Calibration for roofline reporting (no counterpart in the paper): the
+ * rate at which this GPU performs the operation that bounds the grid
+ * adjoint's table-gradient additions (the adjoint of the Sec. 3.3 query in
+ * the App. A.6 backward), 16-byte FP32 vector reductions
+ * (red.global.add.v4.f32) into uniformly random rows of an L2-resident
+ * region.  Every SM runs 8 CTAs of 256 threads, each thread 128 reductions
+ * per launch; two launches warm up, five are timed with CUDA events on
+ * `stream`, and the call waits for them.
+ *   buf      device float32 [rows, 4], 16-byte aligned, owned by the caller;
+ *            its contents are overwritten (sums of ones)
+ *   rows     a power of two in [2^10, 2^26] (the region: rows * 16 bytes)
+ *   paired   0: every lane reduces into its own random row; 1: lanes 2j and
+ *            2j + 1 reduce into the two rows of one 32-byte sector, as the
+ *            adjoint's x-vertex pairs do
+ *   gops     out: rows reduced per second / 1e9 (lane reductions)
+ * Errors: INPC_ERR_INVALID_ARG (null pointers, misaligned buf, rows not a
+ * power of two in range), INPC_ERR_CUDA. */
+inpc_status inpc_l2_reduction_rate(float* buf, int64_t rows, int32_t paired, double* gops, inpc_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

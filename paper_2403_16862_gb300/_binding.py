@@ -48,7 +48,7 @@ DECLARED = [
     "inpc_contract_positions", "inpc_sh_head_fwd", "inpc_sh_head_bwd",
     "inpc_render_batch", "inpc_philox4x32_10",
     "inpc_sample_query_batch_workspace_size", "inpc_sample_query_batch", "inpc_render_batch_persistent",
-    "inpc_set_fault",
+    "inpc_set_fault", "inpc_l2_reduction_rate",
 ]
 
 
@@ -162,6 +162,7 @@ def load(path: str = LIB_PATH):
                                                    _P, C.POINTER(InpcViewJob), C.c_int32, _P, C.POINTER(_P),
                                                    C.c_int32, _P, C.c_size_t, C.c_int64]
         L.inpc_set_fault.argtypes = [C.c_char_p]
+        L.inpc_l2_reduction_rate.argtypes = [_P, C.c_int64, C.c_int32, C.POINTER(C.c_double), _P]
         L.inpc_kernel_timer_enable.argtypes = [C.c_int]
         L.inpc_kernel_timer_read.argtypes = [C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         for name in DECLARED:
@@ -391,3 +392,11 @@ def inpc_sample_query_batch(tree: InpcOctree, seed: int, desc: InpcHashgridDesc,
 
 def inpc_set_fault(spec):
     check(load().inpc_set_fault(spec.encode() if spec else None))
+
+
+def inpc_l2_reduction_rate(buf: int, rows: int, paired: bool, stream) -> float:
+    """Rows reduced per second / 1e9 by 16-byte FP32 vector reductions into
+    random rows of the caller's region (calibration for roofline reports)."""
+    out = C.c_double(0.0)
+    check(load().inpc_l2_reduction_rate(buf, rows, 1 if paired else 0, C.byref(out), stream))
+    return float(out.value)

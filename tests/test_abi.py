@@ -89,6 +89,12 @@ def test_argument_errors_are_reported(B):
     with pytest.raises(B.InpcError) as e:
         B.inpc_hashgrid_n_entries(d)
     assert e.value.status == B.INPC_ERR_INVALID_ARG
+    # the calibration's region must be a power of two of rows in range, and
+    # its buffer 16-byte aligned (checked before anything touches a device)
+    for rows, buf in ((3 << 12, 1 << 20), (1 << 9, 1 << 20), (1 << 27, 1 << 20), (1 << 16, (1 << 20) + 4)):
+        with pytest.raises(B.InpcError) as e:
+            B.inpc_l2_reduction_rate(buf, rows, False, None)
+        assert e.value.status == B.INPC_ERR_INVALID_ARG, rows
     # null pointers are rejected before anything touches a device
     d = api.hashgrid_desc([16, 32], 10)
     with pytest.raises(B.InpcError) as e:

@@ -92,6 +92,7 @@ def _calls(B):
                                                                                [fake], fake, big, 1000),
         "inpc_sample_query_batch": lambda: B.inpc_sample_query_batch(tree, 0, desc, fake, [fv], 1000, fake, big,
                                                                      None),
+        "inpc_l2_reduction_rate": lambda: B.inpc_l2_reduction_rate(fake, 1 << 16, False, None),
     }
 
 
