@@ -927,6 +927,16 @@ __device__ __forceinline__ void load_grad16(const float* __restrict__ g, int q, 
   }
 }
 
+// L2 prefetch of point id's 64-channel feature row (each of its 128-byte
+// lines), issued as soon as a lane knows which row it will need so that the
+// gather finds it in L2.
+template <class FT>
+__device__ __forceinline__ void prefetch_row64(const FT* __restrict__ feat, uint32_t id) {
+  const char* p = reinterpret_cast<const char*>(feat + 64ll * id);
+#pragma unroll
+  for (int k = 0; k < (int)(64 * sizeof(FT)) / 128; ++k) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + 128 * k));
+}
+
 template <class FT, int R>
 __device__ void blend_fwd_slots(const Group<32>& G, const RP& P, const RasterWs& ws, uint32_t s0, int m,
                                 long long pix, const FT* __restrict__ feat, FT* __restrict__ image,
@@ -953,6 +963,10 @@ __device__ void blend_fwd_slots(const Group<32>& G, const RP& P, const RasterWs&
     }
   }
   load_sorted<32, R>(G, P, ws.keys, s0, m, key);
+  // the nearest 64 fragments' rows (blending usually stops within them)
+#pragma unroll
+  for (int r = 0; r < (R < 2 ? R : 2); ++r)
+    if (r * 32 + G.lg < m) prefetch_row64(feat, (uint32_t)reg_id(P, key[r]));
   float a_sorted[R];
   if constexpr (R <= 2) {
 #pragma unroll
@@ -1049,6 +1063,7 @@ __device__ void blend_bwd_slots(const Group<32>& G, const RP& P, const RasterWs&
         slot[r] = o.x;
         idr[r] = o.y;
         a[r] = ws.alpha[s0 + o.x];
+        prefetch_row64(feat, o.y);
       }
       const ChunkT<32> ct = chunk_transmittance<32>(G, P, a[r], valid, min(32, nb - b), T);
       T = G.bcast(ct.Tn, ct.take - 1);
