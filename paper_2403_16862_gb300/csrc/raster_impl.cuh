@@ -1657,24 +1657,30 @@ struct HeavyBuf {
 };
 
 // Front selection for the forward CTA path.  Blending stops once T drops
-// below t_min, which on these buckets takes well under kSelectWant
-// fragments, so only the front of a large bucket needs ordering: a
-// 256-bin histogram of the FP32 depth bits (range [min, max] of the bucket,
-// bins of 2^shift, monotone in depth) gives the smallest bin b* whose
-// cumulative count reaches kSelectWant; every key in bins <= b* is nearer
-// than every key above, so those C candidates are an exact prefix of the
-// order.  Up to 256 candidates are sorted by one warp in registers (no
-// barrier between the network's stages), more by the CTA in shared memory
-// (bitonic_sort_idx).  Returns C, or 0 when the
-// prefix does not fit (C > kHeavyKeys); the caller blends the candidates
-// and falls back to the full sort when they do not reach t_min.  (On the
-// benchmark scene 99 % of the pixels blend at most 66 fragments; targets of
-// 64 and 96 ran equally fast, 256 took 15 % longer.)
+// below t_min, which on these buckets usually takes well under a hundred
+// fragments, so only the front of a large bucket needs ordering: a 256-bin
+// histogram of the FP32 depth bits (range [min, max] of the bucket, bins
+// of 2^shift, monotone in depth) gives the smallest bin b* whose cumulative
+// count reaches `want`; every key in bins < b* is nearer than every key in
+// b* and above.  When b* holds many keys (a tight cluster of depths), a
+// second 256-bin histogram over b*'s finer bits picks the sub-bin where the
+// count reaches `want`.  Either way the selected keys (depth bits up to a
+// threshold) are an exact prefix of the order.  Up to 256 candidates are
+// sorted by one warp in registers (no barrier between the network's
+// stages), more by the CTA in shared memory (bitonic_sort_idx).  Returns
+// the candidate count C, or 0 when the prefix does not fit (C > kHeavyKeys).
+// The caller blends the candidates when they reach t_min and otherwise asks
+// again with a larger `want` (the depth range is measured once per pixel,
+// on the first call).  (On the benchmark scene 99 % of the pixels blend at
+// most 66 fragments; targets of 64 and 96 ran equally fast, 256 took 15 %
+// longer.)
 constexpr int kSelectWant = 96;
 
 struct SelSmem {
   uint32_t dmin, dmax;
   int bstar, count, fill;
+  uint32_t before;  // keys in the bins below b*
+  int b2star;       // sub-bin of b* (-1: the whole bin)
 };
 
 // One warp sorts the C <= 32 R candidates B.K[0 .. C) and writes the
@@ -1692,37 +1698,45 @@ __device__ __forceinline__ void warp_sort_candidates(const RP& P, const HeavyBuf
 }
 
 __device__ int cta_select_front(const RP& P, const RasterWs& ws, uint32_t s0, int m, const HeavyBuf& B, SortSmem& S,
-                                SelSmem& X) {
+                                SelSmem& X, int want, bool range_known) {
   const int lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    X.dmin = 0xFFFFFFFFu;
-    X.dmax = 0u;
-    X.fill = 0;
-  }
   // the sweeps load kUnroll keys per thread before using them, so that the
   // loads of a sweep are in flight together
   constexpr int kUnroll = 8;
-  uint32_t lo = 0xFFFFFFFFu, hi = 0u;
-  for (int i0 = threadIdx.x; i0 < m; i0 += kUnroll * kThreads) {
-    uint32_t d[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int i = i0 + u * kThreads;
-      d[u] = i < m ? (uint32_t)(__ldg(ws.keys + s0 + i) >> P.idb) : 0u;
+  if (!range_known) {
+    if (threadIdx.x == 0) {
+      X.dmin = 0xFFFFFFFFu;
+      X.dmax = 0u;
     }
+    uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+    for (int i0 = threadIdx.x; i0 < m; i0 += kUnroll * kThreads) {
+      uint32_t d[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
-      if (i0 + u * kThreads < m) {
-        lo = min(lo, d[u]);
-        hi = max(hi, d[u]);
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * kThreads;
+        d[u] = i < m ? (uint32_t)(__ldg(ws.keys + s0 + i) >> P.idb) : 0u;
       }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+        if (i0 + u * kThreads < m) {
+          lo = min(lo, d[u]);
+          hi = max(hi, d[u]);
+        }
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    __syncthreads();
+    if (lane == 0) {
+      atomicMin(&X.dmin, lo);
+      atomicMax(&X.dmax, hi);
+    }
   }
-  lo = __reduce_min_sync(0xffffffffu, lo);
-  hi = __reduce_max_sync(0xffffffffu, hi);
-  __syncthreads();
-  if (lane == 0) {
-    atomicMin(&X.dmin, lo);
-    atomicMax(&X.dmax, hi);
+  if (threadIdx.x == 0) {
+    X.fill = 0;
+    X.bstar = 255;  // reached below whenever want <= m
+    X.count = m;
+    X.before = 0;
+    X.b2star = -1;
   }
   S.hist[threadIdx.x] = 0;
   __syncthreads();
@@ -1741,15 +1755,47 @@ __device__ int cta_select_front(const RP& P, const RasterWs& ws, uint32_t s0, in
       if (i0 + u * kThreads < m) atomicAdd(&S.hist[(d[u] - dmin) >> shift], 1u);
   }
   __syncthreads();
-  const uint32_t h = S.hist[threadIdx.x];
-  const uint32_t ex = cta_excl_scan256(h, S.warp_sums);  // bins below this thread's bin
-  if (ex < (uint32_t)kSelectWant && ex + h >= (uint32_t)kSelectWant) {
-    X.bstar = threadIdx.x;
-    X.count = (int)(ex + h);
+  {
+    const uint32_t h = S.hist[threadIdx.x];
+    const uint32_t ex = cta_excl_scan256(h, S.warp_sums);  // bins below this thread's bin
+    if (ex < (uint32_t)want && ex + h >= (uint32_t)want) {
+      X.bstar = threadIdx.x;
+      X.count = (int)(ex + h);
+      X.before = ex;
+    }
   }
   __syncthreads();
-  const int C = X.count;
   const uint32_t bstar = (uint32_t)X.bstar;
+  // sub-bins of b*: the next (at most 8) depth bits below the bin's
+  const int subshift = shift > 8 ? shift - 8 : 0;
+  const uint32_t submask = (1u << (shift - subshift)) - 1u;
+  if (X.count > 256 && shift > 0) {
+    S.hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i0 = threadIdx.x; i0 < m; i0 += kUnroll * kThreads) {
+      uint32_t d[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * kThreads;
+        d[u] = i < m ? (uint32_t)(__ldg(ws.keys + s0 + i) >> P.idb) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+        if (i0 + u * kThreads < m && ((d[u] - dmin) >> shift) == bstar)
+          atomicAdd(&S.hist[((d[u] - dmin) >> subshift) & submask], 1u);
+    }
+    __syncthreads();
+    const uint32_t before = X.before;
+    const uint32_t h = S.hist[threadIdx.x];
+    const uint32_t ex = cta_excl_scan256(h, S.warp_sums);
+    if (before + ex < (uint32_t)want && before + ex + h >= (uint32_t)want) {
+      X.b2star = threadIdx.x;
+      X.count = (int)(before + ex + h);
+    }
+    __syncthreads();
+  }
+  const int C = X.count;
+  const int b2star = X.b2star;
   if (C > kHeavyKeys) return 0;
   for (int i0 = threadIdx.x; i0 < m; i0 += kUnroll * kThreads) {
     unsigned long long key[kUnroll];
@@ -1761,7 +1807,10 @@ __device__ int cta_select_front(const RP& P, const RasterWs& ws, uint32_t s0, in
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int i = i0 + u * kThreads;
-      if (i < m && (((uint32_t)(key[u] >> P.idb) - dmin) >> shift) <= bstar) {
+      const uint32_t dd = (uint32_t)(key[u] >> P.idb) - dmin;
+      const uint32_t bin = dd >> shift;
+      const bool take = bin < bstar || (bin == bstar && (b2star < 0 || ((dd >> subshift) & submask) <= (uint32_t)b2star));
+      if (i < m && take) {
         const int slot = atomicAdd(&X.fill, 1);
         B.K[slot] = key[u];
         B.A[slot] = ws.alpha[s0 + i];
@@ -1801,7 +1850,7 @@ __device__ void cta_order_bucket(const RasterWs& ws, uint32_t s0, int m, const H
 }
 
 template <int V, int GA, class FT>
-__global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const FT* __restrict__ feat, RasterWs ws,
+__global__ void __launch_bounds__(kThreads, 4) k_blend_fwd_heavy(RP P, const FT* __restrict__ feat, RasterWs ws,
                                                                FT* __restrict__ image, float* __restrict__ T_final,
                                                                int32_t* __restrict__ n_contrib) {
   extern __shared__ __align__(16) unsigned char dyn[];
@@ -1822,24 +1871,26 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd_heavy(RP P, const FT* __
     const uint32_t s0 = ws.pix_start[q];
     const int m = (int)(ws.pix_start[q + 1] - s0);
     float T;
-    if (m > 2 * kSelectWant) {
-      const int C = cta_select_front(P, ws, s0, m, B, S, X);
-      if (C > 0) {
-        auto key_at = [&](int k) { return B.K[B.idx[k]]; };
-        auto alpha_at = [&](int k) { return B.A[B.idx[k]]; };
-        const int n = cta_transmittance(P, alpha_at, C, [&](int k, float v) { B.Tk[k] = v; }, H, &T);
-        if (T < P.t_min || C == m) {  // the candidates reach the stop: the prefix is all that blends
-          for (int k = threadIdx.x; k < n; k += kThreads)
-            ws.order[s0 + k] = make_uint2(B.pos[B.idx[k]], (uint32_t)(B.K[B.idx[k]] & P.idm));
-          __syncthreads();
-          blend_fwd_cta<V, GA, FT>(P, key_at, alpha_at, [&](int k) { return B.Tk[k]; }, n, T, q, feat, image,
-                               T_final, n_contrib, H);
-          __syncthreads();
-          continue;
-        }
+    bool done = false;
+    // the nearest 96 fragments, then 384, then 1,536, until the candidates
+    // reach t_min; only then (or when they do not fit) the whole bucket
+    for (int want = kSelectWant; !done && 2 * want < m && want <= kHeavyKeys; want *= 4) {
+      const int C = cta_select_front(P, ws, s0, m, B, S, X, want, want != kSelectWant);
+      if (C == 0) break;
+      auto key_at = [&](int k) { return B.K[B.idx[k]]; };
+      auto alpha_at = [&](int k) { return B.A[B.idx[k]]; };
+      const int n = cta_transmittance(P, alpha_at, C, [&](int k, float v) { B.Tk[k] = v; }, H, &T);
+      if (T < P.t_min || C == m) {  // the candidates reach the stop: the prefix is all that blends
+        for (int k = threadIdx.x; k < n; k += kThreads)
+          ws.order[s0 + k] = make_uint2(B.pos[B.idx[k]], (uint32_t)(B.K[B.idx[k]] & P.idm));
         __syncthreads();
+        blend_fwd_cta<V, GA, FT>(P, key_at, alpha_at, [&](int k) { return B.Tk[k]; }, n, T, q, feat, image,
+                             T_final, n_contrib, H);
+        done = true;
       }
+      __syncthreads();
     }
+    if (done) continue;
     cta_order_bucket(ws, s0, m, B, S);
     if (m <= kHeavyKeys) {
       auto key_at = [&](int k) { return B.K[B.idx[k]]; };
