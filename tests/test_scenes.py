@@ -72,7 +72,7 @@ def test_octree_is_seeded():
 
 
 def test_grid_resolutions_and_table():
-    # geometric from 16 to 4096 over 16 levels, floored (the survey's list)
+    # 16 b^l for l = 0..15 with b = 256^(1/15), floored: 16 to 4096 over 16 levels
     assert scenes.geometric_resolutions(16, 16, 4096) == \
         [16, 23, 33, 48, 70, 101, 147, 212, 307, 445, 645, 933, 1351, 1955, 2830, 4096]
     g = scenes.make_hashgrid(1, 200_000, [16, 32], 17)
